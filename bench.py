@@ -1,0 +1,377 @@
+"""Benchmark of the TV-Stokes hot path on GB300 (one JSON line on stdout).
+
+Workload: a 1024 x 1024 seeded synthetic scene (rectangles, discs, a linear
+ramp and two sinusoidal textures, Gaussian noise sigma = 0.1).  One step is
+one full TV-Stokes denoise through the C ABI (tvs_denoise):
+  step 1: tau0, f1 = P_K tau0 / delta, 300 global TFS updates (Algorithm 1);
+  step 2: xi, f2, then IRV1 under the overlapping Schwarz decomposition with
+          4 x 4 subdomains, overlap 8 px, k = 10 inner updates per outer
+          iteration, 30 outer iterations (Algorithms 2 and 3).
+Unit: dual updates of one grid point per second (Gpixel-iter/s), counting the
+extended grid for step 1 and each image pixel once per inner update for
+step 2.  The state (~60 MB) fits in L2, so L2 is flushed between timed steps.
+
+Also reported: time to relative duality gap 1e-4 (ms per Mpixel) for global
+step 1, global step 2 and Schwarz step 2; per-kernel device time from CUDA
+events; the roofline fraction of the dominant kernel; the FP64 oracle on the
+host cores (``cpu_baseline``).  ``--impl reference`` times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1024
+DELTA, ALPHA, EPS, T = 0.05, 10.0, 1e-3, 0.125
+ITERS1 = 300
+M2 = M1 = 4
+OVERLAP, K_INNER, OUTER = 8, 10, 30
+SIGMA = 0.1
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gap-runs", action="store_true")
+    return ap.parse_args()
+
+
+def make_input(rank: int = 0):
+    from synth import SceneSpec, noisy_scene
+    _, d0 = noisy_scene(SceneSpec(N, N, seed=rank, sigma=SIGMA, texture=True))
+    return d0
+
+
+def work_units() -> float:
+    return float((N + 1) * (N + 1) * ITERS1 + N * N * K_INNER * OUTER)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (host cores)
+# ---------------------------------------------------------------------------
+def oracle_sample(d0: np.ndarray, iters1: int, iters2: int):
+    """Run the FP64 oracle on the same image for a bounded number of updates."""
+    from oracle import schwarz as osch, tvs as otvs
+    t0 = time.perf_counter()
+    tau, _, _ = otvs.tfs(d0, DELTA, T, iters1)
+    t1 = time.perf_counter()
+    f2 = otvs.irv1_data(d0, otvs.normal_field(tau, N, N, EPS), ALPHA)
+    dd = osch.Decomp(N, N, M2, M1, OVERLAP, False)
+    osch.schwarz_irv1(f2, ALPHA, dd, T, iters2, K_INNER)
+    t2 = time.perf_counter()
+    units = (N + 1) * (N + 1) * iters1 + N * N * K_INNER * iters2
+    return units, t2 - t0, (t1 - t0, t2 - t1)
+
+
+def cpu_baseline(d0: np.ndarray) -> dict:
+    units, secs, parts = oracle_sample(d0, 8, 1)
+    return {"value": units / secs / 1e9, "unit": "Gpixel-iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle on the same 1024^2 image: 8 global TFS updates + 1 Schwarz outer "
+                      f"iteration (16 subdomains x {K_INNER} inner updates); {secs:.1f} s single-threaded "
+                      f"NumPy/SciPy",
+            "seconds": secs}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def fft_flops(L: int) -> float:
+    m = 2
+    while m < 2 * L - 2:
+        m <<= 1
+    return 5.0 * m * np.log2(m)
+
+
+def algorithmic(name: str, launches: int) -> tuple[str, float, str]:
+    R = C = N + 1
+    if name == "irv1_update":
+        return "hbm", 20.0 * N * N, "bytes"
+    if name == "tfs_update":
+        # read p (16 B), phi (4), f1 (8); write p (16) per grid point
+        return "hbm", 44.0 * R * C, "bytes"
+    if name == "schwarz2_combine":
+        return "hbm", (8 + 8 + 8 * 1.03) * N * N, "bytes"
+    if name in ("dct_rows_fwd", "dct_rows_inv"):
+        # one packed Bluestein transform (2 FFTs of length M) per pair of rows
+        return "alu", ((R + 1) // 2) * 2 * fft_flops(C), "flops"
+    if name == "dct_cols_solve":
+        return "alu", ((C + 1) // 2) * 4 * fft_flops(R), "flops"
+    if name == "schwarz2_tile":
+        # per inner update and pixel: div (4 add), residual (1), grad (2), norm (3 + sqrt),
+        # update (2 mul + 2 fma + 2 div ~ 8) -- ~20 flops
+        return "alu", 20.0 * K_INNER * (N + 8 * (M1 - 1)) * (N + 8 * (M2 - 1)), "flops"
+    return "hbm", 0.0, "bytes"
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2602_17494_gb300 import binding as B
+
+    d0_np = make_input(rank)
+    d0 = torch.from_numpy(d0_np.astype(np.float32)).to(dev)
+    tau = torch.empty((2, N + 1, N + 1), dtype=torch.float32, device=dev)
+    d = torch.empty((N, N), dtype=torch.float32, device=dev)
+    dd = B.make_decomp(M2, M1, OVERLAP, K_INNER)
+    it1, it2 = B.make_iter(ITERS1, T), B.make_iter(OUTER, T)
+    ws = B.workspace(0, N, N, dd, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return B.tvs_denoise(d0, DELTA, ALPHA, EPS, it1, it2, dd, tau=tau, d=d, ws=ws)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    # ---- device-timed steps (inputs resident in HBM) -------------------------
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+    clocks = clk.summary()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = work_units() * world * args.steps / (total_ms / 1e3) / 1e9
+
+    # ---- per-kernel device time (CUDA events around each launch) ----------
+    B.tvs_profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    prof = B.tvs_profile_read()
+    B.tvs_profile_enable(False)
+    launches = sum(v[0] for v in prof.values()) // args.steps
+
+    # ---- end to end through the API with pinned host buffers -------------
+    d0_host = torch.from_numpy(d0_np.astype(np.float32)).pin_memory()
+    d_host = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    d0_dev = torch.empty_like(d0)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d0_dev.copy_(d0_host, non_blocking=True)
+        B.tvs_denoise(d0_dev, DELTA, ALPHA, EPS, it1, it2, dd, tau=tau, d=d, ws=ws)
+        d_host.copy_(d, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = float(np.sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = work_units() * world * args.steps / (e2e_total / 1e3) / 1e9
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, ms) = dom
+    bound, amount, kind = algorithmic(name, nl)
+    avg_s = ms / max(nl, 1) / 1e3
+    if bound == "hbm":
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = amount / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        peak = FP32_PEAK_TFLOPS
+        achieved = amount / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    roof.update({"frac": achieved / peak, "traffic": None, "kernel": name,
+                 "avg_launch_us": avg_s * 1e6, "launches_per_step": nl // args.steps})
+
+    kernels = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": v[1] / args.steps}
+               for k, v in prof.items() if v[0]}
+
+    # ---- time to relative gap 1e-4 (rank 0 only; not part of the step) ----
+    gap = None
+    if rank == 0 and not args.no_gap_runs:
+        gap = {}
+        mpx = N * N / 1e6
+
+        def timed(fn):
+            barrier()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize(dev)
+            return (time.perf_counter() - t0) * 1e3, r
+
+        ms1, r1 = timed(lambda: B.tvs_step1(d0, DELTA, B.make_iter(20000, T, 1e-4, 10), tau=tau))
+        gap["step1_global"] = {"ms_per_mpixel": ms1 / mpx, "iters": r1.report["iters"],
+                               "rel_gap": r1.report["rel_gap"]}
+        ms2, r2 = timed(lambda: B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(50000, T, 1e-4, 10), d=d))
+        gap["step2_global"] = {"ms_per_mpixel": ms2 / mpx, "iters": r2.report["iters"],
+                               "rel_gap": r2.report["rel_gap"]}
+        ms3, r3 = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(5000, T, 1e-4, 2), out=d))
+        gap["step2_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms3 / mpx, "outer_iters": r3.report["iters"],
+                                            "rel_gap": r3.report["rel_gap"]}
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": "Gpixel-iter/s", "value": value, "unit": "Gpixel-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "tvstokes-1024x1024-textured-sigma0.1",
+                       "step": f"tvs_denoise: global TFS {ITERS1} updates + IRV1 Schwarz {M2}x{M1} "
+                               f"overlap {OVERLAP} k {K_INNER} x {OUTER} outer",
+                       "image": [N, N], "delta": DELTA, "alpha": ALPHA, "eps": EPS, "t": T,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": N * N * 4,
+                    "d2h_bytes_per_step": N * N * 4},
+            "time_to_rel_gap_1e-4": gap,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(d0_np)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return None
+    d0 = make_input(0)
+    for _ in range(args.warmup):
+        oracle_sample(d0, 2, 1)
+    tot_units, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        u, s, _ = oracle_sample(d0, 4, 1)
+        tot_units += u
+        tot_s += s
+    value = tot_units / tot_s / 1e9
+    return {"impl": "reference", "metric": "Gpixel-iter/s", "value": value, "unit": "Gpixel-iter/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tvstokes-1024x1024-textured-sigma0.1",
+                       "step": "FP64 oracle sample: 4 global TFS updates + 1 Schwarz outer iteration (4x4, s 8, k 10)"},
+            "cpu_baseline": {"value": value, "unit": "Gpixel-iter/s", "cores": 1, "kind": "oracle",
+                             "sample": "4 TFS updates + 1 Schwarz outer iteration per step, single-threaded"},
+            "e2e": {"value": value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

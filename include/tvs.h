@@ -1,0 +1,171 @@
+/*
+ * tvs.h -- C ABI of the GB300 TV-Stokes library (libtvs.so).
+ *
+ * The TV-Stokes model (Langer, Runft, Rahman, Tai, Wu, "Functional Analysis
+ * and Parallel Domain Decomposition for the TV-Stokes Model") denoises an
+ * image d0 in two steps:
+ *   step 1 (tangent field smoothing, TFS): the dual problem eq. tfsdualdis on
+ *          the extended grid, solved by Chambolle's semi-implicit iteration
+ *          (Algorithm 1) with the divergence-free projection P_K
+ *          (eq. formula:PKh, evaluated through the DCT, eq. form:DiscInvLapl);
+ *   step 2 (image reconstruction IRV1): the dual problem eq. ir1dualdis on the
+ *          image grid with the normal field xi of eq. defXi2:discrete.
+ * Both may also run under the overlapping Schwarz decomposition of
+ * Section 6 (Algorithm 2 with Algorithm 3, resp. Algorithms 4/5).
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are CUDA DEVICE pointers owned by the caller.  The
+ *    library never frees or keeps them after the call returns.
+ *  - Arrays are dense, row-major float32: element (i, j) of a plane with
+ *    `cols` columns is base[i * cols + j]; i = row = y, j = column = x.
+ *    Vector fields are consecutive planes.
+ *      image grid Omega        : n2 rows x n1 cols
+ *      extended grid ~Omega    : (n2+1) rows x (n1+1) cols
+ *      step-1 dual p           : 4 planes on ~Omega, order p1x, p1y, p2x, p2y
+ *      step-2 dual p           : 2 planes on Omega,  order px, py
+ *      tangent field tau       : 2 planes on ~Omega, order tau1, tau2
+ *  - Scratch memory comes from the caller: `ws` is a device buffer of at
+ *    least tvs_workspace_bytes(...) bytes, 256-byte aligned.  The calls do
+ *    not allocate device memory.
+ *  - All device work is enqueued on `stream`.  Calls that fill a tvs_report
+ *    synchronize `stream` before returning.
+ *  - Argument errors return TVS_ERR_ARG before any work is enqueued.  CUDA
+ *    errors return TVS_ERR_CUDA; tvs_last_error() names the failing call.
+ *  - The grid spacing is h = 1 (Section 5.2).
+ */
+#ifndef TVS_H
+#define TVS_H
+
+#include <stddef.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TVS_OK = 0,
+    TVS_ERR_ARG = 1,            /* invalid argument, nothing enqueued          */
+    TVS_ERR_WORKSPACE = 2,      /* ws NULL, misaligned or smaller than needed   */
+    TVS_ERR_CUDA = 3,           /* a CUDA runtime call failed                   */
+    TVS_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up           */
+    TVS_ERR_NOT_CONVERGED = 5,  /* max_iter reached before rel_gap_tol; outputs valid */
+    TVS_ERR_UNSUPPORTED = 6     /* size or option not supported by this build   */
+} tvs_status;
+
+typedef enum { TVS_F32 = 0, TVS_BF16 = 1, TVS_F16 = 2 } tvs_storage;
+
+/* Iteration control of one dual solve (Sections 4.2 and 5.2). */
+typedef struct {
+    int    max_iter;     /* dual updates (global) or outer iterations (Schwarz), >= 0 */
+    double t;            /* Chambolle step, 0 < t <= 1/8 (convergence theorem, Sec. 4.2) */
+    double rel_gap_tol;  /* stop once gap/E <= tol (checked every check_every); 0 = never */
+    int    check_every;  /* updates between gap checks; <= 0 means only at the end      */
+    int    storage;      /* tvs_storage of the dual fields (TVS_F32 in this build)      */
+} tvs_iter;
+
+/* Values at the returned dual iterate p (duality gap per Appendix A):
+ *   dual_D   = ||Lambda p - f||^2                     (eq. opt_dual_discrete)
+ *   primal_E = TV(u) + (beta/2)||u - g||^2, u recovered from p
+ *   gap      = sum_k sum_ij (|grad u_k| + grad u_k . p_k) >= 0
+ *   rel_gap  = gap / primal_E
+ *   div_res_max = max |div tau| (step 1; 0 for step 2)
+ *   max_p    = max over pixels and channels of |p_k| (<= 1 when feasible) */
+typedef struct {
+    int    iters;
+    double dual_D, primal_E, gap, rel_gap, div_res_max, max_p;
+} tvs_report;
+
+/* Overlapping Schwarz decomposition (Section 6.1): m2 x m1 subdomains whose
+ * cores split each axis evenly; neighbours share a strip of `overlap` pixels;
+ * k_inner Chambolle updates per subdomain and outer iteration; alpha_hat <= 0
+ * selects the colouring rule (1, 1/2 or 1/4). */
+typedef struct {
+    int    m2, m1;
+    int    overlap;
+    int    k_inner;
+    double alpha_hat;
+} tvs_decomp;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tvs_version(void);
+
+/* Human-readable text of a status code (static storage). */
+const char* tvs_status_string(tvs_status st);
+
+/* Text of the last CUDA error recorded on the calling thread ("" if none). */
+const char* tvs_last_error(void);
+
+/* Bytes of scratch needed by a call.
+ *   step = 1: tvs_step1 / tvs_schwarz(step=1); step = 2: tvs_step2 /
+ *   tvs_schwarz(step=2); step = 0: tvs_denoise (covers both); step = 3:
+ *   tvs_project.  dd = NULL means the global iteration.  Returns 0 for
+ *   invalid sizes. */
+size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage);
+
+/* Divergence-free projection P_K = I - grad Delta^dagger div on a grid of
+ * `rows` x `cols` points (eq. formula:PKh, Appendix B), with Delta^dagger by
+ * the 2-D DCT (eqs. form:DiscInvLapl, form:DiscInvLaplTild).
+ *   in   : 2 planes rows x cols (x-part, y-part); out: same layout; in == out allowed.
+ *   rows, cols >= 3.  ws: tvs_workspace_bytes(3, rows-1, cols-1, NULL, 0). */
+tvs_status tvs_project(const float* in, float* out, int rows, int cols,
+                       void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Step 1, TFS (Section 4.2, eq. tfsdualdis, Algorithm 1 with the projected
+ * data term f1 = P_K tau0 / delta).
+ *   d0   : n2 x n1 noisy image.            n2, n1 >= 2.   delta > 0.
+ *   tau  : out, 2 planes on ~Omega, tau = P_K tau0 - delta P_K vecdiv p.
+ *   p    : in/out warm start (4 planes on ~Omega) or NULL to start from 0.
+ *   rep  : filled at the returned p (may be NULL). */
+tvs_status tvs_step1(const float* d0, int n2, int n1, double delta, const tvs_iter* it,
+                     float* tau, float* p, void* ws, size_t ws_bytes,
+                     cudaStream_t stream, tvs_report* rep);
+
+/* Step 2, IRV1 (Section 4.2, eq. ir1dualdis): xi = tau_perp/|tau_perp|_eps
+ * from the first n2 rows and n1 columns of tau (eq. defXi2:discrete),
+ * f2 = alpha d0 - div xi, Chambolle's iteration, d = (f2 - div p)/alpha.
+ *   tau  : 2 planes on ~Omega (from tvs_step1).   alpha > 0, eps > 0.
+ *   d    : out, n2 x n1.   p: in/out (2 planes on Omega) or NULL. */
+tvs_status tvs_step2(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
+                     const tvs_iter* it, float* d, float* p, void* ws, size_t ws_bytes,
+                     cudaStream_t stream, tvs_report* rep);
+
+/* Both steps: d0 -> tau -> xi, f2 -> d.  Step 2 runs under the Schwarz
+ * decomposition dd2 when dd2 != NULL, else globally.  tau may be NULL (kept
+ * in ws).  rep[0] reports step 1, rep[1] step 2 (rep may be NULL). */
+tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alpha, double eps,
+                       const tvs_iter* it1, const tvs_iter* it2, const tvs_decomp* dd2,
+                       float* tau, float* d, void* ws, size_t ws_bytes,
+                       cudaStream_t stream, tvs_report* rep);
+
+/* Overlapping Schwarz iteration (Algorithm 2) of one step.
+ *   step = 2: inner Algorithm 3 for eq. ir1dualdis; `tau` and `eps` as in
+ *             tvs_step2, `weight` = alpha, `out` = d (n2 x n1), p 2 planes.
+ *   step = 1: inner Algorithm 5 for eq. tfsdualdis; `tau` unused, `weight` =
+ *             delta, `out` = tau (2 planes on ~Omega), p 4 planes.
+ *   outer->max_iter outer iterations; dd->k_inner inner updates each.
+ *   p: in/out or NULL (zero start; the per-subdomain warm starts q_m always
+ *   start at 0). */
+tvs_status tvs_schwarz(int step, const float* d0, const float* tau, int n2, int n1,
+                       double weight, double eps, const tvs_decomp* dd, const tvs_iter* outer,
+                       float* out, float* p, void* ws, size_t ws_bytes,
+                       cudaStream_t stream, tvs_report* rep);
+
+/* Kernel timing, for measurement.  tvs_profile_enable(1) clears the
+ * accumulators and starts bracketing every launch of the hot-path kernels
+ * with CUDA events on the launching stream; (0) stops.  tvs_profile_read()
+ * waits for the recorded events and writes one entry per kernel class
+ * (launch count, summed device milliseconds) into out[0..cap); it returns the
+ * number of entries written.  Not a numerical operation of the paper. */
+typedef struct {
+    char   name[32];
+    int    launches;
+    double ms;
+} tvs_kernel_time;
+int tvs_profile_enable(int on);
+int tvs_profile_read(tvs_kernel_time* out, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVS_H */

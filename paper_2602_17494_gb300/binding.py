@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libtvs (declarations in include/tvs.h).
+
+Argument marshalling only: torch tensors supply device pointers and the
+current CUDA stream; every step of the method runs in the library's kernels.
+Importing this module loads ``libtvs.so`` and raises if it is missing -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtvs.so")
+
+TVS_OK = 0
+TVS_ERR_NOT_CONVERGED = 5
+TVS_F32, TVS_BF16, TVS_F16 = 0, 1, 2
+
+
+class TvsIter(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("t", ctypes.c_double), ("rel_gap_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+class TvsReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("dual_D", ctypes.c_double), ("primal_E", ctypes.c_double),
+                ("gap", ctypes.c_double), ("rel_gap", ctypes.c_double), ("div_res_max", ctypes.c_double),
+                ("max_p", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TvsDecomp(ctypes.Structure):
+    _fields_ = [("m2", ctypes.c_int), ("m1", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("k_inner", ctypes.c_int), ("alpha_hat", ctypes.c_double)]
+
+
+class TvsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.tvs_status_string(status).decode()
+        extra = _lib.tvs_last_error().decode()
+        super().__init__(f"{where}: {msg} (status {status}){': ' + extra if extra else ''}")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtvs.so not built ({LIB_PATH}); run paper_2602_17494_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.tvs_version.restype = I
+    lib.tvs_status_string.restype = ctypes.c_char_p
+    lib.tvs_status_string.argtypes = [I]
+    lib.tvs_last_error.restype = ctypes.c_char_p
+    lib.tvs_workspace_bytes.restype = S
+    lib.tvs_workspace_bytes.argtypes = [I, I, I, ctypes.POINTER(TvsDecomp), I]
+    lib.tvs_project.restype = I
+    lib.tvs_project.argtypes = [P, P, I, I, P, S, P]
+    lib.tvs_step1.restype = I
+    lib.tvs_step1.argtypes = [P, I, I, D, ctypes.POINTER(TvsIter), P, P, P, S, P, ctypes.POINTER(TvsReport)]
+    lib.tvs_step2.restype = I
+    lib.tvs_step2.argtypes = [P, P, I, I, D, D, ctypes.POINTER(TvsIter), P, P, P, S, P,
+                              ctypes.POINTER(TvsReport)]
+    lib.tvs_denoise.restype = I
+    lib.tvs_denoise.argtypes = [P, I, I, D, D, D, ctypes.POINTER(TvsIter), ctypes.POINTER(TvsIter),
+                                ctypes.POINTER(TvsDecomp), P, P, P, S, P, ctypes.POINTER(TvsReport)]
+    lib.tvs_schwarz.restype = I
+    lib.tvs_schwarz.argtypes = [I, P, P, I, I, D, D, ctypes.POINTER(TvsDecomp), ctypes.POINTER(TvsIter),
+                                P, P, P, S, P, ctypes.POINTER(TvsReport)]
+    lib.tvs_profile_enable.restype = I
+    lib.tvs_profile_enable.argtypes = [I]
+    lib.tvs_profile_read.restype = I
+    lib.tvs_profile_read.argtypes = [ctypes.POINTER(TvsKernelTime), I]
+    return lib
+
+
+class TvsKernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+_lib = _load()
+
+# Every symbol that include/tvs.h declares.
+EXPORTED = ["tvs_denoise", "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
+            "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2", "tvs_version", "tvs_workspace_bytes"]
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("libtvs takes contiguous float32 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check(st: int, where: str, allow_not_converged: bool = True):
+    if st == TVS_OK or (allow_not_converged and st == TVS_ERR_NOT_CONVERGED):
+        return
+    raise TvsError(st, where)
+
+
+def make_iter(max_iter: int, t: float = 0.125, rel_gap_tol: float = 0.0, check_every: int = 0,
+              storage: int = TVS_F32) -> TvsIter:
+    return TvsIter(int(max_iter), float(t), float(rel_gap_tol), int(check_every), int(storage))
+
+
+def make_decomp(m2: int, m1: int, overlap: int, k_inner: int, alpha_hat: float = 0.0) -> TvsDecomp:
+    return TvsDecomp(int(m2), int(m1), int(overlap), int(k_inner), float(alpha_hat))
+
+
+def workspace_bytes(step: int, n2: int, n1: int, dd: TvsDecomp | None = None, storage: int = TVS_F32) -> int:
+    n = _lib.tvs_workspace_bytes(step, n2, n1, ctypes.byref(dd) if dd is not None else None, storage)
+    if n == 0:
+        raise ValueError(f"unsupported sizes for step {step}: {n2} x {n1}")
+    return int(n)
+
+
+def workspace(step: int, n2: int, n1: int, dd: TvsDecomp | None = None, device=None) -> torch.Tensor:
+    n = workspace_bytes(step, n2, n1, dd)
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class Result:
+    out: torch.Tensor
+    report: dict
+    status: int
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def tvs_project(tau: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """P_K of a 2-plane field of shape (2, rows, cols)."""
+    _, rows, cols = tau.shape
+    out = torch.empty_like(tau) if out is None else out
+    ws = workspace(3, rows - 1, cols - 1, device=tau.device) if ws is None else ws
+    st = _lib.tvs_project(_ptr(tau), _ptr(out), rows, cols, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                          _stream(tau.device))
+    _check(st, "tvs_project", False)
+    return out
+
+
+def tvs_step1(d0: torch.Tensor, delta: float, it: TvsIter, tau: torch.Tensor | None = None,
+              p: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> Result:
+    n2, n1 = d0.shape
+    tau = torch.empty((2, n2 + 1, n1 + 1), dtype=torch.float32, device=d0.device) if tau is None else tau
+    ws = workspace(1, n2, n1, device=d0.device) if ws is None else ws
+    rep = TvsReport()
+    st = _lib.tvs_step1(_ptr(d0), n2, n1, float(delta), ctypes.byref(it), _ptr(tau), _ptr(p),
+                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device), ctypes.byref(rep))
+    _check(st, "tvs_step1")
+    return Result(tau, rep.as_dict(), st)
+
+
+def tvs_step2(d0: torch.Tensor, tau: torch.Tensor, alpha: float, eps: float, it: TvsIter,
+              d: torch.Tensor | None = None, p: torch.Tensor | None = None,
+              ws: torch.Tensor | None = None) -> Result:
+    n2, n1 = d0.shape
+    d = torch.empty_like(d0) if d is None else d
+    ws = workspace(2, n2, n1, device=d0.device) if ws is None else ws
+    rep = TvsReport()
+    st = _lib.tvs_step2(_ptr(d0), _ptr(tau), n2, n1, float(alpha), float(eps), ctypes.byref(it), _ptr(d), _ptr(p),
+                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device), ctypes.byref(rep))
+    _check(st, "tvs_step2")
+    return Result(d, rep.as_dict(), st)
+
+
+def tvs_denoise(d0: torch.Tensor, delta: float, alpha: float, eps: float, it1: TvsIter, it2: TvsIter,
+                dd2: TvsDecomp | None = None, tau: torch.Tensor | None = None, d: torch.Tensor | None = None,
+                ws: torch.Tensor | None = None):
+    n2, n1 = d0.shape
+    d = torch.empty_like(d0) if d is None else d
+    ws = workspace(0, n2, n1, dd2, device=d0.device) if ws is None else ws
+    reps = (TvsReport * 2)()
+    st = _lib.tvs_denoise(_ptr(d0), n2, n1, float(delta), float(alpha), float(eps), ctypes.byref(it1),
+                          ctypes.byref(it2), ctypes.byref(dd2) if dd2 is not None else None, _ptr(tau), _ptr(d),
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device), reps)
+    _check(st, "tvs_denoise")
+    return d, tau, [reps[0].as_dict(), reps[1].as_dict()], st
+
+
+def tvs_schwarz(step: int, d0: torch.Tensor, tau: torch.Tensor | None, weight: float, eps: float,
+                dd: TvsDecomp, outer: TvsIter, out: torch.Tensor | None = None, p: torch.Tensor | None = None,
+                ws: torch.Tensor | None = None) -> Result:
+    n2, n1 = d0.shape
+    if out is None:
+        shape = (n2, n1) if step == 2 else (2, n2 + 1, n1 + 1)
+        out = torch.empty(shape, dtype=torch.float32, device=d0.device)
+    ws = workspace(step, n2, n1, dd, device=d0.device) if ws is None else ws
+    rep = TvsReport()
+    st = _lib.tvs_schwarz(step, _ptr(d0), _ptr(tau), n2, n1, float(weight), float(eps), ctypes.byref(dd),
+                          ctypes.byref(outer), _ptr(out), _ptr(p), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                          _stream(d0.device), ctypes.byref(rep))
+    _check(st, "tvs_schwarz")
+    return Result(out, rep.as_dict(), st)
+
+
+def tvs_profile_enable(on: bool = True) -> None:
+    _lib.tvs_profile_enable(1 if on else 0)
+
+
+def tvs_profile_read() -> dict:
+    """{kernel class: (launches, summed device ms)} since the last enable."""
+    buf = (TvsKernelTime * 16)()
+    n = _lib.tvs_profile_read(buf, 16)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].ms) for i in range(n)}

@@ -1,0 +1,479 @@
+// C ABI of libtvs (declared in include/tvs.h): argument checks, workspace
+// layout and the host-side iteration drivers.  All arithmetic of the method
+// runs in the kernels of dct.cu, tfs.cu, irv.cu and schwarz.cu.
+#include "tvs_internal.cuh"
+#include "launchers.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+
+namespace tvs {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* what, cudaError_t e) {
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    g_last_error = buf;
+}
+
+constexpr int kMaxSide = 8192;   // transform length <= 8193 keeps one FFT line in shared memory
+
+#define TVS_CUDA(call)                                       \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) {                             \
+            set_error(#call, e_);                            \
+            return TVS_ERR_CUDA;                             \
+        }                                                    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Workspace layouts
+// ---------------------------------------------------------------------------
+struct Step1Layout {
+    int R, C, P;
+    long plane;
+    PoissonPlans pp;
+    float *pa, *pb, *f1, *S;
+    RedBuf red;
+};
+
+static size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
+    L.R = n2 + 1;
+    L.C = n1 + 1;
+    L.P = round_up(L.C, kPitchAlign);
+    L.plane = (long)L.R * L.P;
+    carve_poisson(cv, L.pp, L.R, L.C);
+    L.pa = cv.take<float>(4 * (size_t)L.plane);
+    L.pb = cv.take<float>(4 * (size_t)L.plane);
+    L.f1 = cv.take<float>(2 * (size_t)L.plane);
+    L.S = cv.take<float>((size_t)L.plane);
+    carve_red(cv, L.red, tfs_blocks(L.R, L.C));
+    return cv.used();
+}
+
+struct Step2Layout {
+    int R, C, P;
+    long plane;
+    float *pa, *pb, *f2;
+    RedBuf red;
+};
+
+static size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L) {
+    L.R = n2;
+    L.C = n1;
+    L.P = round_up(L.C, kPitchAlign);
+    L.plane = (long)L.R * L.P;
+    L.pa = cv.take<float>(2 * (size_t)L.plane);
+    L.pb = cv.take<float>(2 * (size_t)L.plane);
+    L.f2 = cv.take<float>((size_t)L.plane);
+    carve_red(cv, L.red, irv1_blocks(L.R, L.C));
+    return cv.used();
+}
+
+struct ProjLayout {
+    int P;
+    long plane;
+    PoissonPlans pp;
+    float *u, *S;
+};
+
+static size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
+    L.P = round_up(cols, kPitchAlign);
+    L.plane = (long)rows * L.P;
+    carve_poisson(cv, L.pp, rows, cols);
+    L.u = cv.take<float>(2 * (size_t)L.plane);
+    L.S = cv.take<float>((size_t)L.plane);
+    return cv.used();
+}
+
+// ---------------------------------------------------------------------------
+// Checks
+// ---------------------------------------------------------------------------
+static bool side_ok(int n) { return n >= 2 && n <= kMaxSide; }
+
+static tvs_status check_iter(const tvs_iter* it) {
+    if (!it) return TVS_ERR_ARG;
+    if (it->max_iter < 0 || !(it->t > 0.0) || it->t > 0.125 || it->rel_gap_tol < 0.0) return TVS_ERR_ARG;
+    if (it->storage != TVS_F32) return TVS_ERR_UNSUPPORTED;
+    return TVS_OK;
+}
+
+static tvs_status check_ws(void* ws, size_t ws_bytes, size_t need) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need) return TVS_ERR_WORKSPACE;
+    return TVS_OK;
+}
+
+static tvs_status read_result(const RedBuf& rb, int nblocks, cudaStream_t s, double out[kRedSlots]) {
+    TVS_CUDA(finalize_red(rb, nblocks, s));
+    TVS_CUDA(cudaMemcpyAsync(out, rb.result, kRedSlots * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TVS_CUDA(cudaStreamSynchronize(s));
+    return TVS_OK;
+}
+
+static void report_tfs(const double r[kRedSlots], double delta, int iters, tvs_report* rep) {
+    const double tv = delta * r[0];
+    const double e = tv + 0.5 * delta * r[3];
+    const double gap = delta * (r[0] - r[1]);
+    rep->iters = iters;
+    rep->dual_D = r[2];
+    rep->primal_E = e;
+    rep->gap = gap;
+    rep->rel_gap = e > 0 ? gap / e : 0.0;
+    rep->div_res_max = delta * r[5];
+    rep->max_p = r[4];
+}
+
+static void report_irv1(const double r[kRedSlots], double alpha, int iters, tvs_report* rep) {
+    const double tv = r[0] / alpha;
+    const double e = tv + r[3] / (2.0 * alpha);
+    const double gap = (r[0] - r[1]) / alpha;
+    rep->iters = iters;
+    rep->dual_D = r[2];
+    rep->primal_E = e;
+    rep->gap = gap;
+    rep->rel_gap = e > 0 ? gap / e : 0.0;
+    rep->div_res_max = 0.0;
+    rep->max_p = r[4];
+}
+
+// Copy `planes` dense planes of rows x cols into / out of pitched storage.
+static cudaError_t to_pitched(float* dst, int dpitch, const float* src, int rows, int cols, int planes,
+                             cudaStream_t s) {
+    return cudaMemcpy2DAsync(dst, (size_t)dpitch * sizeof(float), src, (size_t)cols * sizeof(float),
+                             (size_t)cols * sizeof(float), (size_t)rows * planes, cudaMemcpyDeviceToDevice, s);
+}
+static cudaError_t from_pitched(float* dst, const float* src, int spitch, int rows, int cols, int planes,
+                               cudaStream_t s) {
+    return cudaMemcpy2DAsync(dst, (size_t)cols * sizeof(float), src, (size_t)spitch * sizeof(float),
+                             (size_t)cols * sizeof(float), (size_t)rows * planes, cudaMemcpyDeviceToDevice, s);
+}
+
+// ---------------------------------------------------------------------------
+// Drivers
+// ---------------------------------------------------------------------------
+// f1 = P_K tau0 / delta into L.f1 (uses L.S as scratch).
+static tvs_status tfs_setup(const Step1Layout& L, const float* d0, int n2, int n1, double delta, cudaStream_t s) {
+    TVS_CUDA(build_poisson(L.pp, s));
+    TVS_CUDA(launch_tau0(d0, n1, n2, n1, L.f1, L.P, L.plane, s));
+    RowSrcArgs sa{L.f1, L.plane, L.P};
+    TVS_CUDA(poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::DivField, sa, s));
+    TVS_CUDA(launch_grad_sub(L.f1, L.P, L.plane, L.S, L.P, L.R, L.C, (float)(1.0 / delta), L.f1, L.P, L.plane, s));
+    return TVS_OK;
+}
+
+static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1, double delta, const tvs_iter& it,
+                          float* tau, int tau_pitch, long tau_plane, float* p_user, cudaStream_t s,
+                          tvs_report* rep) {
+    tvs_status st = tfs_setup(L, d0, n2, n1, delta, s);
+    if (st != TVS_OK) return st;
+    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 4, s));
+    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 4 * (size_t)L.plane * sizeof(float), s));
+    float* cur = L.pa;
+    float* nxt = L.pb;
+    const int nb = tfs_blocks(L.R, L.C);
+    const bool check_loop = it.rel_gap_tol > 0.0 && it.check_every > 0;
+    const float t = (float)it.t, fd = (float)delta;
+    int n = 0;
+    bool converged = !check_loop;
+    double r[kRedSlots];
+    while (n < it.max_iter) {
+        const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
+        RowSrcArgs sp{cur, L.plane, L.P};
+        TVS_CUDA(poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::DivVecdiv, sp, s));
+        TVS_CUDA(launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
+                                   L.red.partial, s));
+        std::swap(cur, nxt);
+        ++n;
+        if (ck) {
+            st = read_result(L.red, nb, s, r);
+            if (st != TVS_OK) return st;
+            tvs_report tmp;
+            report_tfs(r, delta, n - 1, &tmp);
+            if (tmp.rel_gap <= it.rel_gap_tol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    RowSrcArgs sp{cur, L.plane, L.P};
+    TVS_CUDA(poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::DivVecdiv, sp, s));
+    TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau, tau_pitch,
+                               tau_plane, L.red.partial, s));
+    st = read_result(L.red, nb, s, r);
+    if (st != TVS_OK) return st;
+    tvs_report fin;
+    report_tfs(r, delta, n, &fin);
+    if (rep) *rep = fin;
+    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 4, s));
+    if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
+    return TVS_OK;
+}
+
+static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* tau, int n2, int n1, double alpha,
+                           double eps, const tvs_iter& it, float* d, float* p_user, cudaStream_t s,
+                           tvs_report* rep) {
+    const int R = n2 + 1, C = n1 + 1;
+    TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P, s));
+    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 2, s));
+    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 2 * (size_t)L.plane * sizeof(float), s));
+    float* cur = L.pa;
+    float* nxt = L.pb;
+    const int nb = irv1_blocks(L.R, L.C);
+    const bool check_loop = it.rel_gap_tol > 0.0 && it.check_every > 0;
+    const float t = (float)it.t, fa = (float)alpha;
+    int n = 0;
+    bool converged = !check_loop;
+    double r[kRedSlots];
+    tvs_status st;
+    while (n < it.max_iter) {
+        const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
+        TVS_CUDA(launch_irv1_update(cur, nxt, L.f2, L.R, L.C, L.P, L.plane, t, fa, ck, true, nullptr, 0,
+                                    L.red.partial, s));
+        std::swap(cur, nxt);
+        ++n;
+        if (ck) {
+            st = read_result(L.red, nb, s, r);
+            if (st != TVS_OK) return st;
+            tvs_report tmp;
+            report_irv1(r, alpha, n - 1, &tmp);
+            if (tmp.rel_gap <= it.rel_gap_tol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, d, n1,
+                                L.red.partial, s));
+    st = read_result(L.red, nb, s, r);
+    if (st != TVS_OK) return st;
+    tvs_report fin;
+    report_irv1(r, alpha, n, &fin);
+    if (rep) *rep = fin;
+    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 2, s));
+    if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
+    return TVS_OK;
+}
+
+static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1, double alpha,
+                               const tvs_iter& it, float* d, float* p_user, cudaStream_t s, tvs_report* rep) {
+    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 2, s));
+    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 2 * (size_t)L.plane * sizeof(float), s));
+    TVS_CUDA(schwarz2_reset(S2, s));
+    float* cur = L.pa;
+    float* nxt = L.pb;
+    const int nb = irv1_blocks(L.R, L.C);
+    const bool check_loop = it.rel_gap_tol > 0.0 && it.check_every > 0;
+    const float t = (float)it.t, fa = (float)alpha;
+    const int chunk = check_loop ? it.check_every : (it.max_iter > 0 ? it.max_iter : 1);
+    int n = 0;
+    bool converged = !check_loop;
+    double r[kRedSlots];
+    tvs_status st;
+    while (n < it.max_iter) {
+        const int step = chunk < it.max_iter - n ? chunk : it.max_iter - n;
+        TVS_CUDA(schwarz2_iterate(&cur, &nxt, L.f2, L.P, L.plane, n2, n1, S2, t, step, s));
+        n += step;
+        if (check_loop && n < it.max_iter) {
+            TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, nullptr, 0,
+                                        L.red.partial, s));
+            st = read_result(L.red, nb, s, r);
+            if (st != TVS_OK) return st;
+            tvs_report tmp;
+            report_irv1(r, alpha, n, &tmp);
+            if (tmp.rel_gap <= it.rel_gap_tol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, d, n1,
+                                L.red.partial, s));
+    st = read_result(L.red, nb, s, r);
+    if (st != TVS_OK) return st;
+    tvs_report fin;
+    report_irv1(r, alpha, n, &fin);
+    if (rep) *rep = fin;
+    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 2, s));
+    if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
+    return TVS_OK;
+}
+
+}  // namespace tvs
+
+using namespace tvs;
+
+extern "C" {
+
+int tvs_version(void) { return 100; }
+
+const char* tvs_status_string(tvs_status st) {
+    switch (st) {
+        case TVS_OK: return "ok";
+        case TVS_ERR_ARG: return "invalid argument";
+        case TVS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case TVS_ERR_CUDA: return "CUDA error";
+        case TVS_ERR_TIMEOUT: return "device-side wait timed out";
+        case TVS_ERR_NOT_CONVERGED: return "iteration limit reached before the gap tolerance";
+        case TVS_ERR_UNSUPPORTED: return "unsupported size or option";
+    }
+    return "unknown status";
+}
+
+const char* tvs_last_error(void) { return g_last_error.c_str(); }
+
+size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage) {
+    if (storage != TVS_F32) return 0;
+    Carver cv(nullptr);
+    if (step == 3) {
+        if (n2 < 2 || n1 < 2 || n2 + 1 > kMaxSide + 1 || n1 + 1 > kMaxSide + 1) return 0;
+        ProjLayout L;
+        return layout_project(cv, n2 + 1, n1 + 1, L);
+    }
+    if (!side_ok(n2) || !side_ok(n1)) return 0;
+    if (step == 1) {
+        if (dd) return 0;  // the localized step-1 Schwarz path is not in this build
+        Step1Layout L;
+        return layout_step1(cv, n2, n1, L);
+    }
+    if (step == 2) {
+        Step2Layout L;
+        size_t b = layout_step2(cv, n2, n1, L);
+        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L.P);
+        return b;
+    }
+    if (step == 0) {
+        Step1Layout L1;
+        layout_step1(cv, n2, n1, L1);
+        cv.take<float>(2 * (size_t)(n2 + 1) * (n1 + 1));
+        Step2Layout L2;
+        size_t b = layout_step2(cv, n2, n1, L2);
+        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L2.P);
+        return b;
+    }
+    return 0;
+}
+
+tvs_status tvs_project(const float* in, float* out, int rows, int cols, void* ws, size_t ws_bytes,
+                       cudaStream_t stream) {
+    if (!in || !out || rows < 3 || cols < 3 || rows > kMaxSide + 1 || cols > kMaxSide + 1) return TVS_ERR_ARG;
+    Carver cv0(nullptr);
+    ProjLayout L0;
+    tvs_status st = check_ws(ws, ws_bytes, layout_project(cv0, rows, cols, L0));
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    ProjLayout L;
+    layout_project(cv, rows, cols, L);
+    TVS_CUDA(build_poisson(L.pp, stream));
+    TVS_CUDA(to_pitched(L.u, L.P, in, rows, cols, 2, stream));
+    RowSrcArgs sa{L.u, L.plane, L.P};
+    TVS_CUDA(poisson_solve(L.S, rows, cols, L.P, L.pp, RowSource::DivField, sa, stream));
+    TVS_CUDA(launch_grad_sub(L.u, L.P, L.plane, L.S, L.P, rows, cols, 1.0f, out, cols, (long)rows * cols, stream));
+    return TVS_OK;
+}
+
+tvs_status tvs_step1(const float* d0, int n2, int n1, double delta, const tvs_iter* it, float* tau, float* p,
+                     void* ws, size_t ws_bytes, cudaStream_t stream, tvs_report* rep) {
+    if (!d0 || !tau || !side_ok(n2) || !side_ok(n1) || !(delta > 0.0)) return TVS_ERR_ARG;
+    tvs_status st = check_iter(it);
+    if (st != TVS_OK) return st;
+    Carver cv0(nullptr);
+    Step1Layout L;
+    st = check_ws(ws, ws_bytes, layout_step1(cv0, n2, n1, L));
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    layout_step1(cv, n2, n1, L);
+    return run_tfs(L, d0, n2, n1, delta, *it, tau, n1 + 1, (long)(n2 + 1) * (n1 + 1), p, stream, rep);
+}
+
+tvs_status tvs_step2(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
+                     const tvs_iter* it, float* d, float* p, void* ws, size_t ws_bytes, cudaStream_t stream,
+                     tvs_report* rep) {
+    if (!d0 || !tau || !d || !side_ok(n2) || !side_ok(n1) || !(alpha > 0.0) || !(eps > 0.0)) return TVS_ERR_ARG;
+    tvs_status st = check_iter(it);
+    if (st != TVS_OK) return st;
+    Carver cv0(nullptr);
+    Step2Layout L;
+    st = check_ws(ws, ws_bytes, layout_step2(cv0, n2, n1, L));
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    layout_step2(cv, n2, n1, L);
+    return run_irv1(L, d0, tau, n2, n1, alpha, eps, *it, d, p, stream, rep);
+}
+
+tvs_status tvs_schwarz(int step, const float* d0, const float* tau, int n2, int n1, double weight, double eps,
+                       const tvs_decomp* dd, const tvs_iter* outer, float* out, float* p, void* ws,
+                       size_t ws_bytes, cudaStream_t stream, tvs_report* rep) {
+    if (step == 1) return TVS_ERR_UNSUPPORTED;
+    if (step != 2 || !dd || !d0 || !tau || !out || !side_ok(n2) || !side_ok(n1) || !(weight > 0.0) ||
+        !(eps > 0.0))
+        return TVS_ERR_ARG;
+    tvs_status st = check_iter(outer);
+    if (st != TVS_OK) return st;
+    st = schwarz2_check(n2, n1, *dd);
+    if (st != TVS_OK) return st;
+    Carver cv0(nullptr);
+    Step2Layout L;
+    layout_step2(cv0, n2, n1, L);
+    st = check_ws(ws, ws_bytes, schwarz2_extend(cv0, n2, n1, *dd, L.P));
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    layout_step2(cv, n2, n1, L);
+    Schwarz2State S2;
+    schwarz2_carve(cv, n2, n1, *dd, L.P, S2);
+    const int R = n2 + 1, C = n1 + 1;
+    TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)weight, (float)eps, L.f2, L.P, stream));
+    return run_schwarz2(L, S2, n2, n1, weight, *outer, out, p, stream, rep);
+}
+
+tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alpha, double eps, const tvs_iter* it1,
+                       const tvs_iter* it2, const tvs_decomp* dd2, float* tau, float* d, void* ws, size_t ws_bytes,
+                       cudaStream_t stream, tvs_report* rep) {
+    if (!d0 || !d || !side_ok(n2) || !side_ok(n1) || !(delta > 0.0) || !(alpha > 0.0) || !(eps > 0.0))
+        return TVS_ERR_ARG;
+    tvs_status st = check_iter(it1);
+    if (st != TVS_OK) return st;
+    st = check_iter(it2);
+    if (st != TVS_OK) return st;
+    if (dd2) {
+        st = schwarz2_check(n2, n1, *dd2);
+        if (st != TVS_OK) return st;
+    }
+    const size_t need = tvs_workspace_bytes(0, n2, n1, dd2, TVS_F32);
+    st = check_ws(ws, ws_bytes, need);
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    Step1Layout L1;
+    layout_step1(cv, n2, n1, L1);
+    float* tau_ws = cv.take<float>(2 * (size_t)(n2 + 1) * (n1 + 1));
+    float* tau_use = tau ? tau : tau_ws;
+    Step2Layout L2;
+    layout_step2(cv, n2, n1, L2);
+    tvs_report r1{}, r2{};
+    tvs_status s1 = run_tfs(L1, d0, n2, n1, delta, *it1, tau_use, n1 + 1, (long)(n2 + 1) * (n1 + 1), nullptr,
+                            stream, &r1);
+    if (s1 != TVS_OK && s1 != TVS_ERR_NOT_CONVERGED) return s1;
+    tvs_status s2;
+    if (dd2) {
+        Schwarz2State S2;
+        schwarz2_carve(cv, n2, n1, *dd2, L2.P, S2);
+        const int R = n2 + 1, C = n1 + 1;
+        TVS_CUDA(launch_xi_f2(d0, n1, tau_use, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L2.f2, L2.P,
+                              stream));
+        s2 = run_schwarz2(L2, S2, n2, n1, alpha, *it2, d, nullptr, stream, &r2);
+    } else {
+        s2 = run_irv1(L2, d0, tau_use, n2, n1, alpha, eps, *it2, d, nullptr, stream, &r2);
+    }
+    if (rep) {
+        rep[0] = r1;
+        rep[1] = r2;
+    }
+    if (s2 != TVS_OK) return s2;
+    return s1;
+}
+
+}  // extern "C"

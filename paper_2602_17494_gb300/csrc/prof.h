@@ -1,0 +1,37 @@
+// Opt-in per-kernel-class timing with CUDA events (see prof.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/tvs.h"
+
+namespace tvs {
+
+enum ProfClass : int {
+    kProfRowsFwd = 0,
+    kProfCols = 1,
+    kProfRowsInv = 2,
+    kProfTfsUpdate = 3,
+    kProfIrv1Update = 4,
+    kProfSchwarzTile = 5,
+    kProfSchwarzCombine = 6,
+    kProfOther = 7,
+    kProfClasses = 8
+};
+
+// Records an event on `s` at construction and at destruction when profiling
+// is enabled; a no-op otherwise.
+class ProfScope {
+public:
+    ProfScope(ProfClass cls, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+private:
+    ProfClass cls_;
+    cudaStream_t s_;
+    cudaEvent_t a_;
+};
+
+}  // namespace tvs

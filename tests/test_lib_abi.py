@@ -1,0 +1,88 @@
+"""The C-ABI library builds, loads and exports every symbol include/tvs.h declares.
+
+Runs without a GPU: only host-side entry points and argument checks that
+return before any CUDA call are exercised.
+"""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="needs the CUDA toolkit to build libtvs")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_17494_gb300 import build
+    build.build()
+    from paper_2602_17494_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tvs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tvs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib.lib(), n), n
+    assert sorted(lib.EXPORTED) == names
+
+
+def test_version_and_strings(lib):
+    L = lib.lib()
+    assert L.tvs_version() >= 100
+    assert L.tvs_status_string(0) == b"ok"
+    assert b"argument" in L.tvs_status_string(1)
+
+
+def test_workspace_sizes(lib):
+    a = lib.workspace_bytes(1, 64, 64)
+    b = lib.workspace_bytes(1, 1024, 1024)
+    assert 0 < a < b
+    assert lib.workspace_bytes(2, 1024, 1024) < b
+    dd = lib.make_decomp(4, 4, 8, 10)
+    assert lib.workspace_bytes(2, 1024, 1024, dd) > lib.workspace_bytes(2, 1024, 1024)
+    assert lib.workspace_bytes(0, 1024, 1024, dd) > b
+    L = lib.lib()
+    assert L.tvs_workspace_bytes(1, 1, 64, None, 0) == 0          # too small
+    assert L.tvs_workspace_bytes(1, 8193, 64, None, 0) == 0       # too large
+    assert L.tvs_workspace_bytes(1, 64, 64, None, 1) == 0         # bf16 storage not in this build
+
+
+def test_bad_arguments_rejected_before_any_device_work(lib):
+    L = lib.lib()
+    it = lib.make_iter(10)
+    rep = lib.TvsReport()
+    fake = ctypes.c_void_p(0x1000)        # never dereferenced: checks fail first
+    # n2 < 2
+    assert L.tvs_step1(fake, 1, 8, 0.05, ctypes.byref(it), fake, None, fake, 1 << 30, None, ctypes.byref(rep)) == 1
+    # delta <= 0
+    assert L.tvs_step1(fake, 8, 8, 0.0, ctypes.byref(it), fake, None, fake, 1 << 30, None, ctypes.byref(rep)) == 1
+    # t > 1/8
+    bad = lib.make_iter(10, t=0.2)
+    assert L.tvs_step2(fake, fake, 8, 8, 10.0, 1e-3, ctypes.byref(bad), fake, None, fake, 1 << 30, None,
+                       ctypes.byref(rep)) == 1
+    # workspace missing / too small / misaligned
+    assert L.tvs_step2(fake, fake, 8, 8, 10.0, 1e-3, ctypes.byref(it), fake, None, None, 1 << 30, None,
+                       ctypes.byref(rep)) == 2
+    assert L.tvs_step2(fake, fake, 8, 8, 10.0, 1e-3, ctypes.byref(it), fake, None, fake, 16, None,
+                       ctypes.byref(rep)) == 2
+    assert L.tvs_step2(fake, fake, 8, 8, 10.0, 1e-3, ctypes.byref(it), fake, None, ctypes.c_void_p(0x1004),
+                       1 << 30, None, ctypes.byref(rep)) == 2
+    # Schwarz: cores narrower than the overlap
+    dd = lib.make_decomp(4, 4, 8, 5)
+    assert L.tvs_schwarz(2, fake, fake, 20, 20, 10.0, 1e-3, ctypes.byref(dd), ctypes.byref(it), fake, None, fake,
+                         1 << 30, None, ctypes.byref(rep)) == 1
+    # bf16 storage is not in this build
+    bf = lib.make_iter(10, storage=1)
+    assert L.tvs_step1(fake, 8, 8, 0.05, ctypes.byref(bf), fake, None, fake, 1 << 30, None, ctypes.byref(rep)) == 6
