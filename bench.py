@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gap-runs", action="store_true")
+    ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise"], default=None,
+                    help="run one API call of this step (profiling target) instead of the benchmark")
+    ap.add_argument("--n", type=int, default=N, help="image side for --case")
+    ap.add_argument("--iters", type=int, default=3, help="updates (or outer iterations) for --case")
+    ap.add_argument("--repeat", type=int, default=2, help="calls for --case")
     return ap.parse_args()
 
 
@@ -366,8 +371,39 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_case(args):
+    """One API call per repeat of a single step on an n x n scene (ncu target)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2602_17494_gb300 import binding as B
+    from synth import SceneSpec, noisy_scene
+    n = args.n
+    d0 = torch.from_numpy(noisy_scene(SceneSpec(n, n, 0, SIGMA, True))[1].astype(np.float32)).cuda()
+    tau = torch.zeros((2, n + 1, n + 1), dtype=torch.float32, device="cuda")
+    m = max(1, n // 256)
+    dd = B.make_decomp(m, m, OVERLAP if n // m >= 2 * OVERLAP else 4, K_INNER)
+    it = B.make_iter(args.iters, T)
+    t0 = time.perf_counter()
+    for _ in range(args.repeat):
+        if args.case == "step1":
+            r = B.tvs_step1(d0, DELTA, it, tau=tau)
+        elif args.case == "step2":
+            r = B.tvs_step2(d0, tau, ALPHA, EPS, it)
+        elif args.case == "schwarz2":
+            r = B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, it)
+        else:
+            r = B.tvs_denoise(d0, DELTA, ALPHA, EPS, it, it, dd, tau=tau)
+    torch.cuda.synchronize()
+    return {"case": args.case, "n": n, "iters": args.iters, "repeat": args.repeat,
+            "seconds": time.perf_counter() - t0}
+
+
 def main():
     args = parse()
+    if args.case:
+        print(json.dumps(run_case(args)))
+        return
     line = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if line is not None:
         print(json.dumps(line))

@@ -183,8 +183,7 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
     double r[kRedSlots];
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
-        RowSrcArgs sp{cur, L.plane, L.P};
-        TVS_CUDA(poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::DivVecdiv, sp, s));
+        TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
         TVS_CUDA(launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
                                    L.red.partial, s));
         std::swap(cur, nxt);
@@ -200,8 +199,7 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             }
         }
     }
-    RowSrcArgs sp{cur, L.plane, L.P};
-    TVS_CUDA(poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::DivVecdiv, sp, s));
+    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
     TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau, tau_pitch,
                                tau_plane, L.red.partial, s));
     st = read_result(L.red, nb, s, r);
@@ -303,6 +301,54 @@ static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, 
     return TVS_OK;
 }
 
+static tvs_status run_schwarz1(const Step1Layout& L, Schwarz1State& S1, const float* d0, int n2, int n1,
+                               double delta, const tvs_iter& it, float* tau, float* p_user, cudaStream_t s,
+                               tvs_report* rep) {
+    tvs_status st = tfs_setup(L, d0, n2, n1, delta, s);
+    if (st != TVS_OK) return st;
+    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 4, s));
+    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 4 * (size_t)L.plane * sizeof(float), s));
+    TVS_CUDA(schwarz1_reset(S1, n2, n1, s));
+    float* cur = L.pa;
+    float* nxt = L.pb;
+    const int nb = tfs_blocks(L.R, L.C);
+    const bool check_loop = it.rel_gap_tol > 0.0 && it.check_every > 0;
+    const float t = (float)it.t, fd = (float)delta;
+    const int chunk = check_loop ? it.check_every : (it.max_iter > 0 ? it.max_iter : 1);
+    int n = 0;
+    bool converged = !check_loop;
+    double r[kRedSlots];
+    while (n < it.max_iter) {
+        const int step = chunk < it.max_iter - n ? chunk : it.max_iter - n;
+        TVS_CUDA(schwarz1_iterate(&cur, &nxt, L.f1, L.S, L.P, n2, n1, L.pp, S1, t, step, s));
+        n += step;
+        if (check_loop && n < it.max_iter) {
+            TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+            TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, nullptr,
+                                       0, 0, L.red.partial, s));
+            st = read_result(L.red, nb, s, r);
+            if (st != TVS_OK) return st;
+            tvs_report tmp;
+            report_tfs(r, delta, n, &tmp);
+            if (tmp.rel_gap <= it.rel_gap_tol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+    TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau, n1 + 1,
+                               (long)(n2 + 1) * (n1 + 1), L.red.partial, s));
+    st = read_result(L.red, nb, s, r);
+    if (st != TVS_OK) return st;
+    tvs_report fin;
+    report_tfs(r, delta, n, &fin);
+    if (rep) *rep = fin;
+    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 4, s));
+    if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
+    return TVS_OK;
+}
+
 }  // namespace tvs
 
 using namespace tvs;
@@ -336,9 +382,13 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
     }
     if (!side_ok(n2) || !side_ok(n1)) return 0;
     if (step == 1) {
-        if (dd) return 0;  // the localized step-1 Schwarz path is not in this build
         Step1Layout L;
-        return layout_step1(cv, n2, n1, L);
+        size_t b = layout_step1(cv, n2, n1, L);
+        if (dd) {
+            if (schwarz1_check(n2, n1, *dd) != TVS_OK) return 0;
+            b = schwarz1_extend(cv, n2, n1, *dd, L.P);
+        }
+        return b;
     }
     if (step == 2) {
         Step2Layout L;
@@ -408,7 +458,21 @@ tvs_status tvs_step2(const float* d0, const float* tau, int n2, int n1, double a
 tvs_status tvs_schwarz(int step, const float* d0, const float* tau, int n2, int n1, double weight, double eps,
                        const tvs_decomp* dd, const tvs_iter* outer, float* out, float* p, void* ws,
                        size_t ws_bytes, cudaStream_t stream, tvs_report* rep) {
-    if (step == 1) return TVS_ERR_UNSUPPORTED;
+    if (step == 1) {
+        if (!dd || !d0 || !out || !side_ok(n2) || !side_ok(n1) || !(weight > 0.0)) return TVS_ERR_ARG;
+        tvs_status st = check_iter(outer);
+        if (st != TVS_OK) return st;
+        st = schwarz1_check(n2, n1, *dd);
+        if (st != TVS_OK) return st;
+        st = check_ws(ws, ws_bytes, tvs_workspace_bytes(1, n2, n1, dd, TVS_F32));
+        if (st != TVS_OK) return st;
+        Carver cv(ws);
+        Step1Layout L;
+        layout_step1(cv, n2, n1, L);
+        Schwarz1State S1;
+        schwarz1_carve(cv, n2, n1, *dd, L.P, S1);
+        return run_schwarz1(L, S1, d0, n2, n1, weight, *outer, out, p, stream, rep);
+    }
     if (step != 2 || !dd || !d0 || !tau || !out || !side_ok(n2) || !side_ok(n1) || !(weight > 0.0) ||
         !(eps > 0.0))
         return TVS_ERR_ARG;

@@ -81,46 +81,89 @@ __global__ void plan_tables_kernel(DctPlan pl) {
 // ---- shared-memory FFTs ------------------------------------------------------
 
 // Radix-2 decimation in frequency: natural order in, bit-reversed order out.
-// nfft arrays of length M at buf + g * stride.
+// nfft arrays of length M at buf + g * stride.  Two consecutive radix-2 stages
+// are done by one thread on four elements (same arithmetic as two separate
+// stages, half the passes over shared memory and half the barriers).
 __device__ __forceinline__ void fft_dif(float2* buf, int stride, int nfft, int M, int logM,
                                         const float2* __restrict__ tw) {
-    const int halfM = M >> 1;
-    const int nb = nfft * halfM;
-    for (int s = 0; s < logM; ++s) {
-        const int lh = logM - 1 - s;
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int g = b >> (logM - 1);
-            const int r = b & (halfM - 1);
-            const int pos = r & (half - 1);
-            const int i = ((r >> lh) << (lh + 1)) + pos;
-            float2* x = buf + (size_t)g * stride;
-            const float2 u = x[i], v = x[i + half];
-            x[i] = c_add(u, v);
-            x[i + half] = c_mul(c_sub(u, v), __ldg(&tw[pos << s]));
+    int s = 0;
+    for (; s + 1 < logM; s += 2) {
+        const int lh = logM - 1 - s;          // log2 of the stage-s half length h
+        const int h = 1 << lh, q = h >> 1;
+        const int per = M >> 2;               // radix-4 butterflies per array
+        for (int b = threadIdx.x; b < nfft * per; b += blockDim.x) {
+            const int g = b / per;
+            const int r = b - g * per;
+            const int grp = r >> (lh - 1);    // r / q
+            const int pos = r & (q - 1);
+            float2* x = buf + (size_t)g * stride + grp * 2 * h + pos;
+            const float2 a = x[0], bb = x[q], c = x[h], d = x[h + q];
+            const float2 a1 = c_add(a, c);
+            const float2 c1 = c_mul(c_sub(a, c), __ldg(&tw[pos << s]));
+            const float2 b1 = c_add(bb, d);
+            const float2 d1 = c_mul(c_sub(bb, d), __ldg(&tw[(pos + q) << s]));
+            const float2 w2 = __ldg(&tw[pos << (s + 1)]);
+            x[0] = c_add(a1, b1);
+            x[q] = c_mul(c_sub(a1, b1), w2);
+            x[h] = c_add(c1, d1);
+            x[h + q] = c_mul(c_sub(c1, d1), w2);
+        }
+        __syncthreads();
+    }
+    if (s < logM) {                           // last stage (h = 1) when logM is odd
+        const int halfM = M >> 1;
+        for (int b = threadIdx.x; b < nfft * halfM; b += blockDim.x) {
+            const int g = b / halfM;
+            const int r = b - g * halfM;
+            float2* x = buf + (size_t)g * stride + 2 * r;
+            const float2 u = x[0], v = x[1];
+            x[0] = c_add(u, v);
+            x[1] = c_sub(u, v);
         }
         __syncthreads();
     }
 }
 
 // Radix-2 decimation in time with conjugate twiddles (unnormalised inverse):
-// bit-reversed order in, natural order out.
+// bit-reversed order in, natural order out; stages fused in pairs as above.
 __device__ __forceinline__ void ifft_dit(float2* buf, int stride, int nfft, int M, int logM,
                                          const float2* __restrict__ tw) {
-    const int halfM = M >> 1;
-    const int nb = nfft * halfM;
-    for (int s = 0; s < logM; ++s) {
-        const int half = 1 << s;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int g = b >> (logM - 1);
-            const int r = b & (halfM - 1);
-            const int pos = r & (half - 1);
-            const int i = ((r >> s) << (s + 1)) + pos;
-            float2* x = buf + (size_t)g * stride;
-            const float2 u = x[i];
-            const float2 t = c_mulconj(x[i + half], __ldg(&tw[pos << (logM - 1 - s)]));
-            x[i] = c_add(u, t);
-            x[i + half] = c_sub(u, t);
+    int s = 0;
+    if (logM & 1) {                           // first stage (h = 1) when logM is odd
+        const int halfM = M >> 1;
+        for (int b = threadIdx.x; b < nfft * halfM; b += blockDim.x) {
+            const int g = b / halfM;
+            const int r = b - g * halfM;
+            float2* x = buf + (size_t)g * stride + 2 * r;
+            const float2 u = x[0], v = x[1];
+            x[0] = c_add(u, v);
+            x[1] = c_sub(u, v);
+        }
+        __syncthreads();
+        s = 1;
+    }
+    for (; s + 1 < logM; s += 2) {
+        const int h = 1 << s;                 // stage-s half length; stage s+1 uses 2h
+        const int per = M >> 2;
+        for (int b = threadIdx.x; b < nfft * per; b += blockDim.x) {
+            const int g = b / per;
+            const int r = b - g * per;
+            const int grp = r >> s;           // r / h
+            const int pos = r & (h - 1);
+            float2* x = buf + (size_t)g * stride + grp * 4 * h + pos;
+            const float2 w1 = __ldg(&tw[pos << (logM - 1 - s)]);
+            const float2 a = x[0];
+            const float2 tb = c_mulconj(x[h], w1);
+            const float2 c = x[2 * h];
+            const float2 td = c_mulconj(x[3 * h], w1);
+            const float2 a1 = c_add(a, tb), b1 = c_sub(a, tb);
+            const float2 c1 = c_add(c, td), d1 = c_sub(c, td);
+            const float2 tc = c_mulconj(c1, __ldg(&tw[pos << (logM - 2 - s)]));
+            const float2 tdd = c_mulconj(d1, __ldg(&tw[(pos + h) << (logM - 2 - s)]));
+            x[0] = c_add(a1, tc);
+            x[2 * h] = c_sub(a1, tc);
+            x[h] = c_add(b1, tdd);
+            x[3 * h] = c_sub(b1, tdd);
         }
         __syncthreads();
     }
@@ -289,23 +332,50 @@ __device__ __forceinline__ float row_source(const RowSrcArgs& sa, int r, int c, 
 // --------------------------------------------------------------------------
 // Kernels
 // --------------------------------------------------------------------------
+// Batch mode (Schwarz step 1): blockIdx.y selects one of several arrays spaced
+// `bstride` floats apart; `ranges[b]` = (first row, end row) restricts the
+// transform to the rows a subdomain touches.  ranges == nullptr: all rows.
+// With `packed`, array b stores only its rows: row r lives at storage row
+// r - ranges[b].x.
+struct BatchArgs {
+    const int2* ranges;
+    long bstride;
+    int packed;
+};
+
+__device__ __forceinline__ int2 batch_rows(const BatchArgs& ba, int rows) {
+    return ba.ranges ? ba.ranges[blockIdx.y] : make_int2(0, rows);
+}
+__device__ __forceinline__ size_t row_off(const BatchArgs& ba, int2 rr, int r, int pitch) {
+    return (size_t)(ba.packed ? r - rr.x : r) * pitch;
+}
+
 template <RowSource SRC>
 __global__ void __launch_bounds__(kFftThreads)
 dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, DctPlan pl, RowSrcArgs sa,
-                    int G) {
+                    int G, BatchArgs ba) {
     extern __shared__ float2 sm[];
     const int L = cols, M = pl.M, stride = M + 4;
     float2* buf = sm;
     float2* peel = sm + (size_t)G * stride;
-    const int npairs = (rows + 1) >> 1;
+    const int2 rr = batch_rows(ba, rows);
+    out += (size_t)blockIdx.y * ba.bstride;
+    sa.a += (size_t)blockIdx.y * ba.bstride;
+    const int npairs = (rr.y - rr.x + 1) >> 1;
     for (int base = blockIdx.x * G; base < npairs; base += gridDim.x * G) {
         const int gc = min(G, npairs - base);
         for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
             const int g = b / L;
             const int j = b - g * L;
-            const int r0 = 2 * (base + g), r1 = r0 + 1;
-            const float x0 = row_source<SRC>(sa, r0, j, rows, cols);
-            const float x1 = (r1 < rows) ? row_source<SRC>(sa, r1, j, rows, cols) : 0.f;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+            float x0, x1;
+            if (SRC == RowSource::Plain) {
+                x0 = __ldg(&sa.a[row_off(ba, rr, r0, sa.pitch) + j]);
+                x1 = (r1 < rr.y) ? __ldg(&sa.a[row_off(ba, rr, r1, sa.pitch) + j]) : 0.f;
+            } else {
+                x0 = row_source<SRC>(sa, r0, j, rows, cols);
+                x1 = (r1 < rr.y) ? row_source<SRC>(sa, r1, j, rows, cols) : 0.f;
+            }
             stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(j, L), L, make_float2(x0, x1), pl);
         }
         zero_tail(buf, stride, gc, L, M);
@@ -314,34 +384,36 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, DctP
         for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
             const int g = b / L;
             const int k = b - g * L;
-            const int r0 = 2 * (base + g), r1 = r0 + 1;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
             const float2 X = unpack_dct2(buf + (size_t)g * stride, k, L, pl);
-            out[(size_t)r0 * pitch + k] = X.x;
-            if (r1 < rows) out[(size_t)r1 * pitch + k] = X.y;
+            out[row_off(ba, rr, r0, pitch) + k] = X.x;
+            if (r1 < rr.y) out[row_off(ba, rr, r1, pitch) + k] = X.y;
         }
         __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(kFftThreads)
-dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctPlan pl, int G) {
+dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctPlan pl, int G, BatchArgs ba) {
     extern __shared__ float2 sm[];
     const int L = cols, M = pl.M, stride = M + 4;
     float2* buf = sm;
     float2* peel = sm + (size_t)G * stride;
-    const int npairs = (rows + 1) >> 1;
+    const int2 rr = batch_rows(ba, rows);
+    S += (size_t)blockIdx.y * ba.bstride;
+    const int npairs = (rr.y - rr.x + 1) >> 1;
     const float invL = 1.0f / (float)L;
     for (int base = blockIdx.x * G; base < npairs; base += gridDim.x * G) {
         const int gc = min(G, npairs - base);
         for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
             const int g = b / L;
             const int k = b - g * L;
-            const int r0 = 2 * (base + g), r1 = r0 + 1;
-            const float* a0 = S + (size_t)r0 * pitch;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+            const float* a0 = S + row_off(ba, rr, r0, pitch);
             const float x1k = a0[k], x1m = k ? a0[L - k] : 0.f;
             float x2k = 0.f, x2m = 0.f;
-            if (r1 < rows) {
-                const float* a1 = S + (size_t)r1 * pitch;
+            if (r1 < rr.y) {
+                const float* a1 = S + row_off(ba, rr, r1, pitch);
                 x2k = a1[k];
                 x2m = k ? a1[L - k] : 0.f;
             }
@@ -353,10 +425,10 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctPla
         for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
             const int g = b / L;
             const int j = b - g * L;
-            const int r0 = 2 * (base + g), r1 = r0 + 1;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
             const float2 Y = buf[(size_t)g * stride + mk_perm(j, L)];
-            S[(size_t)r0 * pitch + j] = Y.x * invL;
-            if (r1 < rows) S[(size_t)r1 * pitch + j] = -Y.y * invL;
+            S[row_off(ba, rr, r0, pitch) + j] = Y.x * invL;
+            if (r1 < rr.y) S[row_off(ba, rr, r1, pitch) + j] = -Y.y * invL;
         }
         __syncthreads();
     }
@@ -372,8 +444,10 @@ __device__ __forceinline__ float lap_symbol(int ky, int kx, int R, int C) {
 }
 
 __global__ void __launch_bounds__(kFftThreads)
-dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctPlan pl, int G) {
+dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctPlan pl, int G, BatchArgs ba) {
     extern __shared__ float2 sm[];
+    const int2 rr = batch_rows(ba, rows);       // rows outside rr are read as zero and not written
+    S += (size_t)blockIdx.y * ba.bstride;
     const int L = rows, M = pl.M, stride = M + 4;
     float2* buf = sm;
     float2* ybuf = sm + (size_t)G * stride;       // G x L staged spectra
@@ -387,9 +461,10 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctP
             const int r = b / gc;
             const int g = b - r * gc;
             const int c0 = 2 * (base + g);
-            const float* a = S + (size_t)r * pitch + c0;
-            const float x0 = a[0];
-            const float x1 = (c0 + 1 < cols) ? a[1] : 0.f;
+            const bool in = r >= rr.x && r < rr.y;
+            const float* a = in ? S + row_off(ba, rr, r, pitch) + c0 : S;
+            const float x0 = in ? a[0] : 0.f;
+            const float x1 = (in && c0 + 1 < cols) ? a[1] : 0.f;
             stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(r, L), L, make_float2(x0, x1), pl);
         }
         zero_tail(buf, stride, gc, L, M);
@@ -418,8 +493,9 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, DctP
             const int r = b / gc;
             const int g = b - r * gc;
             const int c0 = 2 * (base + g);
+            if (r < rr.x || r >= rr.y) continue;
             const float2 Y = buf[(size_t)g * stride + mk_perm(r, L)];
-            float* a = S + (size_t)r * pitch + c0;
+            float* a = S + row_off(ba, rr, r, pitch) + c0;
             a[0] = Y.x * invL;
             if (c0 + 1 < cols) a[1] = -Y.y * invL;
         }
@@ -449,49 +525,74 @@ int blocks_for(int units, int G) {
 }
 }  // namespace
 
-cudaError_t poisson_solve(float* S, int rows, int cols, int pitch, const PoissonPlans& pp,
-                          RowSource src, const RowSrcArgs& sa, cudaStream_t s) {
+// Lines per CTA: one pair (the kernels are latency-bound, so resident warps
+// matter more than batching); threads: one radix-4 butterfly per thread and pass.
+int pick_batch(int units, size_t per_line) {
+    (void)units;
+    (void)per_line;
+    return 1;
+}
+int fft_threads(int M) {
+    int t = M / 4;
+    if (t < 128) t = 128;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const PoissonPlans& pp, RowSource src,
+                                  const RowSrcArgs& sa, int nbatch, const int2* ranges, long bstride, int maxrows,
+                                  int packed, cudaStream_t s) {
     std::call_once(g_smem_once, set_all_smem_attrs);
-    // rows transforms: line length cols
+    const BatchArgs ba{ranges, bstride, packed};
+    const int rpairs = (maxrows + 1) / 2, cpairs = (cols + 1) / 2;
+    const int units_r = rpairs * nbatch, units_c = cpairs * nbatch;
     {
         const size_t per = (size_t)(pp.row.M + 4 + 1) * sizeof(float2);
-        const int npairs = (rows + 1) / 2;
-        int G = (int)(kSmemBudget / per);
-        G = G < 1 ? 1 : (G > npairs ? npairs : G);
+        const int G = pick_batch(units_r, per);
         const size_t smem = (size_t)G * per;
-        const int nb = blocks_for(npairs, G);
+        const dim3 grid(blocks_for(rpairs, G), nbatch);
+        const int nt = fft_threads(pp.row.M);
         ProfScope ps(kProfRowsFwd, s);
         switch (src) {
             case RowSource::Plain:
-                dct_rows_fwd_kernel<RowSource::Plain><<<nb, kFftThreads, smem, s>>>(S, rows, cols, pitch, pp.row, sa, G);
+                dct_rows_fwd_kernel<RowSource::Plain><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pp.row, sa, G, ba);
                 break;
             case RowSource::DivField:
-                dct_rows_fwd_kernel<RowSource::DivField><<<nb, kFftThreads, smem, s>>>(S, rows, cols, pitch, pp.row, sa, G);
+                dct_rows_fwd_kernel<RowSource::DivField><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pp.row, sa, G, ba);
                 break;
             case RowSource::DivVecdiv:
-                dct_rows_fwd_kernel<RowSource::DivVecdiv><<<nb, kFftThreads, smem, s>>>(S, rows, cols, pitch, pp.row, sa, G);
+                dct_rows_fwd_kernel<RowSource::DivVecdiv><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pp.row, sa, G, ba);
                 break;
         }
     }
     {
         const size_t per = (size_t)(pp.col.M + 4 + rows + 1) * sizeof(float2);
-        const int npairs = (cols + 1) / 2;
-        int G = (int)(kSmemBudget / per);
-        G = G < 1 ? 1 : (G > npairs ? npairs : G);
+        const int G = pick_batch(units_c, per);
         const size_t smem = (size_t)G * per;
         ProfScope ps(kProfCols, s);
-        dct_cols_solve_kernel<<<blocks_for(npairs, G), kFftThreads, smem, s>>>(S, rows, cols, pitch, pp.col, G);
+        dct_cols_solve_kernel<<<dim3(blocks_for(cpairs, G), nbatch), fft_threads(pp.col.M), smem, s>>>(
+            S, rows, cols, pitch, pp.col, G, ba);
     }
     {
         const size_t per = (size_t)(pp.row.M + 4 + 1) * sizeof(float2);
-        const int npairs = (rows + 1) / 2;
-        int G = (int)(kSmemBudget / per);
-        G = G < 1 ? 1 : (G > npairs ? npairs : G);
+        const int G = pick_batch(units_r, per);
         const size_t smem = (size_t)G * per;
         ProfScope ps(kProfRowsInv, s);
-        dct_rows_inv_kernel<<<blocks_for(npairs, G), kFftThreads, smem, s>>>(S, rows, cols, pitch, pp.row, G);
+        dct_rows_inv_kernel<<<dim3(blocks_for(rpairs, G), nbatch), fft_threads(pp.row.M), smem, s>>>(
+            S, rows, cols, pitch, pp.row, G, ba);
     }
     return cudaGetLastError();
+}
+
+cudaError_t poisson_solve(float* S, int rows, int cols, int pitch, const PoissonPlans& pp,
+                          RowSource src, const RowSrcArgs& sa, cudaStream_t s) {
+    return poisson_launch(S, rows, cols, pitch, pp, src, sa, 1, nullptr, 0, rows, 0, s);
+}
+
+cudaError_t poisson_solve_batched(float* S, int nbatch, long bstride, const int2* ranges, int maxrows, int rows,
+                                  int cols, int pitch, const PoissonPlans& pp, cudaStream_t s) {
+    RowSrcArgs sa{S, 0, pitch};
+    return poisson_launch(S, rows, cols, pitch, pp, RowSource::Plain, sa, nbatch, ranges, bstride, maxrows, 1, s);
 }
 
 }  // namespace tvs

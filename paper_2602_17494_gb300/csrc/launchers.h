@@ -14,6 +14,15 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
                               int pitch, long plane, float t, float delta, bool check, bool write_p, float* tau_out,
                               int tau_pitch, long tau_plane, double* partial, cudaStream_t s);
 int tfs_blocks(int R, int C);
+cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, cudaStream_t s);
+// S <- Delta^dagger div(vecdiv p) on the extended grid (phi of the TFS iteration)
+inline cudaError_t tfs_phi(const float* p, float* S, int R, int C, int pitch, long plane, const PoissonPlans& pp,
+                           cudaStream_t s) {
+    cudaError_t e = launch_div_vecdiv(p, R, C, pitch, plane, S, s);
+    if (e != cudaSuccess) return e;
+    RowSrcArgs sa{S, 0, pitch};
+    return poisson_solve(S, R, C, pitch, pp, RowSource::Plain, sa, s);
+}
 
 // irv.cu
 cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long tplane, int tpitch, int R, int C,
@@ -41,5 +50,22 @@ cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s);
 // *cur and *nxt after each iteration.
 cudaError_t schwarz2_iterate(float** cur, float** nxt, const float* f2, int pitch, long plane, int n2, int n1,
                              const Schwarz2State& st, float t, int n_outer, cudaStream_t s);
+
+// schwarz1.cu -- Algorithm 2 with the localized Algorithm 5 for TFS on the extended grid
+struct Schwarz1State {
+    int m2, m1, s, k, ntiles;
+    double alpha_hat;
+    int hbox, wpad, pitch;   // per-subdomain storage covers A = (tilde Omega_{m,+})_+
+    float *V, *U, *W;        // inner dual v (4 planes), u = vecdiv v (2), omega (2), per subdomain
+    float* S;                // packed Poisson rows of A, per subdomain (rows of A x pitch)
+    float* Q;                // P_K vecdiv p^n on the whole grid (2 planes)
+    int2* ranges;            // rows of A per subdomain (device)
+};
+tvs_status schwarz1_check(int n2, int n1, const tvs_decomp& dd);
+size_t schwarz1_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch);
+void schwarz1_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, Schwarz1State& st);
+cudaError_t schwarz1_reset(const Schwarz1State& st, int n2, int n1, cudaStream_t s);
+cudaError_t schwarz1_iterate(float** cur, float** nxt, const float* f1, float* S_glob, int pitch, int n2, int n1,
+                             const PoissonPlans& pp, const Schwarz1State& st, float t, int n_outer, cudaStream_t s);
 
 }  // namespace tvs

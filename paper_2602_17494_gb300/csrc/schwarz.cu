@@ -15,6 +15,7 @@
 // neighbours share a strip of s pixels [b - ceil(s/2), b + floor(s/2)) around
 // their core boundary b with linear weights theta (pixel-centre values); the
 // 2-D weight is the product of the 1-D weights.
+#include "decomp.cuh"
 #include "launchers.h"
 #include "prof.h"
 
@@ -30,35 +31,6 @@ namespace tvs {
 constexpr int kSchwarzThreads = 512;
 constexpr size_t kSchwarzSmemMax = 200 * 1024;
 
-struct Axis {
-    int N, M, s;
-    __host__ __device__ __forceinline__ int core(int k) const { return (int)(((long long)k * N) / M); }
-    __host__ __device__ __forceinline__ int start(int k) const { return k == 0 ? 0 : core(k) - (s + 1) / 2; }
-    __host__ __device__ __forceinline__ int end(int k) const { return k == M - 1 ? N : core(k + 1) + s / 2; }
-    // theta of part k at pixel x (x inside [start(k), end(k)))
-    __host__ __device__ __forceinline__ float theta(int k, int x) const {
-        const int lo = (s + 1) / 2;
-        if (s > 0 && k > 0) {
-            const int a = core(k) - lo;
-            if (x < a + s) return ((float)(x - a) + 0.5f) / (float)s;
-        }
-        if (s > 0 && k < M - 1) {
-            const int a = core(k + 1) - lo;
-            if (x >= a) return ((float)(a + s - x) - 0.5f) / (float)s;
-        }
-        return 1.0f;
-    }
-    __host__ __device__ __forceinline__ float theta_or0(int k, int x) const {
-        return (x >= start(k) && x < end(k)) ? theta(k, x) : 0.0f;
-    }
-    __host__ __device__ __forceinline__ int core_of(int x) const {
-        int k = (int)(((long long)x * M) / N);
-        while (k + 1 < M && core(k + 1) <= x) ++k;
-        while (k > 0 && core(k) > x) --k;
-        return k;
-    }
-};
-
 struct TileArgs {
     const float* p;   // p^n, 2 planes
     const float* f2;
@@ -71,10 +43,15 @@ struct TileArgs {
     float t;
 };
 
-// Shared memory of one CTA: v_x, v_y (band x wpad), g, z ((band+1) x wpad),
-// theta_x (wpad), theta_y (band + 1).
+// Shared memory of one CTA (floats):
+//   v_x, v_y : (band + 2) x wpad each -- row 0 is the halo row above, rows
+//              1..nown the CTA's own rows, row nown+1 the halo row below
+//   g, z     : (band + 1) x wpad each
+//   theta_x  : wpad;  theta_y : band + 1
+//   outbox   : 2 parities x 3 rows x wpad -- the first row of v_x and v_y and
+//              the last row of v_y, published for the neighbouring CTAs
 __host__ __device__ __forceinline__ size_t tile_smem_floats(int band, int wpad) {
-    return (size_t)2 * band * wpad + (size_t)2 * (band + 1) * wpad + wpad + band + 1;
+    return (size_t)2 * (band + 2) * wpad + (size_t)2 * (band + 1) * wpad + wpad + band + 1 + (size_t)6 * wpad;
 }
 
 __global__ void __launch_bounds__(kSchwarzThreads)
@@ -82,12 +59,13 @@ schwarz2_tile_kernel(TileArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float sm[];
     const int WP = a.wpad, B = a.band;
-    float* vx = sm;
-    float* vy = vx + (size_t)B * WP;
-    float* g = vy + (size_t)B * WP;
+    float* vx = sm;                              // row r of the band at vx + (r + 1) * WP
+    float* vy = vx + (size_t)(B + 2) * WP;
+    float* g = vy + (size_t)(B + 2) * WP;
     float* z = g + (size_t)(B + 1) * WP;
     float* thx = z + (size_t)(B + 1) * WP;
     float* thy = thx + WP;
+    float* outbox = thy + (B + 1);               // [parity][3][WP]
 
     const int N2 = a.ay.N, N1 = a.ax.N;
     const int sub = blockIdx.y;
@@ -96,9 +74,12 @@ schwarz2_tile_kernel(TileArgs a) {
     const int x0 = a.ax.start(mx), x1 = a.ax.end(mx);
     const int w = x1 - x0;
     const int rank = (int)cl.block_rank();
+    const int ncl = (int)cl.num_blocks();
     const int r_lo = y0 + rank * B;
     const int r_hi = min(y1, r_lo + B);
     const int nown = max(0, r_hi - r_lo);
+    const bool has_above = rank > 0 && nown > 0;
+    const bool has_below = rank + 1 < ncl && r_hi < y1;   // the next band owns row r_hi
     // z rows: own rows plus the next row when it exists in Gamma_{m,+}
     const int zrows = nown + ((nown > 0 && r_hi < N2) ? 1 : 0);
     const int zcols = w + (x1 < N1 ? 1 : 0);
@@ -107,21 +88,27 @@ schwarz2_tile_kernel(TileArgs a) {
     float* qx = a.q + (size_t)sub * 2 * a.hmax * WP;
     float* qy = qx + (size_t)a.hmax * WP;
     const float t = a.t;
+    const int nt = blockDim.x;
 
     // ---- set-up: weights, warm start, frozen data g_m --------------------
-    for (int c = threadIdx.x; c < WP; c += blockDim.x) thx[c] = (c < w) ? a.ax.theta(mx, x0 + c) : 0.0f;
-    for (int r = threadIdx.x; r <= B; r += blockDim.x) {
+    for (int c = threadIdx.x; c < WP; c += nt) thx[c] = (c < w) ? a.ax.theta(mx, x0 + c) : 0.0f;
+    for (int r = threadIdx.x; r <= B; r += nt) {
         const int i = r_lo + r;
-        thy[r] = (r <= nown && i < y1) ? a.ay.theta(my, i) : 0.0f;
+        thy[r] = (r < nown) ? a.ay.theta(my, i) : 0.0f;
     }
-    for (int idx = threadIdx.x; idx < nown * w; idx += blockDim.x) {
-        const int r = idx / w, c = idx - r * w;
-        const size_t qo = (size_t)(r_lo - y0 + r) * WP + c;
-        vx[(size_t)r * WP + c] = qx[qo];
-        vy[(size_t)r * WP + c] = qy[qo];
+    for (int idx = threadIdx.x; idx < (B + 2) * WP; idx += nt) {
+        const int r = idx / WP - 1, c = idx - (idx / WP) * WP;
+        float ux = 0.0f, uy = 0.0f;
+        if (r >= 0 && r < nown && c < w) {
+            const size_t qo = (size_t)(r_lo - y0 + r) * WP + c;
+            ux = qx[qo];
+            uy = qy[qo];
+        }
+        vx[idx] = ux;
+        vy[idx] = uy;
     }
     // g = f2 - div(w) with w = (1 - theta_m) p^n, D^- zero-extension rule
-    for (int idx = threadIdx.x; idx < zrows * zcols; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < zrows * zcols; idx += nt) {
         const int r = idx / zcols, c = idx - r * zcols;
         const int i = r_lo + r, j = x0 + c;
         auto wx = [&](int ii, int jj) -> float {
@@ -137,32 +124,46 @@ schwarz2_tile_kernel(TileArgs a) {
         const float divw = (wx(i, j) - wx(i, j - 1)) + (wy(i, j) - wy(i - 1, j));
         g[(size_t)r * WP + c] = __ldg(&a.f2[(size_t)i * a.pitch + j]) - divw;
     }
-
-    // v at a global row of this subdomain: own shared memory or a neighbour's
-    auto vrow = [&](float* plane_base, int i) -> float* {
-        const int owner = (i - y0) / B;
-        float* base = (owner == rank) ? plane_base : cl.map_shared_rank(plane_base, owner);
-        return base + (size_t)(i - y0 - owner * B) * WP;
-    };
+    __syncthreads();
+    // publish the boundary rows of the warm start (parity 0)
+    if (nown > 0) {
+        for (int c = threadIdx.x; c < WP; c += nt) {
+            outbox[0 * WP + c] = vx[(size_t)1 * WP + c];
+            outbox[1 * WP + c] = vy[(size_t)1 * WP + c];
+            outbox[2 * WP + c] = vy[(size_t)nown * WP + c];
+        }
+    }
 
     // ---- k inner updates on chip (Algorithm 3) --------------------------
+    const bool xlast = (x1 == N1);          // D^- reads v_x as zero in the grid's last column
     for (int it = 0; it < a.k; ++it) {
-        cl.sync();   // every band's v of the previous update is visible
-        for (int idx = threadIdx.x; idx < zrows * zcols; idx += blockDim.x) {
+        const int par = it & 1;
+        cl.sync();   // the neighbours' published rows of this parity are complete
+        if (has_above) {
+            const float* ob = cl.map_shared_rank(outbox, rank - 1) + (size_t)par * 3 * WP;
+            for (int c = threadIdx.x; c < WP; c += nt) vy[c] = ob[2 * WP + c];
+        }
+        if (has_below) {
+            const float* ob = cl.map_shared_rank(outbox, rank + 1) + (size_t)par * 3 * WP;
+            for (int c = threadIdx.x; c < WP; c += nt) {
+                vx[(size_t)(nown + 1) * WP + c] = ob[c];
+                vy[(size_t)(nown + 1) * WP + c] = ob[WP + c];
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < zrows * zcols; idx += nt) {
             const int r = idx / zcols, c = idx - r * zcols;
-            const int i = r_lo + r, j = x0 + c;
-            const bool in_i = i < y1;
-            const float* rx = in_i ? vrow(vx, i) : nullptr;
-            const float* ry = in_i ? vrow(vy, i) : nullptr;
-            const float vxc = (in_i && c < w && j <= N1 - 2) ? rx[c] : 0.0f;
-            const float vxl = (in_i && c >= 1 && j - 1 <= N1 - 2) ? rx[c - 1] : 0.0f;
-            const float vyc = (in_i && c < w && i <= N2 - 2) ? ry[c] : 0.0f;
-            float vyu = 0.0f;
-            if (i - 1 >= y0 && c < w && i - 1 <= N2 - 2) vyu = vrow(vy, i - 1)[c];
+            const int i = r_lo + r;
+            const float* rx = vx + (size_t)(r + 1) * WP;
+            const float* ry = vy + (size_t)(r + 1) * WP;
+            const float vxc = (c < w && !(xlast && c == w - 1)) ? rx[c] : 0.0f;
+            const float vxl = (c >= 1 && !(xlast && c - 1 == w - 1)) ? rx[c - 1] : 0.0f;
+            const float vyc = (c < w && i <= N2 - 2) ? ry[c] : 0.0f;
+            const float vyu = (c < w && i - 1 <= N2 - 2) ? ry[c - WP] : 0.0f;
             z[(size_t)r * WP + c] = (vxc - vxl) + (vyc - vyu) - g[(size_t)r * WP + c];
         }
-        cl.sync();   // all residuals computed; v may now be overwritten
-        for (int idx = threadIdx.x; idx < nown * w; idx += blockDim.x) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nown * w; idx += nt) {
             const int r = idx / w, c = idx - r * w;
             const int i = r_lo + r, j = x0 + c;
             const float zc = z[(size_t)r * WP + c];
@@ -170,23 +171,33 @@ schwarz2_tile_kernel(TileArgs a) {
             const float gy = (i < N2 - 1) ? z[(size_t)(r + 1) * WP + c] - zc : 0.0f;
             const float th = thy[r] * thx[c];
             const float den = th + t * sqrtf(gx * gx + gy * gy);
-            float* pvx = vx + (size_t)r * WP + c;
-            float* pvy = vy + (size_t)r * WP + c;
+            float* pvx = vx + (size_t)(r + 1) * WP + c;
+            float* pvy = vy + (size_t)(r + 1) * WP + c;
             if (den > 0.0f) {
-                *pvx = (th * *pvx + t * th * gx) / den;
-                *pvy = (th * *pvy + t * th * gy) / den;
+                const float sc = th / den;
+                *pvx = (*pvx + t * gx) * sc;
+                *pvy = (*pvy + t * gy) * sc;
             } else {
                 *pvx = 0.0f;
                 *pvy = 0.0f;
             }
         }
+        __syncthreads();
+        if (nown > 0) {
+            float* ob = outbox + (size_t)(par ^ 1) * 3 * WP;
+            for (int c = threadIdx.x; c < WP; c += nt) {
+                ob[c] = vx[(size_t)1 * WP + c];
+                ob[WP + c] = vy[(size_t)1 * WP + c];
+                ob[2 * WP + c] = vy[(size_t)nown * WP + c];
+            }
+        }
     }
     // ---- store the new warm start q_m ------------------------------------
-    for (int idx = threadIdx.x; idx < nown * w; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nown * w; idx += nt) {
         const int r = idx / w, c = idx - r * w;
         const size_t qo = (size_t)(r_lo - y0 + r) * WP + c;
-        qx[qo] = vx[(size_t)r * WP + c];
-        qy[qo] = vy[(size_t)r * WP + c];
+        qx[qo] = vx[(size_t)(r + 1) * WP + c];
+        qy[qo] = vy[(size_t)(r + 1) * WP + c];
     }
     cl.sync();   // no CTA leaves while a neighbour could still address its shared memory
 }
@@ -197,7 +208,7 @@ __global__ void schwarz2_combine_kernel(const float* __restrict__ pin, float* __
                                         int hmax, int wpad, float ah) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= ay.N || j >= ax.N) return;
+    if (i >= ay.L || j >= ax.L) return;
     const int ky = ay.core_of(i), kx = ax.core_of(j);
     float sx = 0.0f, sy = 0.0f;
     for (int a = ky - 1; a <= ky + 1; ++a) {
@@ -228,7 +239,7 @@ tvs_status schwarz2_check(int n2, int n1, const tvs_decomp& dd) {
     if (dd.m2 < 1 || dd.m1 < 1 || dd.overlap < 0 || dd.k_inner < 1 || dd.alpha_hat > 1.0) return TVS_ERR_ARG;
     if (dd.m2 > n2 || dd.m1 > n1) return TVS_ERR_ARG;
     const int s = dd.overlap;
-    Axis ay{n2, dd.m2, s}, ax{n1, dd.m1, s};
+    Axis ay{n2, dd.m2, s, n2}, ax{n1, dd.m1, s, n1};
     for (int k = 0; k < dd.m2; ++k)
         if (ay.core(k + 1) - ay.core(k) < (s > 1 ? s : 1)) return TVS_ERR_ARG;
     for (int k = 0; k < dd.m1; ++k)
@@ -247,19 +258,19 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
     st.s = dd.overlap;
     st.k = dd.k_inner;
     st.alpha_hat = dd.alpha_hat > 0.0 ? dd.alpha_hat : colouring(dd.m2, dd.m1);
-    Axis ay{n2, dd.m2, dd.overlap}, ax{n1, dd.m1, dd.overlap};
+    Axis ay{n2, dd.m2, dd.overlap, n2}, ax{n1, dd.m1, dd.overlap, n1};
     st.hmax = 0;
     st.wmax = 0;
     for (int k = 0; k < dd.m2; ++k) st.hmax = std::max(st.hmax, ay.end(k) - ay.start(k));
     for (int k = 0; k < dd.m1; ++k) st.wmax = std::max(st.wmax, ax.end(k) - ax.start(k));
     st.wpad = round_up(st.wmax + 1, 4);
-    // fewest CTAs per subdomain whose band fits; portable cluster sizes first
+    // fewest CTAs per subdomain whose band fits two CTAs per SM; else one CTA per SM
     st.ncl = 0;
-    for (int limit : {8, 16}) {
-        for (int ncl = 1; ncl <= limit && !st.ncl; ++ncl) {
+    for (size_t budget : {size_t(110 * 1024), kSchwarzSmemMax}) {
+        for (int ncl = 1; ncl <= 16 && !st.ncl; ++ncl) {
             const int band = (st.hmax + ncl - 1) / ncl;
             const size_t bytes = tile_smem_floats(band, st.wpad) * sizeof(float);
-            if (bytes <= kSchwarzSmemMax) {
+            if (bytes <= budget) {
                 st.ncl = ncl;
                 st.band = band;
                 st.smem = bytes;
@@ -293,7 +304,7 @@ cudaError_t schwarz2_iterate(float** cur, float** nxt, const float* f2, int pitc
                              (int)kSchwarzSmemMax);
         cudaFuncSetAttribute(schwarz2_tile_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     });
-    Axis ay{n2, st.m2, st.s}, ax{n1, st.m1, st.s};
+    Axis ay{n2, st.m2, st.s, n2}, ax{n1, st.m1, st.s, n1};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(st.ncl, st.m2 * st.m1, 1);
     cfg.blockDim = dim3(kSchwarzThreads, 1, 1);

@@ -49,6 +49,59 @@ cudaError_t launch_tau0(const float* d0, int d_pitch, int n2, int n1, float* tau
 }
 
 // ---------------------------------------------------------------------------
+// s = div(vecdiv p) on the extended grid (the source of the Poisson solve in
+// every TFS iteration), tiled: p with a two-point halo, then w = vecdiv p with
+// a one-point halo, then s.  D^- reads its argument as zero in the last
+// column (x-part) or row (y-part) and outside the grid.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTX * kBY)
+div_vecdiv_kernel(const float* __restrict__ p, int R, int C, int pitch, long plane, float* __restrict__ S) {
+    constexpr int PH = kTY + 2, PW = kTX + 2;      // p region: rows i0-2.., cols j0-2..
+    __shared__ float sp[4][PH][PW + 1];
+    __shared__ float sw[2][PH - 1][PW];            // w region: rows i0-1.., cols j0-1..
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    constexpr int NT = kTX * kBY;
+    const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
+    for (int q = 0; q < 4; ++q) {
+        const bool xpart = (q & 1) == 0;
+        for (int idx = tid; idx < PH * PW; idx += NT) {
+            const int r = idx / PW, c = idx - r * PW;
+            const int i = i0 - 2 + r, j = j0 - 2 + c;
+            const bool ok = i >= 0 && j >= 0 && i < R && j < C && (xpart ? j <= C - 2 : i <= R - 2);
+            sp[q][r][c] = ok ? __ldg(&p[(size_t)q * plane + (size_t)i * pitch + j]) : 0.f;
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (PH - 1) * (PW - 1); idx += NT) {
+        const int r = idx / (PW - 1), c = idx - r * (PW - 1);   // w point (i0-1+r, j0-1+c)
+        const int i = i0 - 1 + r, j = j0 - 1 + c;
+        const int pr = r + 1, pc = c + 1;                          // same point in the p region
+        const float w1 = (sp[0][pr][pc] - sp[0][pr][pc - 1]) + (sp[1][pr][pc] - sp[1][pr - 1][pc]);
+        const float w2 = (sp[2][pr][pc] - sp[2][pr][pc - 1]) + (sp[3][pr][pc] - sp[3][pr - 1][pc]);
+        const bool in = i >= 0 && j >= 0 && i < R && j < C;
+        sw[0][r][c] = (in && j <= C - 2) ? w1 : 0.f;
+        sw[1][r][c] = (in && i <= R - 2) ? w2 : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = ty; rr < kTY; rr += kBY) {
+        const int i = i0 + rr, j = j0 + tx;
+        if (i < R && j < C) {
+            const int r = rr + 1, c = tx + 1;
+            S[(size_t)i * pitch + j] = (sw[0][r][c] - sw[0][r][c - 1]) + (sw[1][r][c] - sw[1][r - 1][c]);
+        }
+    }
+}
+
+cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, cudaStream_t s) {
+    dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
+    ProfScope ps(kProfOther, s);
+    div_vecdiv_kernel<<<grd, blk, 0, s>>>(p, R, C, pitch, plane, S);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // out = scale * (u - grad phi) for a 2-plane field u (the last step of P_K).
 // ---------------------------------------------------------------------------
 __global__ void grad_sub_kernel(const float* __restrict__ u, int upitch, long uplane,

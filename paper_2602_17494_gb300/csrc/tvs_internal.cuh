@@ -10,7 +10,7 @@
 namespace tvs {
 
 constexpr int kPitchAlign = 32;        // floats; internal planes start rows on 128-byte lines
-constexpr int kFftThreads = 512;       // threads of the DCT kernels
+constexpr int kFftThreads = 1024;      // upper bound on threads of the DCT kernels
 constexpr int kSmemBudget = 200 * 1024;  // dynamic shared memory the DCT kernels may use
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -93,6 +93,13 @@ struct RowSrcArgs {
 };
 cudaError_t poisson_solve(float* S, int rows, int cols, int pitch, const PoissonPlans& pp,
                           RowSource src, const RowSrcArgs& sa, cudaStream_t s);
+// nbatch independent rows x cols problems; problem b's source is zero outside
+// rows [ranges[b].x, ranges[b].y) and only those rows are stored, packed, at
+// S + b * bstride (storage row 0 = grid row ranges[b].x).  Only those rows of
+// Delta^dagger of the source are produced (in place).  maxrows bounds
+// ranges[b].y - ranges[b].x; ranges is a device array.
+cudaError_t poisson_solve_batched(float* S, int nbatch, long bstride, const int2* ranges, int maxrows, int rows,
+                                  int cols, int pitch, const PoissonPlans& pp, cudaStream_t s);
 
 // --------------------------------------------------------------------------
 // Reductions for the gap / energy checks (FP64, deterministic two-pass).

@@ -243,3 +243,26 @@ def test_step2_full_size_window_parity(B, n):
         got = ph[:, cy:cy + 16, cx:cx + 16]
         # pixels further than 2m+1 from an artificial window edge are exact
         assert np.abs(got - ref).max() <= TOL, (cy, cx, iy0)
+
+
+# ---------------------------------------------------------------------------
+# Schwarz step 1 (Algorithm 2 with the localized Algorithm 5)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n2,n1,m2,m1,s,k,outer", [(14, 12, 2, 2, 2, 3, 5), (40, 36, 2, 3, 4, 4, 6),
+                                                   (33, 47, 3, 1, 3, 2, 4), (64, 64, 4, 4, 8, 3, 3)])
+def test_schwarz1_matches_oracle(B, n2, n1, m2, m1, s, k, outer):
+    d0 = image(n2, n1, 17)
+    dd = osch.Decomp(n2, n1, m2, m1, s, True)
+    tau_o, p_o, rep_o = osch.schwarz_tfs(d0.astype(np.float32).astype(np.float64), 0.05, dd, 0.125, outer, k)
+    p = torch.zeros((4, n2 + 1, n1 + 1), dtype=torch.float32, device="cuda")
+    res = B.tvs_schwarz(1, cuda(d0), None, 0.05, 1e-3, B.make_decomp(m2, m1, s, k), B.make_iter(outer), p=p)
+    assert np.abs(host(p).reshape(2, 2, n2 + 1, n1 + 1) - p_o).max() <= TOL
+    assert np.abs(host(res.out) - tau_o).max() <= TOL
+    assert rel(res.report["primal_E"], rep_o.primal_E) <= EREL
+
+
+def test_schwarz1_single_subdomain_equals_global(B):
+    d0 = cuda(image(30, 26, 18))
+    g = B.tvs_step1(d0, 0.05, B.make_iter(12))
+    s = B.tvs_schwarz(1, d0, None, 0.05, 1e-3, B.make_decomp(1, 1, 0, 4), B.make_iter(3))
+    assert torch.abs(g.out - s.out).max().item() <= 2e-6

@@ -86,3 +86,11 @@ def test_bad_arguments_rejected_before_any_device_work(lib):
     # bf16 storage is not in this build
     bf = lib.make_iter(10, storage=1)
     assert L.tvs_step1(fake, 8, 8, 0.05, ctypes.byref(bf), fake, None, fake, 1 << 30, None, ctypes.byref(rep)) == 6
+
+
+def test_schwarz1_workspace_and_limits(lib):
+    dd = lib.make_decomp(4, 4, 8, 10)
+    assert lib.workspace_bytes(1, 1024, 1024, dd) > lib.workspace_bytes(1, 1024, 1024)
+    L = lib.lib()
+    big = lib.make_decomp(128, 128, 4, 4)     # 16384 subdomains x full-width rows: beyond the scratch limit
+    assert L.tvs_workspace_bytes(1, 8192, 8192, ctypes.byref(big), 0) == 0
