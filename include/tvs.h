@@ -111,6 +111,23 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
 tvs_status tvs_project(const float* in, float* out, int rows, int cols,
                        void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Divergence-free projection for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is tvs_project without a workspace, for
+ * code that must not call cudaMalloc or take memory from a caching allocator
+ * (for example a plug-in running inside another framework's allocator or a
+ * host callback where allocation is forbidden).
+ *   in, out : 2 planes rows x cols each, as in tvs_project (in == out allowed).
+ *   Maximum : rows and cols at most 1025 each (images up to 1024 x 1024).  The
+ *             scratch is one fixed 5 MiB device array inside the library, held
+ *             on every GPU that loads the library until the process exits.
+ *             Larger grids return TVS_ERR_UNSUPPORTED with a message in
+ *             tvs_last_error().
+ *   The first call on a device looks up that array's device address; make
+ *   that first call before any stream capture.  All calls share the one
+ *   array, so calls whose GPU work overlaps (other streams, other host
+ *   threads) race; serialize them on one stream.  Allocates nothing. */
+tvs_status tvs_project_noalloc(const float* in, float* out, int rows, int cols, cudaStream_t stream);
+
 /* Step 1, TFS (Section 4.2, eq. tfsdualdis, Algorithm 1 with the projected
  * data term f1 = P_K tau0 / delta).
  *   d0   : n2 x n1 noisy image.            n2, n1 >= 2.   delta > 0.

@@ -72,6 +72,8 @@ def _load() -> ctypes.CDLL:
     lib.tvs_schwarz.restype = I
     lib.tvs_schwarz.argtypes = [I, P, P, I, I, D, D, ctypes.POINTER(TvsDecomp), ctypes.POINTER(TvsIter),
                                 P, P, P, S, P, ctypes.POINTER(TvsReport)]
+    lib.tvs_project_noalloc.restype = I
+    lib.tvs_project_noalloc.argtypes = [P, P, I, I, P]
     lib.tvs_profile_enable.restype = I
     lib.tvs_profile_enable.argtypes = [I]
     lib.tvs_profile_read.restype = I
@@ -87,7 +89,8 @@ _lib = _load()
 
 # Every symbol that include/tvs.h declares.
 EXPORTED = ["tvs_denoise", "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
-            "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2", "tvs_version", "tvs_workspace_bytes"]
+            "tvs_project_noalloc", "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2", "tvs_version",
+            "tvs_workspace_bytes"]
 
 
 def lib() -> ctypes.CDLL:
@@ -154,6 +157,15 @@ def tvs_project(tau: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Te
     st = _lib.tvs_project(_ptr(tau), _ptr(out), rows, cols, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                           _stream(tau.device))
     _check(st, "tvs_project", False)
+    return out
+
+
+def tvs_project_noalloc(tau: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """P_K without a workspace (fixed internal scratch, grids up to 1025 x 1025)."""
+    _, rows, cols = tau.shape
+    out = torch.empty_like(tau) if out is None else out
+    st = _lib.tvs_project_noalloc(_ptr(tau), _ptr(out), rows, cols, _stream(tau.device))
+    _check(st, "tvs_project_noalloc", False)
     return out
 
 

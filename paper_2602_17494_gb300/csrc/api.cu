@@ -20,6 +20,8 @@ void set_error(const char* what, cudaError_t e) {
     g_last_error = buf;
 }
 
+void set_error_text(const char* msg) { g_last_error = msg; }
+
 constexpr int kMaxSide = 8192;   // transform length <= 8193 keeps one FFT line in shared memory
 
 #define TVS_CUDA(call)                                       \

@@ -146,5 +146,6 @@ __device__ __forceinline__ void block_reduce_store(double v[kRedSlots], double* 
 // Error bookkeeping
 // --------------------------------------------------------------------------
 void set_error(const char* what, cudaError_t e);
+void set_error_text(const char* msg);
 
 }  // namespace tvs
