@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gap-runs", action="store_true")
+    ap.add_argument("--large-n", type=int, default=8192,
+                    help="side of the large-image measurements (0 = skip them)")
     ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise"], default=None,
                     help="run one API call of this step (profiling target) instead of the benchmark")
     ap.add_argument("--n", type=int, default=N, help="image side for --case")
@@ -166,14 +168,14 @@ def algorithmic(name: str, launches: int) -> tuple[str, float, str]:
     if name == "tfs_update":
         # read p (16 B), phi (4), f1 (8); write p (16) per grid point
         return "hbm", 44.0 * R * C, "bytes"
-    if name == "schwarz2_combine":
+    if name == "schwarz_combine":
         return "hbm", (8 + 8 + 8 * 1.03) * N * N, "bytes"
     if name in ("dct_rows_fwd", "dct_rows_inv"):
         # one packed Bluestein transform (2 FFTs of length M) per pair of rows
         return "alu", ((R + 1) // 2) * 2 * fft_flops(C), "flops"
     if name == "dct_cols_solve":
         return "alu", ((C + 1) // 2) * 4 * fft_flops(R), "flops"
-    if name == "schwarz2_tile":
+    if name == "schwarz_tile":
         # per inner update and pixel: div (4 add), residual (1), grad (2), norm (3 + sqrt),
         # update (2 mul + 2 fma + 2 div ~ 8) -- ~20 flops
         return "alu", 20.0 * K_INNER * (N + 8 * (M1 - 1)) * (N + 8 * (M2 - 1)), "flops"
@@ -322,6 +324,10 @@ def run_gpu(args):
         gap["step2_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms3 / mpx, "outer_iters": r3.report["iters"],
                                             "rel_gap": r3.report["rel_gap"]}
 
+    large = None
+    if rank == 0 and args.large_n > 0:
+        large = run_large(args, B, dev, torch)
+
     line = None
     if rank == 0:
         line = {
@@ -337,6 +343,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": N * N * 4,
                     "d2h_bytes_per_step": N * N * 4},
             "time_to_rel_gap_1e-4": gap,
+            "large": large,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(d0_np)
@@ -344,6 +351,94 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def run_large(args, B, dev, torch):
+    """Measurements on an n x n image whose state exceeds L2 (HBM-bound regime).
+
+    * the global IRV1 update kernel against the HBM roofline (20 algorithmic
+      bytes per pixel: read p 8, f2 4, write p 8), timed with CUDA events;
+    * global TFS: per-iteration device time of each kernel;
+    * time to relative duality gap 1e-4 of step 2: global vs Schwarz with
+      64 x 64 cores, overlap 4 and k inner updates.
+    """
+    n = args.large_n
+    from synth import SceneSpec, noisy_scene
+    d0 = torch.from_numpy(noisy_scene(SceneSpec(n, n, 3, SIGMA, True))[1].astype(np.float32)).to(dev)
+    tau = torch.empty((2, n + 1, n + 1), dtype=torch.float32, device=dev)
+    d = torch.empty((n, n), dtype=torch.float32, device=dev)
+    out = {"n": n}
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    mpx = n * n / 1e6
+
+    # step 1: a fixed number of TFS updates, kernel breakdown
+    iters1 = 40
+    ws1 = B.workspace(1, n, n, device=dev)
+    B.tvs_step1(d0, DELTA, B.make_iter(2, T), tau=tau, ws=ws1)
+    torch.cuda.synchronize(dev)
+    B.tvs_profile_enable(True)
+    t0 = time.perf_counter()
+    B.tvs_step1(d0, DELTA, B.make_iter(iters1, T), tau=tau, ws=ws1)
+    torch.cuda.synchronize(dev)
+    wall1 = time.perf_counter() - t0
+    prof = B.tvs_profile_read()
+    B.tvs_profile_enable(False)
+    per_it = {k: v[1] / max(v[0], 1) for k, v in prof.items() if v[0]}
+    out["step1_global"] = {"iters": iters1, "ms_per_iter_wall": wall1 * 1e3 / iters1,
+                           "kernel_us_per_launch": {k: 1e3 * v for k, v in per_it.items()}}
+    del ws1
+    torch.cuda.empty_cache()
+
+    # step 2 global: roofline of the update kernel
+    ws2 = B.workspace(2, n, n, device=dev)
+    B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(3, T), d=d, ws=ws2)
+    torch.cuda.synchronize(dev)
+    B.tvs_profile_enable(True)
+    B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(50, T), d=d, ws=ws2)
+    torch.cuda.synchronize(dev)
+    prof = B.tvs_profile_read()
+    B.tvs_profile_enable(False)
+    nl, ms = prof["irv1_update"]          # update launches only (the check pass is its own class)
+    avg_s = ms / nl / 1e3
+    achieved = 20.0 * n * n / avg_s / 1e9
+    out["irv1_update_roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                   "frac": achieved / hbm, "avg_launch_us": avg_s * 1e6,
+                                   "bytes_per_launch": 20.0 * n * n,
+                                   "gpix_iter_per_s": n * n / avg_s / 1e9}
+
+    # time to relative gap 1e-4: global vs Schwarz
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3, r
+
+    ms_g, r_g = timed(lambda: B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(100000, T, 1e-4, 20), d=d, ws=ws2))
+    out["step2_to_gap"] = {"global": {"ms_per_mpixel": ms_g / mpx, "iters": r_g.report["iters"],
+                                      "rel_gap": r_g.report["rel_gap"]}}
+    del ws2
+    torch.cuda.empty_cache()
+    m = n // 64
+    for k in (4, 16):
+        dd = B.make_decomp(m, m, 4, k)
+        wss = B.workspace(2, n, n, dd, device=dev)
+        B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(2, T), out=d, ws=wss)
+        ms_s, r_s = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(100000, T, 1e-4,
+                                                                                      max(1, 40 // k)),
+                                                out=d, ws=wss))
+        out["step2_to_gap"][f"schwarz_64x64_s4_k{k}"] = {"ms_per_mpixel": ms_s / mpx,
+                                                         "outer_iters": r_s.report["iters"],
+                                                         "rel_gap": r_s.report["rel_gap"]}
+        del wss
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):

@@ -1,0 +1,660 @@
+// DCT-II / DCT-III of arbitrary length and the Neumann Poisson pseudo-inverse
+// Delta^dagger = C^T (tilde Delta)^dagger C of eqs. form:DiscInvLapl,
+// form:DiscInvLaplTild, eq:DCT2D (Section 4.1).
+//
+// The extended grid of an N2 x N1 image has (N2+1) x (N1+1) points, so the
+// transform lengths are awkward (1025 = 5^2*41, 8193 = 3*2731, ...).  Every
+// length L is handled the same way:
+//   * Makhoul's reordering turns an L-point DCT-II of real data into one
+//     L-point complex DFT; two real lines are packed into one complex DFT and
+//     separated afterwards by conjugate symmetry.  The inverse (DCT-III) runs
+//     the same steps backwards.
+//   * The L-point DFT is Bluestein's chirp-z transform: a circular
+//     convolution of length M = 2^m done with two power-of-two Stockham FFTs
+//     in shared memory (radix-16 passes held in registers, see below) and a
+//     pointwise product with the precomputed filter spectrum.  The last input sample
+//     is added separately (one complex multiply-add per output), which lets the
+//     remaining L-1 samples fit a convolution of length M >= 2L-2; for
+//     L = 2^k + 1 that is M = 2^(k+1) instead of 2^(k+2).
+// Transforms here are unnormalised: the forward gives X'_k = sum_n x_n
+// cos(pi (2n+1) k / (2L)) and the inverse is its exact inverse.  The
+// orthonormal scalings of C_N cancel in C^T Lambda C because Lambda is
+// diagonal, so Delta^dagger = D'^{-1} Lambda D' with the unnormalised pair.
+//
+// Kernels:
+//   dct_rows_fwd  : per pair of rows, optional fused stencil source -> X'
+//   dct_cols_solve: per strip of column pairs, forward DCT along y, multiply
+//                   by Lambda(k_y, k_x), inverse DCT along y (in place)
+//   dct_rows_inv  : per pair of rows, inverse DCT along x (in place)
+//
+// This header holds the templated device code; dct_lm_*.cu instantiate it for
+// each FFT length and dct.cu holds the plans and the host dispatch.
+#pragma once
+
+#include "dct_launch.h"
+#include "prof.h"
+
+#include <mutex>
+
+namespace tvs {
+
+// ---- shared-memory FFTs ------------------------------------------------------
+//
+// Stockham autosort FFT (natural order in and out) of length M = 2^m on
+// shared-memory arrays.  Every pass is one radix-R step (R = 16 while at least
+// 16 points remain per sub-transform, then the remaining 8, 4 or 2): thread u
+// loads 16 complex values (16 / R butterflies of radix R), multiplies by the
+// twiddles, runs the R-point DFTs in registers and writes the results to
+// their autosorted positions.  Each pass reads and writes every element once,
+// with one barrier between the reads and the writes (the transform is in
+// place), so a thread must own all of its butterflies at once: launches use at
+// least nfft * M / 16 threads.  Shared-memory indices are padded by one slot
+// every 16 to keep the strided writes of the first passes conflict-free.
+//
+// Twiddle table: tw[k] = exp(-2 pi i k / M), k < M; the inverse uses conj.
+
+__device__ __forceinline__ int pidx(int a) { return a + (a >> 4); }
+
+// threadIdx.x read through a volatile asm: index arithmetic derived from it
+// stays inside the pass that uses it instead of being hoisted (with its live
+// registers) to the start of the kernel.
+__device__ __forceinline__ int tid_here() {
+    int t;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t)::"memory");
+    return t;
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {   // a * (-i) forward, a * (+i) inverse
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = c_add(t, b);
+    b = c_sub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 t0 = c_add(a0, a2), t1 = c_sub(a0, a2);
+    const float2 t2 = c_add(a1, a3), t3 = mul_mi<INV>(c_sub(a1, a3));
+    a0 = c_add(t0, t2);
+    a2 = c_sub(t0, t2);
+    a1 = c_add(t1, t3);
+    a3 = c_sub(t1, t3);
+}
+
+// exp(-+ 2 pi i m / 16) constants
+template <bool INV>
+__device__ __forceinline__ float2 w16(int m) {
+    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+    float2 w;
+    switch (m & 15) {
+        case 0: w = make_float2(1.f, 0.f); break;
+        case 1: w = make_float2(c1, -s1); break;
+        case 2: w = make_float2(h, -h); break;
+        case 3: w = make_float2(s1, -c1); break;
+        case 4: w = make_float2(0.f, -1.f); break;
+        case 5: w = make_float2(-s1, -c1); break;
+        case 6: w = make_float2(-h, -h); break;
+        case 7: w = make_float2(-c1, -s1); break;
+        case 8: w = make_float2(-1.f, 0.f); break;
+        case 9: w = make_float2(-c1, s1); break;
+        default: w = make_float2(0.f, 0.f); break;
+    }
+    return INV ? c_conj(w) : w;
+}
+
+// In-register DFTs on v[OFF .. OFF + R) of a 16-entry array (natural order
+// in and out); all indices are compile-time constants so v stays in registers.
+template <bool INV, int OFF>
+__device__ __forceinline__ void dft8_at(float2 (&v)[16]) {
+    // n = 2 n1 + n2: dft4 over n1, twiddle exp(-2 pi i n2 k1 / 8), dft2 over n2
+    dft4<INV>(v[OFF + 0], v[OFF + 2], v[OFF + 4], v[OFF + 6]);
+    dft4<INV>(v[OFF + 1], v[OFF + 3], v[OFF + 5], v[OFF + 7]);
+    v[OFF + 3] = c_mul(v[OFF + 3], w16<INV>(2));
+    v[OFF + 5] = c_mul(v[OFF + 5], w16<INV>(4));
+    v[OFF + 7] = c_mul(v[OFF + 7], w16<INV>(6));
+    const float2 a0 = v[OFF + 0], b0 = v[OFF + 1], a1 = v[OFF + 2], b1 = v[OFF + 3];
+    const float2 a2 = v[OFF + 4], b2 = v[OFF + 5], a3 = v[OFF + 6], b3 = v[OFF + 7];
+    v[OFF + 0] = c_add(a0, b0);
+    v[OFF + 4] = c_sub(a0, b0);
+    v[OFF + 1] = c_add(a1, b1);
+    v[OFF + 5] = c_sub(a1, b1);
+    v[OFF + 2] = c_add(a2, b2);
+    v[OFF + 6] = c_sub(a2, b2);
+    v[OFF + 3] = c_add(a3, b3);
+    v[OFF + 7] = c_sub(a3, b3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    // n = 4 n1 + n2: dft4 over n1 (gives A[n2][k1] at v[4 k1 + n2]), twiddle
+    // exp(-2 pi i n2 k1 / 16), dft4 over n2; output X[k1 + 4 k2]
+    dft4<INV>(v[0], v[4], v[8], v[12]);
+    dft4<INV>(v[1], v[5], v[9], v[13]);
+    dft4<INV>(v[2], v[6], v[10], v[14]);
+    dft4<INV>(v[3], v[7], v[11], v[15]);
+    v[5] = c_mul(v[5], w16<INV>(1));
+    v[9] = c_mul(v[9], w16<INV>(2));
+    v[13] = c_mul(v[13], w16<INV>(3));
+    v[6] = c_mul(v[6], w16<INV>(2));
+    v[10] = c_mul(v[10], w16<INV>(4));
+    v[14] = c_mul(v[14], w16<INV>(6));
+    v[7] = c_mul(v[7], w16<INV>(3));
+    v[11] = c_mul(v[11], w16<INV>(6));
+    v[15] = c_mul(v[15], w16<INV>(9));
+    dft4<INV>(v[0], v[1], v[2], v[3]);       // k1 = 0 -> X[0], X[4], X[8], X[12]
+    dft4<INV>(v[4], v[5], v[6], v[7]);       // k1 = 1 -> X[1], X[5], X[9], X[13]
+    dft4<INV>(v[8], v[9], v[10], v[11]);     // k1 = 2
+    dft4<INV>(v[12], v[13], v[14], v[15]);   // k1 = 3
+    // transpose 4 x 4: X[k1 + 4 k2] sits at v[4 k1 + k2]
+    float2 t;
+    t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[2]; v[2] = v[8]; v[8] = t;
+    t = v[3]; v[3] = v[12]; v[12] = t;
+    t = v[6]; v[6] = v[9]; v[9] = t;
+    t = v[7]; v[7] = v[13]; v[13] = t;
+    t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_all(float2 (&v)[16]) {
+    if (R == 16) {
+        dft16<INV>(v);
+    } else if (R == 8) {
+        dft8_at<INV, 0>(v);
+        dft8_at<INV, 8>(v);
+    } else if (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+        dft4<INV>(v[4], v[5], v[6], v[7]);
+        dft4<INV>(v[8], v[9], v[10], v[11]);
+        dft4<INV>(v[12], v[13], v[14], v[15]);
+    } else {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) dft2<INV>(v[2 * b], v[2 * b + 1]);
+    }
+}
+
+// One Stockham pass with everything about the shape known at compile time.
+// A thread "unit" holds UV = min(16, M) points: UV / R butterflies of radix R.
+template <int R, bool INV, int UPT, int M, int NS>
+__device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+    constexpr int UV = M < 16 ? M : 16;          // points per unit
+    constexpr int B = UV / R;                    // butterflies per unit
+    constexpr int U = M / UV;                    // units per transform
+    constexpr int MR = M / R;
+    float2 v[UPT][16];
+    const int tid0 = tid_here();
+#pragma unroll
+    for (int q = 0; q < UPT; ++q) {
+        const int u = tid0 + q * blockDim.x;
+        if (u < nfft * U) {
+            const int g = u / U;
+            const int uu = u - g * U;
+            const float2* x = buf + (size_t)g * stride;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int j = b * U + uu;        // butterfly index in [0, M/R)
+                const int jm = j & (NS - 1);
+                const int tstep = MR / NS * jm;  // jm * M / (NS R): twiddle w^r = tw[tstep * r]
+                // w^r = (w^4)^(r/4) * w^(r%4) from two table entries (a few ulps each)
+                float2 wb[4], wa[4];
+                wb[0] = make_float2(1.f, 0.f);
+                wb[1] = __ldg(&tw[tstep]);
+                wb[2] = c_mul(wb[1], wb[1]);
+                wb[3] = c_mul(wb[2], wb[1]);
+                wa[0] = make_float2(1.f, 0.f);
+                if (R > 4) {
+                    wa[1] = __ldg(&tw[4 * tstep]);
+                    wa[2] = c_mul(wa[1], wa[1]);
+                    wa[3] = c_mul(wa[2], wa[1]);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float2 a = x[pidx(j + r * MR)];
+                    if (r > 0 && NS > 1) {
+                        float2 w = (r >> 2) == 0 ? wb[r & 3]
+                                                 : ((r & 3) == 0 ? wa[r >> 2] : c_mul(wa[r >> 2], wb[r & 3]));
+                        if (INV) w = c_conj(w);
+                        a = c_mul(a, w);
+                    }
+                    v[q][b * R + r] = a;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int tid1 = tid_here();
+#pragma unroll
+    for (int q = 0; q < UPT; ++q) {
+        const int u = tid1 + q * blockDim.x;
+        if (u < nfft * U) {
+            const int g = u / U;
+            const int uu = u - g * U;
+            float2* x = buf + (size_t)g * stride;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                if (R == 16) dft16<INV>(v[q]);
+                else if (R == 8) { if (b == 0) dft8_at<INV, 0>(v[q]); else dft8_at<INV, 8>(v[q]); }
+                else if (R == 4) dft4<INV>(v[q][4 * b], v[q][4 * b + 1], v[q][4 * b + 2], v[q][4 * b + 3]);
+                else dft2<INV>(v[q][2 * b], v[q][2 * b + 1]);
+                const int j = b * U + uu;
+                const int jm = j & (NS - 1);
+                const int dst = (j - jm) * R + jm;   // (j / NS) * NS * R + j % NS
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[pidx(dst + r * NS)] = v[q][b * R + r];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// The pass sequence for M = 2^LOGM: radix 16 while at least 16 points remain
+// per sub-transform, then the remaining 8, 4 or 2.
+template <int LOGM, int LOGNS, bool INV, int UPT>
+__device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+    if constexpr (LOGNS < LOGM) {
+        constexpr int REM = LOGM - LOGNS;
+        constexpr int LR = REM >= 4 ? 4 : REM;
+        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS)>(buf, stride, nfft, tw);
+        fft_from<LOGM, LOGNS + LR, INV, UPT>(buf, stride, nfft, tw);
+    }
+}
+
+// Units per thread: transforms of 16384 points have 1024 units for 512 threads.
+template <int LOGM>
+struct FftShape {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int UNITS = M < 16 ? 1 : M / 16;
+    static constexpr int UPT = UNITS > 512 ? 2 : 1;
+};
+
+template <int LOGM, bool INV>
+__device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT>(buf, stride, nfft, tw);
+}
+
+// Chirp filter spectrum: b[m] = conj(c_m) for lags m in [-(L-2), L-1] stored
+// circularly, FFT'd (natural order) and scaled by 1/M.  One block.
+template <int LOGM>
+__global__ void __launch_bounds__(kDctThreads) plan_bhat_kernel(const __grid_constant__ DctPlan pl) {
+    extern __shared__ float2 sm[];
+    const int L = pl.L, M = pl.M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        int lag = -1;
+        if (m <= L - 1) lag = m;
+        else if (m >= M - (L - 2)) lag = M - m;
+        float2 v = make_float2(0.f, 0.f);
+        if (lag >= 0) {
+            const long long q = ((long long)lag * (long long)lag) % (2LL * L);
+            double s, c;
+            sincospi((double)q / (double)L, &s, &c);
+            v = make_float2((float)c, (float)s);  // conj(exp(-i pi lag^2 / L))
+        }
+        sm[pidx(m)] = v;
+    }
+    __syncthreads();
+    fft_stockham<LOGM, false>(sm, padded_len(M), 1, pl.tw);
+    const float inv = 1.0f / (float)M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x)
+        pl.bhat[m] = make_float2(sm[pidx(m)].x * inv, sm[pidx(m)].y * inv);
+}
+
+__device__ __forceinline__ int2 batch_rows(const BatchArgs& ba, int rows) {
+    return ba.ranges ? ba.ranges[blockIdx.y] : make_int2(0, rows);
+}
+__device__ __forceinline__ size_t row_off(const BatchArgs& ba, int2 rr, int r, int pitch) {
+    return (size_t)(ba.packed ? r - rr.x : r) * pitch;
+}
+
+// --------------------------------------------------------------------------
+// Bluestein core: buf[g][0 .. L-2] holds the chirped input a_n = z_n c_n,
+// buf[g][L-1 .. M) is zero and peel[g] = z_{L-1}.  On return buf[g][k] =
+// Z_k = sum_n z_n exp(-2 pi i n k / L) for k < L.
+// --------------------------------------------------------------------------
+template <int LOGM>
+__device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const DctPlan& pl, const float2* peel) {
+    const int L = pl.L, M = pl.M;
+    fft_stockham<LOGM, false>(buf, stride, G, pl.tw);
+    for (int b = threadIdx.x; b < G * M; b += blockDim.x) {
+        const int g = b >> pl.logM;
+        const int k = b & (M - 1);
+        float2* x = buf + (size_t)g * stride + pidx(k);
+        *x = c_mul(*x, __ldg(&pl.bhat[k]));
+    }
+    __syncthreads();
+    fft_stockham<LOGM, true>(buf, stride, G, pl.tw);
+    for (int b = threadIdx.x; b < G * L; b += blockDim.x) {
+        const int g = b / L;
+        const int k = b - g * L;
+        float2* x = buf + (size_t)g * stride + pidx(k);
+        *x = c_add(c_mul(__ldg(&pl.chirp[k]), *x), c_mul(peel[g], __ldg(&pl.rot[k])));
+    }
+    __syncthreads();
+}
+
+// Makhoul's reordering: position of input sample j in the reordered line.
+__device__ __forceinline__ int mk_perm(int j, int L) { return (j & 1) ? (L - 1 - (j >> 1)) : (j >> 1); }
+
+// Stage one packed complex sample z (position n of the reordered line).
+__device__ __forceinline__ void stage_sample(float2* bufg, float2* peelg, int n, int L, float2 z,
+                                            const DctPlan& pl) {
+    if (n == L - 1) *peelg = z;
+    else bufg[pidx(n)] = c_mul(z, __ldg(&pl.chirp[n]));
+}
+
+__device__ __forceinline__ void zero_tail(float2* buf, int stride, int G, int L, int M) {
+    const int t = M - (L - 1);
+    for (int b = threadIdx.x; b < G * t; b += blockDim.x) {
+        const int g = b / t;
+        buf[(size_t)g * stride + pidx((L - 1) + (b - g * t))] = make_float2(0.f, 0.f);
+    }
+}
+
+// Separate two real lines packed as z = x1 + i x2 from Z = DFT(z) and return
+// the unnormalised DCT-II values X'_k of both lines.
+__device__ __forceinline__ float2 unpack_dct2(const float2* bufg, int k, int L, const DctPlan& pl) {
+    const float2 zk = bufg[pidx(k)];
+    const float2 zm = bufg[pidx(k == 0 ? 0 : L - k)];
+    const float2 v1 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    const float2 v2 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    const float2 w = __ldg(&pl.post[k]);
+    return make_float2(w.x * v1.x - w.y * v1.y, w.x * v2.x - w.y * v2.y);
+}
+
+// Input of the inverse: conj(Z_k) with Z = V1 + i V2, V = e^{i pi k/2L}(X_k - i X_{L-k}).
+__device__ __forceinline__ float2 pack_dct3(float x1k, float x1m, float x2k, float x2m, int k,
+                                            const DctPlan& pl) {
+    const float2 w = __ldg(&pl.post[k]);  // e^{-i pi k / 2L}; we need its conjugate
+    // V1 = conj(w) * (x1k - i x1m)
+    const float2 v1 = make_float2(w.x * x1k - w.y * x1m, -w.x * x1m - w.y * x1k);
+    const float2 v2 = make_float2(w.x * x2k - w.y * x2m, -w.x * x2m - w.y * x2k);
+    const float2 z = make_float2(v1.x - v2.y, v1.y + v2.x);
+    return c_conj(z);
+}
+
+// --------------------------------------------------------------------------
+// Row sources (stencils evaluated on the fly; Section 4.1 operators)
+// --------------------------------------------------------------------------
+struct Fld {
+    const float* a;
+    int pitch;
+    __device__ __forceinline__ float operator()(int r, int c) const { return __ldg(&a[(size_t)r * pitch + c]); }
+};
+
+// D^-_x u at (r, c) on a grid with C columns.
+template <class F>
+__device__ __forceinline__ float dxm_at(const F& u, int r, int c, int C) {
+    if (c == 0) return u(r, 0);
+    if (c == C - 1) return -u(r, C - 2);
+    return u(r, c) - u(r, c - 1);
+}
+template <class F>
+__device__ __forceinline__ float dym_at(const F& u, int r, int c, int R) {
+    if (r == 0) return u(0, c);
+    if (r == R - 1) return -u(R - 2, c);
+    return u(r, c) - u(r - 1, c);
+}
+
+struct DivOf {  // div of the 2-plane field (ux, uy)
+    Fld ux, uy;
+    int R, C;
+    __device__ __forceinline__ float operator()(int r, int c) const {
+        return dxm_at(ux, r, c, C) + dym_at(uy, r, c, R);
+    }
+};
+
+template <RowSource SRC>
+__device__ __forceinline__ float row_source(const RowSrcArgs& sa, int r, int c, int R, int C) {
+    if (SRC == RowSource::Plain) {
+        return __ldg(&sa.a[(size_t)r * sa.pitch + c]);
+    } else if (SRC == RowSource::DivField) {
+        DivOf d{Fld{sa.a, sa.pitch}, Fld{sa.a + sa.plane, sa.pitch}, R, C};
+        return d(r, c);
+    } else {
+        // s = div(vecdiv p) = D-x w1 + D-y w2, w_k = div(p_kx, p_ky)
+        DivOf w1{Fld{sa.a, sa.pitch}, Fld{sa.a + sa.plane, sa.pitch}, R, C};
+        DivOf w2{Fld{sa.a + 2 * sa.plane, sa.pitch}, Fld{sa.a + 3 * sa.plane, sa.pitch}, R, C};
+        return dxm_at(w1, r, c, C) + dym_at(w2, r, c, R);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Kernels
+// --------------------------------------------------------------------------
+template <RowSource SRC, int LOGM>
+__global__ void __launch_bounds__(kDctThreads)
+dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
+                    RowSrcArgs sa, int G, const __grid_constant__ BatchArgs ba) {
+    extern __shared__ float2 sm[];
+    const int L = cols, M = pl.M, stride = padded_len(M);
+    float2* buf = sm;
+    float2* peel = sm + (size_t)G * stride;
+    const int2 rr = batch_rows(ba, rows);
+    out += (size_t)blockIdx.y * ba.bstride;
+    sa.a += (size_t)blockIdx.y * ba.bstride;
+    const int npairs = (rr.y - rr.x + 1) >> 1;
+    {
+        const int base = blockIdx.x * G;
+        if (base >= npairs) return;
+        const int gc = min(G, npairs - base);
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int g = b / L;
+            const int j = b - g * L;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+            float x0, x1;
+            if (SRC == RowSource::Plain) {
+                x0 = __ldg(&sa.a[row_off(ba, rr, r0, sa.pitch) + j]);
+                x1 = (r1 < rr.y) ? __ldg(&sa.a[row_off(ba, rr, r1, sa.pitch) + j]) : 0.f;
+            } else {
+                x0 = row_source<SRC>(sa, r0, j, rows, cols);
+                x1 = (r1 < rr.y) ? row_source<SRC>(sa, r1, j, rows, cols) : 0.f;
+            }
+            stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(j, L), L, make_float2(x0, x1), pl);
+        }
+        zero_tail(buf, stride, gc, L, M);
+        __syncthreads();
+        bluestein<LOGM>(buf, stride, gc, pl, peel);
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int g = b / L;
+            const int k = b - g * L;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+            const float2 X = unpack_dct2(buf + (size_t)g * stride, k, L, pl);
+            out[row_off(ba, rr, r0, pitch) + k] = X.x;
+            if (r1 < rr.y) out[row_off(ba, rr, r1, pitch) + k] = X.y;
+        }
+        __syncthreads();
+    }
+}
+
+template <int LOGM>
+__global__ void __launch_bounds__(kDctThreads)
+dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl, int G,
+                    const __grid_constant__ BatchArgs ba) {
+    extern __shared__ float2 sm[];
+    const int L = cols, M = pl.M, stride = padded_len(M);
+    float2* buf = sm;
+    float2* peel = sm + (size_t)G * stride;
+    const int2 rr = batch_rows(ba, rows);
+    S += (size_t)blockIdx.y * ba.bstride;
+    const int npairs = (rr.y - rr.x + 1) >> 1;
+    const float invL = 1.0f / (float)L;
+    {
+        const int base = blockIdx.x * G;
+        if (base >= npairs) return;
+        const int gc = min(G, npairs - base);
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int g = b / L;
+            const int k = b - g * L;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+            const float* a0 = S + row_off(ba, rr, r0, pitch);
+            const float x1k = a0[k], x1m = k ? a0[L - k] : 0.f;
+            float x2k = 0.f, x2m = 0.f;
+            if (r1 < rr.y) {
+                const float* a1 = S + row_off(ba, rr, r1, pitch);
+                x2k = a1[k];
+                x2m = k ? a1[L - k] : 0.f;
+            }
+            stage_sample(buf + (size_t)g * stride, peel + g, k, L, pack_dct3(x1k, x1m, x2k, x2m, k, pl), pl);
+        }
+        zero_tail(buf, stride, gc, L, M);
+        __syncthreads();
+        bluestein<LOGM>(buf, stride, gc, pl, peel);
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int g = b / L;
+            const int j = b - g * L;
+            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+            const float2 Y = buf[(size_t)g * stride + pidx(mk_perm(j, L))];
+            S[row_off(ba, rr, r0, pitch) + j] = Y.x * invL;
+            if (r1 < rr.y) S[row_off(ba, rr, r1, pitch) + j] = -Y.y * invL;
+        }
+        __syncthreads();
+    }
+}
+
+// Lambda(ky, kx) = -1 / (sigma_{R,ky}^2 + sigma_{C,kx}^2), 0 at (0, 0):
+// the row frequency pairs with the row count (see the oracle's reading).
+__device__ __forceinline__ float lap_symbol(int ky, int kx, int R, int C) {
+    const float sy = 2.0f * sinpif((float)ky / (2.0f * (float)R));
+    const float sx = 2.0f * sinpif((float)kx / (2.0f * (float)C));
+    const float den = sy * sy + sx * sx;
+    return den > 0.f ? -1.0f / den : 0.f;
+}
+
+template <int LOGM>
+__global__ void __launch_bounds__(kDctThreads)
+dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
+                      int G, const __grid_constant__ BatchArgs ba) {
+    extern __shared__ float2 sm[];
+    const int2 rr = batch_rows(ba, rows);       // rows outside rr are read as zero and not written
+    S += (size_t)blockIdx.y * ba.bstride;
+    const int L = rows, M = pl.M, stride = padded_len(M);
+    float2* buf = sm;
+    float2* ybuf = sm + (size_t)G * stride;       // G x L staged spectra
+    float2* peel = ybuf + (size_t)G * L;
+    const int npairs = (cols + 1) >> 1;
+    const float invL = 1.0f / (float)L;
+    {
+        const int base = blockIdx.x * G;
+        if (base >= npairs) return;
+        const int gc = min(G, npairs - base);
+        // load with the pair index fastest so that a warp reads contiguous row segments
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int r = b / gc;
+            const int g = b - r * gc;
+            const int c0 = 2 * (base + g);
+            const bool in = r >= rr.x && r < rr.y;
+            const float* a = in ? S + row_off(ba, rr, r, pitch) + c0 : S;
+            const float x0 = in ? a[0] : 0.f;
+            const float x1 = (in && c0 + 1 < cols) ? a[1] : 0.f;
+            stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(r, L), L, make_float2(x0, x1), pl);
+        }
+        zero_tail(buf, stride, gc, L, M);
+        __syncthreads();
+        bluestein<LOGM>(buf, stride, gc, pl, peel);
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int g = b / L;
+            const int k = b - g * L;
+            const int c0 = 2 * (base + g);
+            const float2 X = unpack_dct2(buf + (size_t)g * stride, k, L, pl);
+            ybuf[(size_t)g * L + k] = make_float2(X.x * lap_symbol(k, c0, rows, cols),
+                                                  X.y * lap_symbol(k, c0 + 1, rows, cols));
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int g = b / L;
+            const int k = b - g * L;
+            const float2 yk = ybuf[(size_t)g * L + k];
+            const float2 ym = k ? ybuf[(size_t)g * L + L - k] : make_float2(0.f, 0.f);
+            stage_sample(buf + (size_t)g * stride, peel + g, k, L, pack_dct3(yk.x, ym.x, yk.y, ym.y, k, pl), pl);
+        }
+        zero_tail(buf, stride, gc, L, M);
+        __syncthreads();
+        bluestein<LOGM>(buf, stride, gc, pl, peel);
+        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+            const int r = b / gc;
+            const int g = b - r * gc;
+            const int c0 = 2 * (base + g);
+            if (r < rr.x || r >= rr.y) continue;
+            const float2 Y = buf[(size_t)g * stride + pidx(mk_perm(r, L))];
+            float* a = S + row_off(ba, rr, r, pitch) + c0;
+            a[0] = Y.x * invL;
+            if (c0 + 1 < cols) a[1] = -Y.y * invL;
+        }
+        __syncthreads();
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Launchers for one FFT length
+// ---------------------------------------------------------------------------
+template <class K>
+inline void allow_dct_smem(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 16 * 1024);
+}
+
+template <int LM>
+cudaError_t launch_bhat_lm(const DctPlan& pl, cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] { allow_dct_smem(plan_bhat_kernel<LM>); });
+    const size_t smem = (size_t)padded_len(pl.M) * sizeof(float2);
+    plan_bhat_kernel<LM><<<1, kDctThreads, smem, s>>>(pl);
+    return cudaGetLastError();
+}
+
+template <int LM>
+cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int pitch, const DctPlan& pl,
+                               const RowSrcArgs& sa, const BatchArgs& ba, int nbatch, int maxrows, cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        allow_dct_smem(dct_rows_fwd_kernel<RowSource::Plain, LM>);
+        allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivField, LM>);
+    });
+    const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    const dim3 grid((maxrows + 1) / 2, nbatch);
+    const int nt = fft_threads(pl.M);
+    if (src == RowSource::Plain)
+        dct_rows_fwd_kernel<RowSource::Plain, LM><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pl, sa, 1, ba);
+    else if (src == RowSource::DivField)
+        dct_rows_fwd_kernel<RowSource::DivField, LM><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pl, sa, 1, ba);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <int LM>
+cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
+                           int nbatch, cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] { allow_dct_smem(dct_cols_solve_kernel<LM>); });
+    const size_t smem = (size_t)(padded_len(pl.M) + rows + 1) * sizeof(float2);
+    const dim3 grid((cols + 1) / 2, nbatch);
+    dct_cols_solve_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
+    return cudaGetLastError();
+}
+
+template <int LM>
+cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
+                               int nbatch, int maxrows, cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] { allow_dct_smem(dct_rows_inv_kernel<LM>); });
+    const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    const dim3 grid((maxrows + 1) / 2, nbatch);
+    dct_rows_inv_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
+    return cudaGetLastError();
+}
+
+#define TVS_DCT_INSTANTIATE(LM)                                                                                   \
+    template cudaError_t launch_bhat_lm<LM>(const DctPlan&, cudaStream_t);                                        \
+    template cudaError_t launch_rows_fwd_lm<LM>(RowSource, float*, int, int, int, const DctPlan&,                  \
+                                                const RowSrcArgs&, const BatchArgs&, int, int, cudaStream_t);      \
+    template cudaError_t launch_cols_lm<LM>(float*, int, int, int, const DctPlan&, const BatchArgs&, int,           \
+                                            cudaStream_t);                                                        \
+    template cudaError_t launch_rows_inv_lm<LM>(float*, int, int, int, const DctPlan&, const BatchArgs&, int, int, \
+                                                cudaStream_t);
+
+}  // namespace tvs

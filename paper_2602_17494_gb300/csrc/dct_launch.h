@@ -1,0 +1,64 @@
+// Launchers of the DCT kernels, one explicit instantiation per FFT length
+// M = 2^LM (dct_lm_*.cu); dct.cu dispatches on the runtime length.
+#pragma once
+
+#include "tvs_internal.cuh"
+
+namespace tvs {
+
+constexpr int kDctThreads = 512;             // threads per DCT CTA (at most)
+constexpr int kMinLogM = 2, kMaxLogM = 14;   // FFT lengths 4 .. 16384 (transform lengths 3 .. 8193)
+
+// Shared-memory FFT arrays are padded by one slot every 16 entries.
+__host__ __device__ __forceinline__ int padded_len(int M) { return M + (M >> 4) + 4; }
+
+// Batch mode (Schwarz step 1): blockIdx.y selects one of several arrays spaced
+// `bstride` floats apart; `ranges[b]` = (first row, end row) restricts the
+// transform to the rows a subdomain touches.  ranges == nullptr: all rows.
+// With `packed`, array b stores only its rows: row r lives at storage row
+// r - ranges[b].x.
+struct BatchArgs {
+    const int2* ranges;
+    long bstride;
+    int packed;
+};
+
+
+template <int LM>
+cudaError_t launch_bhat_lm(const DctPlan& pl, cudaStream_t s);
+template <int LM>
+cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int pitch, const DctPlan& pl,
+                               const RowSrcArgs& sa, const BatchArgs& ba, int nbatch, int maxrows, cudaStream_t s);
+template <int LM>
+cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
+                           int nbatch, cudaStream_t s);
+template <int LM>
+cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
+                               int nbatch, int maxrows, cudaStream_t s);
+
+// Threads for a transform of length M: one per 16-point unit, two units per
+// thread for the 16384-point transforms.
+inline int fft_threads(int M) {
+    int units = M < 16 ? 1 : M / 16;
+    if (units > kDctThreads) units = (units + 1) / 2;
+    int t = (units + 31) / 32 * 32;
+    if (t < 64) t = 64;
+    return t > kDctThreads ? kDctThreads : t;
+}
+
+// Runs STMT with the compile-time constant LM equal to the runtime value v.
+#define TVS_LOGM_CASE(N, STMT) \
+    case N: {                  \
+        constexpr int LM = N;  \
+        STMT;                  \
+    } break;
+#define TVS_LOGM_SWITCH(v, STMT)                                                                   \
+    switch (v) {                                                                                   \
+        TVS_LOGM_CASE(2, STMT) TVS_LOGM_CASE(3, STMT) TVS_LOGM_CASE(4, STMT) TVS_LOGM_CASE(5, STMT)  \
+        TVS_LOGM_CASE(6, STMT) TVS_LOGM_CASE(7, STMT) TVS_LOGM_CASE(8, STMT) TVS_LOGM_CASE(9, STMT)  \
+        TVS_LOGM_CASE(10, STMT) TVS_LOGM_CASE(11, STMT) TVS_LOGM_CASE(12, STMT)                     \
+        TVS_LOGM_CASE(13, STMT) TVS_LOGM_CASE(14, STMT)                                            \
+        default: break;                                                                            \
+    }
+
+}  // namespace tvs

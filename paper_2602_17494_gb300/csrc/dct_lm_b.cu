@@ -1,0 +1,8 @@
+// Explicit instantiation of the DCT kernels for FFT lengths 2^LM, LM in {9, 10}
+// (split across files so that the build compiles them in parallel).
+#include "dct_kernels.cuh"
+
+namespace tvs {
+TVS_DCT_INSTANTIATE(9)
+TVS_DCT_INSTANTIATE(10)
+}  // namespace tvs

@@ -134,7 +134,7 @@ cudaError_t launch_irv1_update(const float* pin, float* pout, const float* f2, i
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     const float ainv = 1.0f / alpha;
     const bool wd = d_out != nullptr;
-    ProfScope ps(kProfIrv1Update, s);
+    ProfScope ps((check || !write_p) ? kProfIrv1Check : kProfIrv1Update, s);
 #define TVS_IRV1(CK, WP, WD) \
     irv1_update_kernel<CK, WP, WD><<<grd, blk, 0, s>>>(pin, pout, f2, R, C, pitch, plane, t, ainv, d_out, d_pitch, partial)
     if (!check && write_p && !wd) TVS_IRV1(false, true, false);

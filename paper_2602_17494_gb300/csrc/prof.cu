@@ -11,8 +11,9 @@
 
 namespace tvs {
 
-static const char* kNames[kProfClasses] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "tfs_update",
-                                           "irv1_update",  "schwarz2_tile",  "schwarz2_combine", "other"};
+static const char* kNames[kProfClasses] = {"dct_rows_fwd",     "dct_cols_solve", "dct_rows_inv", "tfs_update",
+                                           "irv1_update",      "schwarz_tile",   "schwarz_combine", "stencil_other",
+                                           "tfs_check",        "irv1_check"};
 
 namespace {
 std::atomic<int> g_on{0};

@@ -16,7 +16,9 @@ enum ProfClass : int {
     kProfSchwarzTile = 5,
     kProfSchwarzCombine = 6,
     kProfOther = 7,
-    kProfClasses = 8
+    kProfTfsCheck = 8,
+    kProfIrv1Check = 9,
+    kProfClasses = 10
 };
 
 // Records an event on `s` at construction and at destruction when profiling

@@ -89,6 +89,7 @@ schwarz2_tile_kernel(TileArgs a) {
     float* qy = qx + (size_t)a.hmax * WP;
     const float t = a.t;
     const int nt = blockDim.x;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nwy = blockDim.x >> 5;
 
     // ---- set-up: weights, warm start, frozen data g_m --------------------
     for (int c = threadIdx.x; c < WP; c += nt) thx[c] = (c < w) ? a.ax.theta(mx, x0 + c) : 0.0f;
@@ -151,20 +152,21 @@ schwarz2_tile_kernel(TileArgs a) {
             }
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < zrows * zcols; idx += nt) {
-            const int r = idx / zcols, c = idx - r * zcols;
+        for (int r = wy; r < zrows; r += nwy) {
             const int i = r_lo + r;
             const float* rx = vx + (size_t)(r + 1) * WP;
             const float* ry = vy + (size_t)(r + 1) * WP;
-            const float vxc = (c < w && !(xlast && c == w - 1)) ? rx[c] : 0.0f;
-            const float vxl = (c >= 1 && !(xlast && c - 1 == w - 1)) ? rx[c - 1] : 0.0f;
-            const float vyc = (c < w && i <= N2 - 2) ? ry[c] : 0.0f;
-            const float vyu = (c < w && i - 1 <= N2 - 2) ? ry[c - WP] : 0.0f;
-            z[(size_t)r * WP + c] = (vxc - vxl) + (vyc - vyu) - g[(size_t)r * WP + c];
+            for (int c = lane; c < zcols; c += 32) {
+                const float vxc = (c < w && !(xlast && c == w - 1)) ? rx[c] : 0.0f;
+                const float vxl = (c >= 1 && !(xlast && c - 1 == w - 1)) ? rx[c - 1] : 0.0f;
+                const float vyc = (c < w && i <= N2 - 2) ? ry[c] : 0.0f;
+                const float vyu = (c < w && i - 1 <= N2 - 2) ? ry[c - WP] : 0.0f;
+                z[(size_t)r * WP + c] = (vxc - vxl) + (vyc - vyu) - g[(size_t)r * WP + c];
+            }
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nown * w; idx += nt) {
-            const int r = idx / w, c = idx - r * w;
+        for (int r = wy; r < nown; r += nwy)
+            for (int c = lane; c < w; c += 32) {
             const int i = r_lo + r, j = x0 + c;
             const float zc = z[(size_t)r * WP + c];
             const float gx = (j < N1 - 1) ? z[(size_t)r * WP + c + 1] - zc : 0.0f;
@@ -181,7 +183,7 @@ schwarz2_tile_kernel(TileArgs a) {
                 *pvx = 0.0f;
                 *pvy = 0.0f;
             }
-        }
+            }
         __syncthreads();
         if (nown > 0) {
             float* ob = outbox + (size_t)(par ^ 1) * 3 * WP;

@@ -248,7 +248,7 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
                               float* tau_out, int tau_pitch, long tau_plane, double* partial, cudaStream_t s) {
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     const bool wt = tau_out != nullptr;
-    ProfScope ps(kProfTfsUpdate, s);
+    ProfScope ps((check || !write_p) ? kProfTfsCheck : kProfTfsUpdate, s);
 #define TVS_TFS(CK, WP, WT)                                                                              \
     tfs_update_kernel<CK, WP, WT><<<grd, blk, 0, s>>>(pin, pout, phi, f1, R, C, pitch, plane, t, delta, \
                                                       tau_out, tau_pitch, tau_plane, partial)
