@@ -180,9 +180,9 @@ __device__ __forceinline__ void dft_all(float2 (&v)[16]) {
 
 // One Stockham pass with everything about the shape known at compile time.
 // A thread "unit" holds UV = min(16, M) points: UV / R butterflies of radix R.
-template <int R, bool INV, int UPT, int M, int NS>
+template <int R, bool INV, int UPT, int M, int NS, int UVMAX>
 __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
-    constexpr int UV = M < 16 ? M : 16;          // points per unit
+    constexpr int UV = M < UVMAX ? M : UVMAX;    // points per unit
     constexpr int B = UV / R;                    // butterflies per unit
     constexpr int U = M / UV;                    // units per transform
     constexpr int MR = M / R;
@@ -254,27 +254,31 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
 
 // The pass sequence for M = 2^LOGM: radix 16 while at least 16 points remain
 // per sub-transform, then the remaining 8, 4 or 2.
-template <int LOGM, int LOGNS, bool INV, int UPT>
+template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV>
 __device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
     if constexpr (LOGNS < LOGM) {
         constexpr int REM = LOGM - LOGNS;
-        constexpr int LR = REM >= 4 ? 4 : REM;
-        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS)>(buf, stride, nfft, tw);
-        fft_from<LOGM, LOGNS + LR, INV, UPT>(buf, stride, nfft, tw);
+        constexpr int LR = REM >= LOGUV ? LOGUV : REM;
+        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS), (1 << LOGUV)>(buf, stride, nfft, tw);
+        fft_from<LOGM, LOGNS + LR, INV, UPT, LOGUV>(buf, stride, nfft, tw);
     }
 }
 
-// Units per thread: transforms of 16384 points have 1024 units for 512 threads.
+// Unit size and units per thread: 8-point units (radix-8 passes) up to 4096
+// points, so short transforms get twice the threads; 16-point units beyond;
+// transforms of 16384 points have 1024 units for 512 threads.
 template <int LOGM>
 struct FftShape {
     static constexpr int M = 1 << LOGM;
-    static constexpr int UNITS = M < 16 ? 1 : M / 16;
-    static constexpr int UPT = UNITS > 512 ? 2 : 1;
+    static constexpr int LOGUV = LOGM <= 12 ? 3 : 4;
+    static constexpr int UV = 1 << LOGUV;
+    static constexpr int UNITS = M < UV ? 1 : M / UV;
+    static constexpr int UPT = UNITS > kDctThreads ? 2 : 1;
 };
 
 template <int LOGM, bool INV>
 __device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
-    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT>(buf, stride, nfft, tw);
+    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT, FftShape<LOGM>::LOGUV>(buf, stride, nfft, tw);
 }
 
 // Chirp filter spectrum: b[m] = conj(c_m) for lags m in [-(L-2), L-1] stored

@@ -6,16 +6,12 @@
 //
 // The backward difference D^-_x of Section 4.1 equals the plain difference of
 // the field with its last column (and everything left of the grid) read as
-// zero; D^-_y likewise with the last row.  The tiles below load the dual with
+// zero; D^-_y likewise with the last row.  The kernels below read the dual with
 // exactly those zeros, so one stencil covers the interior and the boundary.
 #include "tvs_internal.cuh"
 #include "prof.h"
 
 namespace tvs {
-
-constexpr int kTX = 32;   // tile width (one 128-byte line of floats)
-constexpr int kTY = 16;   // tile height
-constexpr int kBY = 8;    // thread rows; each thread does kTY / kBY output rows
 
 // ---------------------------------------------------------------------------
 // xi and f2 (eq. defXi2:discrete, eq. ir1dualdis)
@@ -51,92 +47,227 @@ cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long t
 }
 
 // ---------------------------------------------------------------------------
-// Fused IRV1 update (and/or check) kernel.
-//   CHECK  : block partial sums of the gap/energy terms at the input p
+// Streaming IRV1 update: each warp owns a strip of 128 columns (4 per lane,
+// float4 loads) and walks down a chunk of rows, keeping the previous row's
+// dual and residual in registers.  Left/right neighbours come from warp
+// shuffles; only the strip edges load scalar halo values.  No shared memory
+// and no barriers, so HBM traffic is the 20 algorithmic bytes per pixel plus
+// one extra row per chunk.  Requires pitch % 4 == 0 and 16-byte aligned planes.
+//   CHECK  : per-warp partial sums of the gap/energy terms at the input p
 //   WRITE_P: write the updated dual
 //   WRITE_D: write d = -z / alpha at the input p
 // ---------------------------------------------------------------------------
+constexpr int kStrip = 128;      // columns per warp
+constexpr int kChunk = 32;       // output rows per warp
+constexpr int kStreamWarps = 4;  // warps per block
+
+struct Row4 {
+    float4 px, py, f;
+};
+
+__device__ __forceinline__ float4 ld4(const float* __restrict__ a, size_t o) {
+    return __ldg(reinterpret_cast<const float4*>(a + o));
+}
+__device__ __forceinline__ float comp(const float4& v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
 template <bool CHECK, bool WRITE_P, bool WRITE_D>
-__global__ void __launch_bounds__(kTX * kBY)
-irv1_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const float* __restrict__ f2,
-                   int R, int C, int pitch, long plane, float t, float alpha_inv,
-                   float* __restrict__ d_out, int d_pitch, double* __restrict__ partial) {
-    __shared__ float sx[kTY + 1][kTX + 2];  // p_x rows i0..i0+TY, cols j0-1..j0+TX
-    __shared__ float sy[kTY + 2][kTX + 1];  // p_y rows i0-1..i0+TY, cols j0..j0+TX
-    __shared__ float sf[kTY + 1][kTX + 1];
-    __shared__ float sz[kTY + 1][kTX + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTX + tx;
-    constexpr int NT = kTX * kBY;
-    const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
+__global__ void __launch_bounds__(32 * kStreamWarps, 8)
+irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, const float* __restrict__ f2, int R,
+                   int C, int pitch, long plane, float t, float alpha_inv, float* __restrict__ d_out, int d_pitch,
+                   double* __restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int strip = blockIdx.x;
+    const int chunk = blockIdx.y * kStreamWarps + wib;
+    const int r0 = chunk * kChunk;
+    const int j0 = strip * kStrip + 4 * lane;     // first column of this lane
+    const int r1 = min(r0 + kChunk, R);           // output rows [r0, r1)
     const float* __restrict__ px = pin;
     const float* __restrict__ py = pin + plane;
-
-    for (int idx = tid; idx < (kTY + 1) * (kTX + 2); idx += NT) {
-        const int r = idx / (kTX + 2), c = idx - r * (kTX + 2);
-        const int i = i0 + r, j = j0 - 1 + c;
-        sx[r][c] = (i < R && j >= 0 && j <= C - 2) ? __ldg(&px[(size_t)i * pitch + j]) : 0.f;
-    }
-    for (int idx = tid; idx < (kTY + 2) * (kTX + 1); idx += NT) {
-        const int r = idx / (kTX + 1), c = idx - r * (kTX + 1);
-        const int i = i0 - 1 + r, j = j0 + c;
-        sy[r][c] = (i >= 0 && i <= R - 2 && j < C) ? __ldg(&py[(size_t)i * pitch + j]) : 0.f;
-    }
-    for (int idx = tid; idx < (kTY + 1) * (kTX + 1); idx += NT) {
-        const int r = idx / (kTX + 1), c = idx - r * (kTX + 1);
-        const int i = i0 + r, j = j0 + c;
-        sf[r][c] = (i < R && j < C) ? __ldg(&f2[(size_t)i * pitch + j]) : 0.f;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < (kTY + 1) * (kTX + 1); idx += NT) {
-        const int r = idx / (kTX + 1), c = idx - r * (kTX + 1);
-        sz[r][c] = (sx[r][c + 1] - sx[r][c]) + (sy[r + 1][c] - sy[r][c]) - sf[r][c];
-    }
-    __syncthreads();
-
     double acc[kRedSlots];
 #pragma unroll
     for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+
+    if (r0 < R) {
+        const int jr = strip * kStrip + kStrip;   // first column right of the strip
+        // column masks: D^- reads p_x as zero in the last column and beyond the grid
+        float mx[4], mv[4];
 #pragma unroll
-    for (int rr = ty; rr < kTY; rr += kBY) {
-        const int i = i0 + rr, j = j0 + tx;
-        if (i < R && j < C) {
-            const float z = sz[rr][tx];
-            const float gx = (j < C - 1) ? sz[rr][tx + 1] - z : 0.f;
-            const float gy = (i < R - 1) ? sz[rr + 1][tx] - z : 0.f;
-            const size_t o = (size_t)i * pitch + j;
-            const float pxv = __ldg(&px[o]), pyv = __ldg(&py[o]);
-            if (WRITE_P) {
-                const float den = 1.0f + t * sqrtf(gx * gx + gy * gy);
-                pout[o] = (pxv + t * gx) / den;
-                pout[plane + o] = (pyv + t * gy) / den;
+        for (int e = 0; e < 4; ++e) {
+            mv[e] = (j0 + e < C) ? 1.f : 0.f;
+            mx[e] = (j0 + e <= C - 2) ? 1.f : 0.f;
+        }
+        const size_t cbase = (size_t)j0;
+        // row r0 - 1: p_y (for div at row r0)
+        float4 pyu = make_float4(0.f, 0.f, 0.f, 0.f);
+        float pyu_r = 0.f;                         // p_y(r0 - 1, jr) for the right halo (lane 31)
+        if (r0 >= 1 && r0 - 1 <= R - 2) {
+            pyu = ld4(py, (size_t)(r0 - 1) * pitch + cbase);
+            if (lane == 31 && jr < C) pyu_r = __ldg(&py[(size_t)(r0 - 1) * pitch + jr]);
+        }
+        auto load_row = [&](int i, Row4& rw, float& pxl, float& pxr, float& pyr, float& fr) {
+            const size_t o = (size_t)i * pitch + cbase;
+            rw.px = ld4(px, o);
+            rw.py = ld4(py, o);
+            rw.f = ld4(f2, o);
+            pxl = (lane == 0 && j0 >= 1) ? __ldg(&px[(size_t)i * pitch + j0 - 1]) : 0.f;
+            pxr = 0.f;
+            pyr = 0.f;
+            fr = 0.f;
+            if (lane == 31 && jr < C) {
+                pxr = __ldg(&px[(size_t)i * pitch + jr]);
+                pyr = __ldg(&py[(size_t)i * pitch + jr]);
+                fr = __ldg(&f2[(size_t)i * pitch + jr]);
             }
-            if (WRITE_D) d_out[(size_t)i * d_pitch + j] = -z * alpha_inv;
-            if (CHECK) {
-                const double dgx = gx, dgy = gy, dpx = pxv, dpy = pyv;
-                acc[0] += sqrt(dgx * dgx + dgy * dgy);
-                acc[1] += dgx * dpx + dgy * dpy;
-                acc[2] += (double)z * (double)z;
-                const double dv = (double)z + (double)sf[rr][tx];
-                acc[3] += dv * dv;
-                acc[4] = fmax(acc[4], sqrt(dpx * dpx + dpy * dpy));
+        };
+        Row4 cur, nxt;
+        float cpxl, cpxr, cpyr, cfr, npxl = 0.f, npxr = 0.f, npyr = 0.f, nfr = 0.f;
+        load_row(r0, cur, cpxl, cpxr, cpyr, cfr);
+        float zp[4] = {0.f, 0.f, 0.f, 0.f};        // z of the previous row
+        float zpr = 0.f;                           // z(prev row, jr) on lane 31
+        float4 pprevx = make_float4(0.f, 0.f, 0.f, 0.f), pprevy = pprevx;
+        const int rend = min(r1 + 1, R);           // rows whose z is needed
+        for (int i = r0; i <= r1; ++i) {
+            const bool have = i < rend;
+            if (i + 1 < rend) load_row(i + 1, nxt, npxl, npxr, npyr, nfr);
+            float zc[4] = {0.f, 0.f, 0.f, 0.f};
+            float zcr = 0.f;
+            if (have) {
+                // z = div p - f2 at row i (zero-extension rule of D^-)
+                const float ymask = (i <= R - 2) ? 1.f : 0.f;
+                float pxs[4] = {cur.px.x * mx[0], cur.px.y * mx[1], cur.px.z * mx[2], cur.px.w * mx[3]};
+                float left = __shfl_up_sync(0xffffffffu, pxs[3], 1);
+                if (lane == 0) left = (j0 >= 1 && j0 - 1 <= C - 2) ? cpxl : 0.f;
+                const float pyc[4] = {cur.py.x * ymask, cur.py.y * ymask, cur.py.z * ymask, cur.py.w * ymask};
+                const float pyp[4] = {pyu.x, pyu.y, pyu.z, pyu.w};
+                const float fv[4] = {cur.f.x, cur.f.y, cur.f.z, cur.f.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float pl = e == 0 ? left : pxs[e - 1];
+                    zc[e] = ((pxs[e] - pl) + (pyc[e] - pyp[e]) - fv[e]) * mv[e];
+                }
+                if (lane == 31 && jr < C) {
+                    const float pxr_m = (jr <= C - 2) ? cpxr : 0.f;
+                    zcr = (pxr_m - pxs[3]) + (cpyr * ymask - pyu_r) - cfr;
+                }
+                if (WRITE_D && i < r1) {
+                    float* dd = d_out + (size_t)i * d_pitch;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (j0 + e < C) dd[j0 + e] = -zc[e] * alpha_inv;
+                }
+                pyu = make_float4(pyc[0], pyc[1], pyc[2], pyc[3]);
+                pyu_r = cpyr * ymask;
             }
+            if (i > r0) {
+                // update row i - 1 from z(i-1) (zp), z(i) (zc)
+                const int ir = i - 1;
+                float zright = __shfl_down_sync(0xffffffffu, zp[0], 1);
+                if (lane == 31) zright = zpr;
+                float res_x[4], res_y[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float zn = e == 3 ? zright : zp[e + 1];
+                    const float gx = (j0 + e < C - 1) ? zn - zp[e] : 0.f;
+                    const float gy = (ir < R - 1) ? zc[e] - zp[e] : 0.f;
+                    const float pxv = comp(pprevx, e), pyv = comp(pprevy, e);
+                    if (WRITE_P) {
+                        const float den = 1.0f + t * sqrtf(gx * gx + gy * gy);
+                        res_x[e] = (pxv + t * gx) / den;
+                        res_y[e] = (pyv + t * gy) / den;
+                    }
+                    if (CHECK && j0 + e < C) {
+                        const double dgx = gx, dgy = gy, dpx = pxv, dpy = pyv;
+                        acc[0] += sqrt(dgx * dgx + dgy * dgy);
+                        acc[1] += dgx * dpx + dgy * dpy;
+                        acc[2] += (double)zp[e] * (double)zp[e];
+                        // div p = z + f2 at (ir, j): recover from z and the stored f2 of row ir
+                        acc[4] = fmax(acc[4], sqrt(dpx * dpx + dpy * dpy));
+                    }
+                }
+                if (WRITE_P) {
+                    const size_t o = (size_t)ir * pitch + cbase;
+                    if (j0 + 3 < C) {
+                        *reinterpret_cast<float4*>(pout + o) = make_float4(res_x[0], res_x[1], res_x[2], res_x[3]);
+                        *reinterpret_cast<float4*>(pout + plane + o) =
+                            make_float4(res_y[0], res_y[1], res_y[2], res_y[3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (j0 + e < C) {
+                                pout[o + e] = res_x[e];
+                                pout[plane + o + e] = res_y[e];
+                            }
+                    }
+                }
+            }
+            if (CHECK && have && i < r1) {
+                const float fv[4] = {cur.f.x, cur.f.y, cur.f.z, cur.f.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j0 + e < C) {
+                        const double dv = (double)zc[e] + (double)fv[e];
+                        acc[3] += dv * dv;
+                    }
+            }
+            // rotate
+#pragma unroll
+            for (int e = 0; e < 4; ++e) zp[e] = zc[e];
+            zpr = zcr;
+            if (have) {
+                pprevx = cur.px;
+                pprevy = cur.py;
+            }
+            cur = nxt;
+            cpxl = npxl;
+            cpxr = npxr;
+            cpyr = npyr;
+            cfr = nfr;
         }
     }
-    if (CHECK) block_reduce_store<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
+    if (CHECK) {
+        // deterministic warp reduction, one partial per warp
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) {
+            double x = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = red_is_max(k) ? fmax(x, y) : x + y;
+            }
+            acc[k] = x;
+        }
+        if (lane < kRedSlots) {
+            const size_t w = (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStreamWarps + wib;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < kRedSlots; ++k)
+                if (k == lane) v = acc[k];
+            partial[w * kRedSlots + lane] = v;
+        }
+    }
 }
 
-int irv1_blocks(int R, int C) { return ((C + kTX - 1) / kTX) * ((R + kTY - 1) / kTY); }
+int irv1_blocks(int R, int C) {
+    // partial slots: one per warp of the streaming kernel
+    const int strips = (C + kStrip - 1) / kStrip;
+    const int chunks = (R + kChunk - 1) / kChunk;
+    return strips * ((chunks + kStreamWarps - 1) / kStreamWarps) * kStreamWarps;
+}
 
 cudaError_t launch_irv1_update(const float* pin, float* pout, const float* f2, int R, int C, int pitch,
                                long plane, float t, float alpha, bool check, bool write_p,
                                float* d_out, int d_pitch, double* partial, cudaStream_t s) {
-    dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
+    const int strips = (C + kStrip - 1) / kStrip;
+    const int chunks = (R + kChunk - 1) / kChunk;
+    dim3 blk(32 * kStreamWarps), grd(strips, (chunks + kStreamWarps - 1) / kStreamWarps);
     const float ainv = 1.0f / alpha;
     const bool wd = d_out != nullptr;
     ProfScope ps((check || !write_p) ? kProfIrv1Check : kProfIrv1Update, s);
 #define TVS_IRV1(CK, WP, WD) \
-    irv1_update_kernel<CK, WP, WD><<<grd, blk, 0, s>>>(pin, pout, f2, R, C, pitch, plane, t, ainv, d_out, d_pitch, partial)
+    irv1_stream_kernel<CK, WP, WD><<<grd, blk, 0, s>>>(pin, pout, f2, R, C, pitch, plane, t, ainv, d_out, d_pitch, partial)
     if (!check && write_p && !wd) TVS_IRV1(false, true, false);
     else if (check && write_p && !wd) TVS_IRV1(true, true, false);
     else if (check && !write_p && wd) TVS_IRV1(true, false, true);

@@ -266,3 +266,22 @@ def test_schwarz1_single_subdomain_equals_global(B):
     g = B.tvs_step1(d0, 0.05, B.make_iter(12))
     s = B.tvs_schwarz(1, d0, None, 0.05, 1e-3, B.make_decomp(1, 1, 0, 4), B.make_iter(3))
     assert torch.abs(g.out - s.out).max().item() <= 2e-6
+
+
+@pytest.mark.parametrize("n,k", [(8192, 4), (2048, 16)])
+def test_schwarz2_full_size_reaches_global_minimiser(B, n, k):
+    # Strong convexity of the primal (Appendix A) certifies ||d - d*|| <= sqrt(2 gap / alpha);
+    # both runs stop on their own duality gap, so their distance is bounded by the sum.
+    d0 = cuda(image(n, n, 41, texture=True))
+    tau = B.tvs_step1(d0, 0.05, B.make_iter(30)).out
+    g = B.tvs_step2(d0, tau, 10.0, 1e-3, B.make_iter(20000, rel_gap_tol=2e-5, check_every=50))
+    s = B.tvs_schwarz(2, d0, tau, 10.0, 1e-3, B.make_decomp(n // 64, n // 64, 4, k),
+                      B.make_iter(20000, rel_gap_tol=2e-5, check_every=max(1, 50 // k)))
+    assert g.status == 0 and s.status == 0
+    # |q| <= theta holds exactly only in exact arithmetic: once t|psi| drops below
+    # half an ulp of theta the FP32 denominator rounds to theta while q still
+    # moves by t psi, so each inner update may overshoot by about one ulp.
+    assert s.report["max_p"] <= 1.0 + 1.2e-7 * s.report["iters"] * k
+    dist = torch.linalg.vector_norm((g.out - s.out).double()).item()
+    bound = np.sqrt(2 * g.report["gap"] / 10.0) + np.sqrt(2 * s.report["gap"] / 10.0)
+    assert dist <= bound * 1.05 + 1e-6 * n, (dist, bound)   # + FP32 rounding of d
