@@ -426,10 +426,24 @@ def run_large(args, B, dev, torch):
     del ws2
     torch.cuda.empty_cache()
     m = n // 64
-    for k in (4, 16):
+    for k in (1, 4, 16):
         dd = B.make_decomp(m, m, 4, k)
         wss = B.workspace(2, n, n, dd, device=dev)
         B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(2, T), out=d, ws=wss)
+        # kernel breakdown over 8 outer iterations (one check at the end)
+        torch.cuda.synchronize(dev)
+        B.tvs_profile_enable(True)
+        B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(8, T, 0.0, 8), out=d, ws=wss)
+        torch.cuda.synchronize(dev)
+        prof = B.tvs_profile_read()
+        B.tvs_profile_enable(False)
+        kern = {kk: {"launches": v[0], "us_per_launch": 1e3 * v[1] / v[0]} for kk, v in prof.items() if v[0]}
+        # pixel updates per tile launch: k inner updates over every Gamma_m (overlap counted once per subdomain)
+        sides = [min(n, (i + 1) * 64 + 2) - max(0, i * 64 - 2) for i in range(m)]
+        upd = k * sum(sides) ** 2
+        tile_us = kern.get("schwarz_tile", {}).get("us_per_launch", float("nan"))
+        out[f"schwarz_64x64_s4_k{k}_kernels"] = {"kernels": kern, "redundancy": upd / (k * n * n),
+                                                 "tile_gpix_updates_per_s": upd / tile_us / 1e3}
         ms_s, r_s = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(100000, T, 1e-4,
                                                                                       max(1, 40 // k)),
                                                 out=d, ws=wss))

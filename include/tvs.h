@@ -61,7 +61,14 @@ typedef struct {
     double t;            /* Chambolle step, 0 < t <= 1/8 (convergence theorem, Sec. 4.2) */
     double rel_gap_tol;  /* stop once gap/E <= tol (checked every check_every); 0 = never */
     int    check_every;  /* updates between gap checks; <= 0 means only at the end      */
-    int    storage;      /* tvs_storage of the dual fields (TVS_F32 in this build)      */
+    int    storage;      /* tvs_storage of the dual fields kept between updates:
+                          * TVS_F32 everywhere; TVS_BF16 or TVS_F16 for step 2
+                          * (tvs_step2, tvs_schwarz step 2, tvs_denoise it2),
+                          * where p and the Schwarz warm starts q are stored in
+                          * 16 bits and widened to FP32 for every update (round
+                          * to nearest on store).  The caller's p stays FP32.
+                          * Step 1 with a 16-bit storage: TVS_ERR_UNSUPPORTED;
+                          * any other value: TVS_ERR_ARG.                        */
 } tvs_iter;
 
 /* Values at the returned dual iterate p (duality gap per Appendix A):
@@ -99,8 +106,9 @@ const char* tvs_last_error(void);
 /* Bytes of scratch needed by a call.
  *   step = 1: tvs_step1 / tvs_schwarz(step=1); step = 2: tvs_step2 /
  *   tvs_schwarz(step=2); step = 0: tvs_denoise (covers both); step = 3:
- *   tvs_project.  dd = NULL means the global iteration.  Returns 0 for
- *   invalid sizes. */
+ *   tvs_project.  dd = NULL means the global iteration.  storage: the
+ *   tvs_iter.storage of the (step-2) call.  Returns 0 for invalid sizes or
+ *   a storage the step does not support. */
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage);
 
 /* Divergence-free projection P_K = I - grad Delta^dagger div on a grid of

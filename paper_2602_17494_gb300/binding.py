@@ -134,8 +134,9 @@ def workspace_bytes(step: int, n2: int, n1: int, dd: TvsDecomp | None = None, st
     return int(n)
 
 
-def workspace(step: int, n2: int, n1: int, dd: TvsDecomp | None = None, device=None) -> torch.Tensor:
-    n = workspace_bytes(step, n2, n1, dd)
+def workspace(step: int, n2: int, n1: int, dd: TvsDecomp | None = None, device=None,
+              storage: int = TVS_F32) -> torch.Tensor:
+    n = workspace_bytes(step, n2, n1, dd, storage)
     return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
 
@@ -186,7 +187,7 @@ def tvs_step2(d0: torch.Tensor, tau: torch.Tensor, alpha: float, eps: float, it:
               ws: torch.Tensor | None = None) -> Result:
     n2, n1 = d0.shape
     d = torch.empty_like(d0) if d is None else d
-    ws = workspace(2, n2, n1, device=d0.device) if ws is None else ws
+    ws = workspace(2, n2, n1, device=d0.device, storage=it.storage) if ws is None else ws
     rep = TvsReport()
     st = _lib.tvs_step2(_ptr(d0), _ptr(tau), n2, n1, float(alpha), float(eps), ctypes.byref(it), _ptr(d), _ptr(p),
                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device), ctypes.byref(rep))
@@ -199,7 +200,7 @@ def tvs_denoise(d0: torch.Tensor, delta: float, alpha: float, eps: float, it1: T
                 ws: torch.Tensor | None = None):
     n2, n1 = d0.shape
     d = torch.empty_like(d0) if d is None else d
-    ws = workspace(0, n2, n1, dd2, device=d0.device) if ws is None else ws
+    ws = workspace(0, n2, n1, dd2, device=d0.device, storage=it2.storage) if ws is None else ws
     reps = (TvsReport * 2)()
     st = _lib.tvs_denoise(_ptr(d0), n2, n1, float(delta), float(alpha), float(eps), ctypes.byref(it1),
                           ctypes.byref(it2), ctypes.byref(dd2) if dd2 is not None else None, _ptr(tau), _ptr(d),
@@ -215,7 +216,7 @@ def tvs_schwarz(step: int, d0: torch.Tensor, tau: torch.Tensor | None, weight: f
     if out is None:
         shape = (n2, n1) if step == 2 else (2, n2 + 1, n1 + 1)
         out = torch.empty(shape, dtype=torch.float32, device=d0.device)
-    ws = workspace(step, n2, n1, dd, device=d0.device) if ws is None else ws
+    ws = workspace(step, n2, n1, dd, device=d0.device, storage=outer.storage) if ws is None else ws
     rep = TvsReport()
     st = _lib.tvs_schwarz(step, _ptr(d0), _ptr(tau), n2, n1, float(weight), float(eps), ctypes.byref(dd),
                           ctypes.byref(outer), _ptr(out), _ptr(p), ctypes.c_void_p(ws.data_ptr()), ws.numel(),

@@ -61,17 +61,20 @@ static size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
 struct Step2Layout {
     int R, C, P;
     long plane;
-    float *pa, *pb, *f2;
+    int st;            // tvs_storage of the dual p (pa, pb)
+    void *pa, *pb;
+    float* f2;
     RedBuf red;
 };
 
-static size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L) {
+static size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int storage) {
     L.R = n2;
     L.C = n1;
     L.P = round_up(L.C, kPitchAlign);
     L.plane = (long)L.R * L.P;
-    L.pa = cv.take<float>(2 * (size_t)L.plane);
-    L.pb = cv.take<float>(2 * (size_t)L.plane);
+    L.st = storage;
+    L.pa = cv.take<char>(2 * (size_t)L.plane * storage_bytes(storage));
+    L.pb = cv.take<char>(2 * (size_t)L.plane * storage_bytes(storage));
     L.f2 = cv.take<float>((size_t)L.plane);
     carve_red(cv, L.red, irv1_blocks(L.R, L.C));
     return cv.used();
@@ -98,10 +101,12 @@ static size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
 // ---------------------------------------------------------------------------
 static bool side_ok(int n) { return n >= 2 && n <= kMaxSide; }
 
-static tvs_status check_iter(const tvs_iter* it) {
+// step 1 keeps its dual in FP32; step 2 also stores it as bf16 or fp16
+static tvs_status check_iter(const tvs_iter* it, bool narrow_ok) {
     if (!it) return TVS_ERR_ARG;
     if (it->max_iter < 0 || !(it->t > 0.0) || it->t > 0.125 || it->rel_gap_tol < 0.0) return TVS_ERR_ARG;
-    if (it->storage != TVS_F32) return TVS_ERR_UNSUPPORTED;
+    if (storage_bytes(it->storage) == 0) return TVS_ERR_ARG;
+    if (it->storage != TVS_F32 && !narrow_ok) return TVS_ERR_UNSUPPORTED;
     return TVS_OK;
 }
 
@@ -120,7 +125,7 @@ static tvs_status read_result(const RedBuf& rb, int nblocks, cudaStream_t s, dou
 static void report_tfs(const double r[kRedSlots], double delta, int iters, tvs_report* rep) {
     const double tv = delta * r[0];
     const double e = tv + 0.5 * delta * r[3];
-    const double gap = delta * (r[0] - r[1]);
+    const double gap = delta * r[1];
     rep->iters = iters;
     rep->dual_D = r[2];
     rep->primal_E = e;
@@ -133,7 +138,7 @@ static void report_tfs(const double r[kRedSlots], double delta, int iters, tvs_r
 static void report_irv1(const double r[kRedSlots], double alpha, int iters, tvs_report* rep) {
     const double tv = r[0] / alpha;
     const double e = tv + r[3] / (2.0 * alpha);
-    const double gap = (r[0] - r[1]) / alpha;
+    const double gap = r[1] / alpha;
     rep->iters = iters;
     rep->dual_D = r[2];
     rep->primal_E = e;
@@ -153,6 +158,18 @@ static cudaError_t from_pitched(float* dst, const float* src, int spitch, int ro
                                cudaStream_t s) {
     return cudaMemcpy2DAsync(dst, (size_t)cols * sizeof(float), src, (size_t)spitch * sizeof(float),
                              (size_t)cols * sizeof(float), (size_t)rows * planes, cudaMemcpyDeviceToDevice, s);
+}
+// The caller's dense float dual into / out of the step-2 state (any storage).
+static cudaError_t p2_in(const Step2Layout& L, const float* src, cudaStream_t s) {
+    if (L.st == TVS_F32) return to_pitched(static_cast<float*>(L.pa), L.P, src, L.R, L.C, 2, s);
+    return convert_planes(L.pa, L.st, L.P, L.plane, src, TVS_F32, L.C, (long)L.R * L.C, L.R, L.C, 2, s);
+}
+static cudaError_t p2_out(const Step2Layout& L, float* dst, const void* cur, cudaStream_t s) {
+    if (L.st == TVS_F32) return from_pitched(dst, static_cast<const float*>(cur), L.P, L.R, L.C, 2, s);
+    return convert_planes(dst, TVS_F32, L.C, (long)L.R * L.C, cur, L.st, L.P, L.plane, L.R, L.C, 2, s);
+}
+static cudaError_t p2_zero(const Step2Layout& L, cudaStream_t s) {
+    return cudaMemsetAsync(L.pa, 0, 2 * (size_t)L.plane * storage_bytes(L.st), s);
 }
 
 // ---------------------------------------------------------------------------
@@ -219,10 +236,10 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
                            tvs_report* rep) {
     const int R = n2 + 1, C = n1 + 1;
     TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P, s));
-    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 2, s));
-    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 2 * (size_t)L.plane * sizeof(float), s));
-    float* cur = L.pa;
-    float* nxt = L.pb;
+    if (p_user) TVS_CUDA(p2_in(L, p_user, s));
+    else TVS_CUDA(p2_zero(L, s));
+    void* cur = L.pa;
+    void* nxt = L.pb;
     const int nb = irv1_blocks(L.R, L.C);
     const bool check_loop = it.rel_gap_tol > 0.0 && it.check_every > 0;
     const float t = (float)it.t, fa = (float)alpha;
@@ -233,7 +250,7 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
         TVS_CUDA(launch_irv1_update(cur, nxt, L.f2, L.R, L.C, L.P, L.plane, t, fa, ck, true, nullptr, 0,
-                                    L.red.partial, s));
+                                    L.red.partial, L.st, s));
         std::swap(cur, nxt);
         ++n;
         if (ck) {
@@ -248,24 +265,24 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
         }
     }
     TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, d, n1,
-                                L.red.partial, s));
+                                L.red.partial, L.st, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;
     report_irv1(r, alpha, n, &fin);
     if (rep) *rep = fin;
-    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 2, s));
+    if (p_user) TVS_CUDA(p2_out(L, p_user, cur, s));
     if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
     return TVS_OK;
 }
 
 static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1, double alpha,
                                const tvs_iter& it, float* d, float* p_user, cudaStream_t s, tvs_report* rep) {
-    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 2, s));
-    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 2 * (size_t)L.plane * sizeof(float), s));
+    if (p_user) TVS_CUDA(p2_in(L, p_user, s));
+    else TVS_CUDA(p2_zero(L, s));
     TVS_CUDA(schwarz2_reset(S2, s));
-    float* cur = L.pa;
-    float* nxt = L.pb;
+    void* cur = L.pa;
+    void* nxt = L.pb;
     const int nb = irv1_blocks(L.R, L.C);
     const bool check_loop = it.rel_gap_tol > 0.0 && it.check_every > 0;
     const float t = (float)it.t, fa = (float)alpha;
@@ -280,7 +297,7 @@ static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, 
         n += step;
         if (check_loop && n < it.max_iter) {
             TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, nullptr, 0,
-                                        L.red.partial, s));
+                                        L.red.partial, L.st, s));
             st = read_result(L.red, nb, s, r);
             if (st != TVS_OK) return st;
             tvs_report tmp;
@@ -292,13 +309,13 @@ static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, 
         }
     }
     TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, d, n1,
-                                L.red.partial, s));
+                                L.red.partial, L.st, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;
     report_irv1(r, alpha, n, &fin);
     if (rep) *rep = fin;
-    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 2, s));
+    if (p_user) TVS_CUDA(p2_out(L, p_user, cur, s));
     if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
     return TVS_OK;
 }
@@ -375,7 +392,8 @@ const char* tvs_status_string(tvs_status st) {
 const char* tvs_last_error(void) { return g_last_error.c_str(); }
 
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage) {
-    if (storage != TVS_F32) return 0;
+    if (storage_bytes(storage) == 0) return 0;
+    if (storage != TVS_F32 && (step == 1 || step == 3)) return 0;   // step 1 keeps an FP32 dual
     Carver cv(nullptr);
     if (step == 3) {
         if (n2 < 2 || n1 < 2 || n2 + 1 > kMaxSide + 1 || n1 + 1 > kMaxSide + 1) return 0;
@@ -394,8 +412,8 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
     }
     if (step == 2) {
         Step2Layout L;
-        size_t b = layout_step2(cv, n2, n1, L);
-        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L.P);
+        size_t b = layout_step2(cv, n2, n1, L, storage);
+        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L.P, storage);
         return b;
     }
     if (step == 0) {
@@ -403,8 +421,8 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
         layout_step1(cv, n2, n1, L1);
         cv.take<float>(2 * (size_t)(n2 + 1) * (n1 + 1));
         Step2Layout L2;
-        size_t b = layout_step2(cv, n2, n1, L2);
-        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L2.P);
+        size_t b = layout_step2(cv, n2, n1, L2, storage);
+        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L2.P, storage);
         return b;
     }
     return 0;
@@ -431,7 +449,7 @@ tvs_status tvs_project(const float* in, float* out, int rows, int cols, void* ws
 tvs_status tvs_step1(const float* d0, int n2, int n1, double delta, const tvs_iter* it, float* tau, float* p,
                      void* ws, size_t ws_bytes, cudaStream_t stream, tvs_report* rep) {
     if (!d0 || !tau || !side_ok(n2) || !side_ok(n1) || !(delta > 0.0)) return TVS_ERR_ARG;
-    tvs_status st = check_iter(it);
+    tvs_status st = check_iter(it, false);
     if (st != TVS_OK) return st;
     Carver cv0(nullptr);
     Step1Layout L;
@@ -446,14 +464,14 @@ tvs_status tvs_step2(const float* d0, const float* tau, int n2, int n1, double a
                      const tvs_iter* it, float* d, float* p, void* ws, size_t ws_bytes, cudaStream_t stream,
                      tvs_report* rep) {
     if (!d0 || !tau || !d || !side_ok(n2) || !side_ok(n1) || !(alpha > 0.0) || !(eps > 0.0)) return TVS_ERR_ARG;
-    tvs_status st = check_iter(it);
+    tvs_status st = check_iter(it, true);
     if (st != TVS_OK) return st;
     Carver cv0(nullptr);
     Step2Layout L;
-    st = check_ws(ws, ws_bytes, layout_step2(cv0, n2, n1, L));
+    st = check_ws(ws, ws_bytes, layout_step2(cv0, n2, n1, L, it->storage));
     if (st != TVS_OK) return st;
     Carver cv(ws);
-    layout_step2(cv, n2, n1, L);
+    layout_step2(cv, n2, n1, L, it->storage);
     return run_irv1(L, d0, tau, n2, n1, alpha, eps, *it, d, p, stream, rep);
 }
 
@@ -462,7 +480,7 @@ tvs_status tvs_schwarz(int step, const float* d0, const float* tau, int n2, int 
                        size_t ws_bytes, cudaStream_t stream, tvs_report* rep) {
     if (step == 1) {
         if (!dd || !d0 || !out || !side_ok(n2) || !side_ok(n1) || !(weight > 0.0)) return TVS_ERR_ARG;
-        tvs_status st = check_iter(outer);
+        tvs_status st = check_iter(outer, false);
         if (st != TVS_OK) return st;
         st = schwarz1_check(n2, n1, *dd);
         if (st != TVS_OK) return st;
@@ -478,19 +496,19 @@ tvs_status tvs_schwarz(int step, const float* d0, const float* tau, int n2, int 
     if (step != 2 || !dd || !d0 || !tau || !out || !side_ok(n2) || !side_ok(n1) || !(weight > 0.0) ||
         !(eps > 0.0))
         return TVS_ERR_ARG;
-    tvs_status st = check_iter(outer);
+    tvs_status st = check_iter(outer, true);
     if (st != TVS_OK) return st;
     st = schwarz2_check(n2, n1, *dd);
     if (st != TVS_OK) return st;
     Carver cv0(nullptr);
     Step2Layout L;
-    layout_step2(cv0, n2, n1, L);
-    st = check_ws(ws, ws_bytes, schwarz2_extend(cv0, n2, n1, *dd, L.P));
+    layout_step2(cv0, n2, n1, L, outer->storage);
+    st = check_ws(ws, ws_bytes, schwarz2_extend(cv0, n2, n1, *dd, L.P, outer->storage));
     if (st != TVS_OK) return st;
     Carver cv(ws);
-    layout_step2(cv, n2, n1, L);
+    layout_step2(cv, n2, n1, L, outer->storage);
     Schwarz2State S2;
-    schwarz2_carve(cv, n2, n1, *dd, L.P, S2);
+    schwarz2_carve(cv, n2, n1, *dd, L.P, outer->storage, S2);
     const int R = n2 + 1, C = n1 + 1;
     TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)weight, (float)eps, L.f2, L.P, stream));
     return run_schwarz2(L, S2, n2, n1, weight, *outer, out, p, stream, rep);
@@ -501,15 +519,15 @@ tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alp
                        cudaStream_t stream, tvs_report* rep) {
     if (!d0 || !d || !side_ok(n2) || !side_ok(n1) || !(delta > 0.0) || !(alpha > 0.0) || !(eps > 0.0))
         return TVS_ERR_ARG;
-    tvs_status st = check_iter(it1);
+    tvs_status st = check_iter(it1, false);
     if (st != TVS_OK) return st;
-    st = check_iter(it2);
+    st = check_iter(it2, true);
     if (st != TVS_OK) return st;
     if (dd2) {
         st = schwarz2_check(n2, n1, *dd2);
         if (st != TVS_OK) return st;
     }
-    const size_t need = tvs_workspace_bytes(0, n2, n1, dd2, TVS_F32);
+    const size_t need = tvs_workspace_bytes(0, n2, n1, dd2, it2->storage);
     st = check_ws(ws, ws_bytes, need);
     if (st != TVS_OK) return st;
     Carver cv(ws);
@@ -518,7 +536,7 @@ tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alp
     float* tau_ws = cv.take<float>(2 * (size_t)(n2 + 1) * (n1 + 1));
     float* tau_use = tau ? tau : tau_ws;
     Step2Layout L2;
-    layout_step2(cv, n2, n1, L2);
+    layout_step2(cv, n2, n1, L2, it2->storage);
     tvs_report r1{}, r2{};
     tvs_status s1 = run_tfs(L1, d0, n2, n1, delta, *it1, tau_use, n1 + 1, (long)(n2 + 1) * (n1 + 1), nullptr,
                             stream, &r1);
@@ -526,7 +544,7 @@ tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alp
     tvs_status s2;
     if (dd2) {
         Schwarz2State S2;
-        schwarz2_carve(cv, n2, n1, *dd2, L2.P, S2);
+        schwarz2_carve(cv, n2, n1, *dd2, L2.P, it2->storage, S2);
         const int R = n2 + 1, C = n1 + 1;
         TVS_CUDA(launch_xi_f2(d0, n1, tau_use, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L2.f2, L2.P,
                               stream));

@@ -13,7 +13,11 @@
 struct Axis {
     int N, M, s;   // image pixels on the axis, subdomains, overlap
     int L;         // grid points on the axis (N, or N + 1 for the extended grid)
-    __host__ __device__ __forceinline__ int core(int k) const { return (int)(((long long)k * N) / M); }
+    __host__ __device__ __forceinline__ int core(int k) const {
+        // k <= M <= N < 2^16 keeps k N in 32 bits; wider axes take the 64-bit path
+        if (N < 65536) return (int)(((unsigned)k * (unsigned)N) / (unsigned)M);
+        return (int)(((long long)k * N) / M);
+    }
     __host__ __device__ __forceinline__ int start(int k) const { return k == 0 ? 0 : core(k) - (s + 1) / 2; }
     __host__ __device__ __forceinline__ int end(int k) const { return k == M - 1 ? L : core(k + 1) + s / 2; }
     // theta of part k at grid point x (x inside [start(k), end(k)))

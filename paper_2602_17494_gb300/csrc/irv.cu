@@ -64,17 +64,13 @@ constexpr int kStreamWarps = 4;  // warps per block
 struct Row4 {
     float4 px, py, f;
 };
-
-__device__ __forceinline__ float4 ld4(const float* __restrict__ a, size_t o) {
-    return __ldg(reinterpret_cast<const float4*>(a + o));
-}
 __device__ __forceinline__ float comp(const float4& v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
-template <bool CHECK, bool WRITE_P, bool WRITE_D>
-__global__ void __launch_bounds__(32 * kStreamWarps, 8)
-irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, const float* __restrict__ f2, int R,
+template <class S, bool CHECK, bool WRITE_P, bool WRITE_D>
+__global__ void __launch_bounds__(32 * kStreamWarps, CHECK ? 5 : 8)
+irv1_stream_kernel(const S* __restrict__ pin, S* __restrict__ pout, const float* __restrict__ f2, int R,
                    int C, int pitch, long plane, float t, float alpha_inv, float* __restrict__ d_out, int d_pitch,
                    double* __restrict__ partial) {
     const int lane = threadIdx.x & 31;
@@ -84,11 +80,11 @@ irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, cons
     const int r0 = chunk * kChunk;
     const int j0 = strip * kStrip + 4 * lane;     // first column of this lane
     const int r1 = min(r0 + kChunk, R);           // output rows [r0, r1)
-    const float* __restrict__ px = pin;
-    const float* __restrict__ py = pin + plane;
-    double acc[kRedSlots];
-#pragma unroll
-    for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+    using St = Stor<S>;
+    const S* __restrict__ px = pin;
+    const S* __restrict__ py = pin + plane;
+    KSum ks[4];
+    float pmax = 0.0f;
 
     if (r0 < R) {
         const int jr = strip * kStrip + kStrip;   // first column right of the strip
@@ -104,21 +100,21 @@ irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, cons
         float4 pyu = make_float4(0.f, 0.f, 0.f, 0.f);
         float pyu_r = 0.f;                         // p_y(r0 - 1, jr) for the right halo (lane 31)
         if (r0 >= 1 && r0 - 1 <= R - 2) {
-            pyu = ld4(py, (size_t)(r0 - 1) * pitch + cbase);
-            if (lane == 31 && jr < C) pyu_r = __ldg(&py[(size_t)(r0 - 1) * pitch + jr]);
+            pyu = St::ld4(py + (size_t)(r0 - 1) * pitch + cbase);
+            if (lane == 31 && jr < C) pyu_r = St::ld1(py + (size_t)(r0 - 1) * pitch + jr);
         }
         auto load_row = [&](int i, Row4& rw, float& pxl, float& pxr, float& pyr, float& fr) {
             const size_t o = (size_t)i * pitch + cbase;
-            rw.px = ld4(px, o);
-            rw.py = ld4(py, o);
-            rw.f = ld4(f2, o);
-            pxl = (lane == 0 && j0 >= 1) ? __ldg(&px[(size_t)i * pitch + j0 - 1]) : 0.f;
+            rw.px = St::ld4(px + o);
+            rw.py = St::ld4(py + o);
+            rw.f = Stor<float>::ld4(f2 + o);
+            pxl = (lane == 0 && j0 >= 1) ? St::ld1(px + (size_t)i * pitch + j0 - 1) : 0.f;
             pxr = 0.f;
             pyr = 0.f;
             fr = 0.f;
             if (lane == 31 && jr < C) {
-                pxr = __ldg(&px[(size_t)i * pitch + jr]);
-                pyr = __ldg(&py[(size_t)i * pitch + jr]);
+                pxr = St::ld1(px + (size_t)i * pitch + jr);
+                pyr = St::ld1(py + (size_t)i * pitch + jr);
                 fr = __ldg(&f2[(size_t)i * pitch + jr]);
             }
         };
@@ -179,26 +175,24 @@ irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, cons
                         res_y[e] = (pyv + t * gy) / den;
                     }
                     if (CHECK && j0 + e < C) {
-                        const double dgx = gx, dgy = gy, dpx = pxv, dpy = pyv;
-                        acc[0] += sqrt(dgx * dgx + dgy * dgy);
-                        acc[1] += dgx * dpx + dgy * dpy;
-                        acc[2] += (double)zp[e] * (double)zp[e];
-                        // div p = z + f2 at (ir, j): recover from z and the stored f2 of row ir
-                        acc[4] = fmax(acc[4], sqrt(dpx * dpx + dpy * dpy));
+                        const float ng = sqrtf(gx * gx + gy * gy);
+                        ks[0].add(ng);
+                        ks[1].add(ng - (gx * pxv + gy * pyv));
+                        ks[2].add(zp[e] * zp[e]);
+                        pmax = fmaxf(pmax, sqrtf(pxv * pxv + pyv * pyv));
                     }
                 }
                 if (WRITE_P) {
                     const size_t o = (size_t)ir * pitch + cbase;
                     if (j0 + 3 < C) {
-                        *reinterpret_cast<float4*>(pout + o) = make_float4(res_x[0], res_x[1], res_x[2], res_x[3]);
-                        *reinterpret_cast<float4*>(pout + plane + o) =
-                            make_float4(res_y[0], res_y[1], res_y[2], res_y[3]);
+                        St::st4(pout + o, make_float4(res_x[0], res_x[1], res_x[2], res_x[3]));
+                        St::st4(pout + plane + o, make_float4(res_y[0], res_y[1], res_y[2], res_y[3]));
                     } else {
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             if (j0 + e < C) {
-                                pout[o + e] = res_x[e];
-                                pout[plane + o + e] = res_y[e];
+                                St::st1(pout + o + e, res_x[e]);
+                                St::st1(pout + plane + o + e, res_y[e]);
                             }
                     }
                 }
@@ -208,8 +202,8 @@ irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, cons
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     if (j0 + e < C) {
-                        const double dv = (double)zc[e] + (double)fv[e];
-                        acc[3] += dv * dv;
+                        const float dv = zc[e] + fv[e];   // div p
+                        ks[3].add(dv * dv);
                     }
             }
             // rotate
@@ -228,6 +222,9 @@ irv1_stream_kernel(const float* __restrict__ pin, float* __restrict__ pout, cons
         }
     }
     if (CHECK) {
+        double acc[kRedSlots];
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) acc[k] = k < 4 ? ks[k].value() : (k == 4 ? (double)pmax : 0.0);
         // deterministic warp reduction, one partial per warp
 #pragma unroll
         for (int k = 0; k < kRedSlots; ++k) {
@@ -257,24 +254,54 @@ int irv1_blocks(int R, int C) {
     return strips * ((chunks + kStreamWarps - 1) / kStreamWarps) * kStreamWarps;
 }
 
-cudaError_t launch_irv1_update(const float* pin, float* pout, const float* f2, int R, int C, int pitch,
+cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int R, int C, int pitch,
                                long plane, float t, float alpha, bool check, bool write_p,
-                               float* d_out, int d_pitch, double* partial, cudaStream_t s) {
+                               float* d_out, int d_pitch, double* partial, int storage, cudaStream_t s) {
     const int strips = (C + kStrip - 1) / kStrip;
     const int chunks = (R + kChunk - 1) / kChunk;
     dim3 blk(32 * kStreamWarps), grd(strips, (chunks + kStreamWarps - 1) / kStreamWarps);
     const float ainv = 1.0f / alpha;
     const bool wd = d_out != nullptr;
     ProfScope ps((check || !write_p) ? kProfIrv1Check : kProfIrv1Update, s);
-#define TVS_IRV1(CK, WP, WD) \
-    irv1_stream_kernel<CK, WP, WD><<<grd, blk, 0, s>>>(pin, pout, f2, R, C, pitch, plane, t, ainv, d_out, d_pitch, partial)
-    if (!check && write_p && !wd) TVS_IRV1(false, true, false);
-    else if (check && write_p && !wd) TVS_IRV1(true, true, false);
-    else if (check && !write_p && wd) TVS_IRV1(true, false, true);
-    else if (check && !write_p && !wd) TVS_IRV1(true, false, false);
-    else if (!check && !write_p && wd) TVS_IRV1(false, false, true);
-    else TVS_IRV1(true, true, true);
+#define TVS_IRV1(CK, WP, WD)                                                                              \
+    irv1_stream_kernel<S, CK, WP, WD><<<grd, blk, 0, s>>>(static_cast<const S*>(pin), static_cast<S*>(pout), f2, R, \
+                                                          C, pitch, plane, t, ainv, d_out, d_pitch, partial)
+    TVS_STORAGE_SWITCH(storage, {
+        if (!check && write_p && !wd) TVS_IRV1(false, true, false);
+        else if (check && write_p && !wd) TVS_IRV1(true, true, false);
+        else if (check && !write_p && wd) TVS_IRV1(true, false, true);
+        else if (check && !write_p && !wd) TVS_IRV1(true, false, false);
+        else if (!check && !write_p && wd) TVS_IRV1(false, false, true);
+        else TVS_IRV1(true, true, true);
+    })
 #undef TVS_IRV1
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plane copies between layouts and storage formats (dense or pitched; float,
+// bf16 or fp16), rounding to nearest when narrowing.  blockIdx.z = plane.
+// ---------------------------------------------------------------------------
+template <class SD, class SS>
+__global__ void convert_planes_kernel(SD* __restrict__ dst, int dpitch, long dplane, const SS* __restrict__ src,
+                                      int spitch, long splane, int rows, int cols) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= rows || j >= cols) return;
+    const float v = Stor<SS>::ld1(src + (size_t)blockIdx.z * splane + (size_t)i * spitch + j);
+    Stor<SD>::st1(dst + (size_t)blockIdx.z * dplane + (size_t)i * dpitch + j, v);
+}
+
+cudaError_t convert_planes(void* dst, int dst_storage, int dpitch, long dplane, const void* src, int src_storage,
+                           int spitch, long splane, int rows, int cols, int planes, cudaStream_t s) {
+    const dim3 blk(32, 8), grd((cols + 31) / 32, (rows + 7) / 8, planes);
+    TVS_STORAGE_SWITCH(dst_storage, {
+        using SD = S;
+        TVS_STORAGE_SWITCH(src_storage, {
+            convert_planes_kernel<SD, S><<<grd, blk, 0, s>>>(static_cast<SD*>(dst), dpitch, dplane,
+                                                             static_cast<const S*>(src), spitch, splane, rows, cols);
+        })
+    })
     return cudaGetLastError();
 }
 

@@ -27,28 +27,36 @@ inline cudaError_t tfs_phi(const float* p, float* S, int R, int C, int pitch, lo
 // irv.cu
 cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long tplane, int tpitch, int R, int C,
                          float alpha, float eps, float* f2, int fpitch, cudaStream_t s);
-cudaError_t launch_irv1_update(const float* pin, float* pout, const float* f2, int R, int C, int pitch, long plane,
+// p (pin, pout) is stored as `storage` (tvs_storage); everything else is float.
+cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int R, int C, int pitch, long plane,
                                float t, float alpha, bool check, bool write_p, float* d_out, int d_pitch,
-                               double* partial, cudaStream_t s);
+                               double* partial, int storage, cudaStream_t s);
 int irv1_blocks(int R, int C);
+// Copy `planes` planes of rows x cols between layouts and storage formats
+// (element pitches and plane strides in elements of each side's format).
+cudaError_t convert_planes(void* dst, int dst_storage, int dpitch, long dplane, const void* src, int src_storage,
+                           int spitch, long splane, int rows, int cols, int planes, cudaStream_t s);
 
 // schwarz.cu -- Algorithm 2 with Algorithm 3 for IRV1 on the image grid
 struct Schwarz2State {
     int m2, m1, s, k;
     double alpha_hat;
-    int hmax, wmax, wpad;   // largest subdomain extent, padded width of q storage
-    int ncl, band;          // CTAs per subdomain (cluster size) and rows per CTA
+    int hmax, wmax, wpad;   // largest subdomain extent, padded shared-memory row of the cluster kernel
+    int qp;                 // row pitch of q; a subdomain's row starts at column start & ~3
+    int small, tx, ty;      // whole subdomain in one CTA of tx x ty threads (4 x 4 pixels each)
+    int ncl, band;          // otherwise: CTAs per subdomain (cluster size) and rows per CTA
     size_t smem;            // dynamic shared memory per CTA
-    float* q;               // per-subdomain warm starts, [m2*m1][2][hmax][wpad]
+    int stor;               // tvs_storage of p and q
+    void* q;                // per-subdomain warm starts, [m2*m1][2][hmax][qp]
 };
 tvs_status schwarz2_check(int n2, int n1, const tvs_decomp& dd);
-size_t schwarz2_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch);
-void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, Schwarz2State& st);
+size_t schwarz2_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, int storage);
+void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, int storage, Schwarz2State& st);
 // Zero the warm starts q_m (Algorithm 3 starts every subdomain from 0).
 cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s);
 // n_outer outer iterations of Algorithm 2: p^{n+1} from p^n = *cur, swapping
 // *cur and *nxt after each iteration.
-cudaError_t schwarz2_iterate(float** cur, float** nxt, const float* f2, int pitch, long plane, int n2, int n1,
+cudaError_t schwarz2_iterate(void** cur, void** nxt, const float* f2, int pitch, long plane, int n2, int n1,
                              const Schwarz2State& st, float t, int n_outer, cudaStream_t s);
 
 // schwarz1.cu -- Algorithm 2 with the localized Algorithm 5 for TFS on the extended grid

@@ -2,13 +2,18 @@
 // Algorithm 2 (outer, additive with damping alpha_hat) with Algorithm 3
 // (inner Chambolle iteration on one subdomain), Lambda = div, f = f2.
 //
-// GB300 mapping: one subdomain is one thread-block cluster; each CTA of the
-// cluster keeps a horizontal band of the subdomain's inner dual v, the frozen
-// data g_m = f2 - div((1 - theta_m) p^n) and the residual z in shared memory
-// and runs all k inner updates on chip.  Rows next to a band boundary are read
-// from the neighbouring CTA through distributed shared memory.  The outer
-// combine p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum_l q_l goes through HBM
-// between launches -- that is the grid-wide halo exchange.
+// GB300 mapping: every subdomain runs all k inner updates on chip.
+//   * Small subdomains (up to about 88 x 88 pixels with the overlap, e.g. the
+//     64 x 64 tiles of a large image) are one CTA each: a thread holds a 4 x 4
+//     block of the inner dual v, the frozen data g_m = f2 - div((1 - theta_m)
+//     p^n) and the residual z in registers, and only the block edges go
+//     through shared memory (two barriers per inner update).
+//   * Larger subdomains are one thread-block cluster each; every CTA keeps a
+//     horizontal band of v, g_m and z in shared memory, and rows next to a band
+//     boundary are read from the neighbouring CTA through distributed shared
+//     memory.
+// The outer combine p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum_l q_l goes
+// through HBM between launches -- that is the grid-wide halo exchange.
 //
 // Decomposition (same reading as the oracle): cores split each axis as
 // evenly as integers allow, core k = [floor(kN/M), floor((k+1)N/M)); two
@@ -31,13 +36,14 @@ namespace tvs {
 constexpr int kSchwarzThreads = 512;
 constexpr size_t kSchwarzSmemMax = 200 * 1024;
 
+template <class S>
 struct TileArgs {
-    const float* p;   // p^n, 2 planes
+    const S* p;       // p^n, 2 planes
     const float* f2;
     int pitch;
     long plane;
-    float* q;         // [sub][2][hmax][wpad]
-    int hmax, wpad;
+    S* q;             // [sub][2][hmax][qp], columns from start & ~3
+    int hmax, wpad, qp;
     Axis ay, ax;
     int band, k;
     float t;
@@ -54,8 +60,10 @@ __host__ __device__ __forceinline__ size_t tile_smem_floats(int band, int wpad) 
     return (size_t)2 * (band + 2) * wpad + (size_t)2 * (band + 1) * wpad + wpad + band + 1 + (size_t)6 * wpad;
 }
 
+template <class S>
 __global__ void __launch_bounds__(kSchwarzThreads)
-schwarz2_tile_kernel(TileArgs a) {
+schwarz2_tile_kernel(TileArgs<S> a) {
+    using St = Stor<S>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float sm[];
     const int WP = a.wpad, B = a.band;
@@ -83,10 +91,10 @@ schwarz2_tile_kernel(TileArgs a) {
     // z rows: own rows plus the next row when it exists in Gamma_{m,+}
     const int zrows = nown + ((nown > 0 && r_hi < N2) ? 1 : 0);
     const int zcols = w + (x1 < N1 ? 1 : 0);
-    const float* __restrict__ px = a.p;
-    const float* __restrict__ py = a.p + a.plane;
-    float* qx = a.q + (size_t)sub * 2 * a.hmax * WP;
-    float* qy = qx + (size_t)a.hmax * WP;
+    const S* __restrict__ px = a.p;
+    const S* __restrict__ py = a.p + a.plane;
+    S* qx = a.q + (size_t)sub * 2 * a.hmax * a.qp + (x0 & 3);   // q column of pixel x0 + c: c + (x0 & 3)
+    S* qy = qx + (size_t)a.hmax * a.qp;
     const float t = a.t;
     const int nt = blockDim.x;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nwy = blockDim.x >> 5;
@@ -101,9 +109,9 @@ schwarz2_tile_kernel(TileArgs a) {
         const int r = idx / WP - 1, c = idx - (idx / WP) * WP;
         float ux = 0.0f, uy = 0.0f;
         if (r >= 0 && r < nown && c < w) {
-            const size_t qo = (size_t)(r_lo - y0 + r) * WP + c;
-            ux = qx[qo];
-            uy = qy[qo];
+            const size_t qo = (size_t)(r_lo - y0 + r) * a.qp + c;
+            ux = St::ld1c(qx + qo);
+            uy = St::ld1c(qy + qo);
         }
         vx[idx] = ux;
         vy[idx] = uy;
@@ -115,12 +123,12 @@ schwarz2_tile_kernel(TileArgs a) {
         auto wx = [&](int ii, int jj) -> float {
             if (jj < 0 || jj > N1 - 2) return 0.0f;
             const float th = a.ay.theta_or0(my, ii) * a.ax.theta_or0(mx, jj);
-            return (1.0f - th) * __ldg(&px[(size_t)ii * a.pitch + jj]);
+            return (1.0f - th) * St::ld1(px + (size_t)ii * a.pitch + jj);
         };
         auto wy = [&](int ii, int jj) -> float {
             if (ii < 0 || ii > N2 - 2) return 0.0f;
             const float th = a.ay.theta_or0(my, ii) * a.ax.theta_or0(mx, jj);
-            return (1.0f - th) * __ldg(&py[(size_t)ii * a.pitch + jj]);
+            return (1.0f - th) * St::ld1(py + (size_t)ii * a.pitch + jj);
         };
         const float divw = (wx(i, j) - wx(i, j - 1)) + (wy(i, j) - wy(i - 1, j));
         g[(size_t)r * WP + c] = __ldg(&a.f2[(size_t)i * a.pitch + j]) - divw;
@@ -197,35 +205,400 @@ schwarz2_tile_kernel(TileArgs a) {
     // ---- store the new warm start q_m ------------------------------------
     for (int idx = threadIdx.x; idx < nown * w; idx += nt) {
         const int r = idx / w, c = idx - r * w;
-        const size_t qo = (size_t)(r_lo - y0 + r) * WP + c;
-        qx[qo] = vx[(size_t)(r + 1) * WP + c];
-        qy[qo] = vy[(size_t)(r + 1) * WP + c];
+        const size_t qo = (size_t)(r_lo - y0 + r) * a.qp + c;
+        St::st1(qx + qo, vx[(size_t)(r + 1) * WP + c]);
+        St::st1(qy + qo, vy[(size_t)(r + 1) * WP + c]);
     }
     cl.sync();   // no CTA leaves while a neighbour could still address its shared memory
 }
 
-// p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum over subdomains containing x of q_l(x)
-__global__ void schwarz2_combine_kernel(const float* __restrict__ pin, float* __restrict__ pout,
-                                        const float* __restrict__ q, int pitch, long plane, Axis ay, Axis ax,
-                                        int hmax, int wpad, float ah) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= ay.L || j >= ax.L) return;
-    const int ky = ay.core_of(i), kx = ax.core_of(j);
-    float sx = 0.0f, sy = 0.0f;
-    for (int a = ky - 1; a <= ky + 1; ++a) {
-        if (a < 0 || a >= ay.M || i < ay.start(a) || i >= ay.end(a)) continue;
-        for (int b = kx - 1; b <= kx + 1; ++b) {
-            if (b < 0 || b >= ax.M || j < ax.start(b) || j >= ax.end(b)) continue;
-            const int sub = a * ax.M + b;
-            const size_t off = ((size_t)sub * 2 * hmax + (i - ay.start(a))) * wpad + (j - ax.start(b));
-            sx += q[off];
-            sy += q[off + (size_t)hmax * wpad];
+// ---------------------------------------------------------------------------
+// Small subdomains: one CTA per subdomain, 4 x 4 pixels per thread
+// ---------------------------------------------------------------------------
+constexpr int kSmallRH = 4;              // rows per thread
+constexpr int kSmallCW = 4;              // columns per thread (one float4 of q)
+constexpr int kSmallMaxThreads = 512;    // larger subdomains use the cluster kernel
+constexpr int kSmallPairThreads = 336;   // up to this many threads two CTAs share an SM
+
+template <class S>
+struct SmallTileArgs {
+    const S* p;       // p^n, 2 planes
+    S* pnext;         // p^{n+1}, written on the exclusive part of the core
+    const float* f2;
+    int pitch;
+    long plane;
+    S* q;             // [sub][2][hmax][qp], columns from start & ~3
+    int hmax, qp;
+    Axis ay, ax;
+    int k;
+    float t, ahat;
+};
+
+// Rows of core k that no other subdomain's Gamma reaches: [excl_lo, excl_hi).
+__host__ __device__ __forceinline__ int excl_lo(const Axis& A, int k) { return k == 0 ? 0 : A.core(k) + A.s / 2; }
+__host__ __device__ __forceinline__ int excl_hi(const Axis& A, int k) {
+    return k == A.M - 1 ? A.L : A.core(k + 1) - (A.s + 1) / 2;
+}
+
+// Thread (tx, ty) of subdomain m owns rows y0 + 4 ty + [0, 4) and columns
+// xa + 4 tx + [0, 4), xa = x0 & ~3, so that p, f2 and q move as aligned
+// float4.  The CTA covers Gamma_m plus the row below and the column right of
+// it, where the residual z is needed for the forward differences.
+//   set-up : p^n (kept in shared memory), f2 -> g_m = f2 - div((1 - theta) p^n);
+//            warm start v = q_m
+//   k times: publish v_x of the last column and v_y of the last row, barrier,
+//            z = div v - g_m; publish z of the first column and row, barrier,
+//            v <- (v + t psi) / (1 + (t / theta) |psi|), psi = grad z
+//            (= theta (v + t psi) / (theta + t |psi|) of Algorithm 3; v = 0
+//            outside Gamma_m)
+//   end    : q_m = v; on the part of the core that no other subdomain
+//            reaches, p^{n+1} = (1 - alpha_hat) p^n + alpha_hat q_m directly
+//            (the overlap strips are combined by schwarz2_strip_kernel).
+// Shared memory: p^n_x, p^n_y and g_m as float4 [4 ty + r][tx]; edge arrays
+// (floats) vedge_x [4 ty + r][tx], vedge_y [ty][c][tx], the same two for z;
+// theta_x and theta_y of the block's columns and rows.
+__host__ __device__ __forceinline__ size_t small_tile_smem_bytes(int tx, int ty) {
+    return ((size_t)ty * tx * (12 * kSmallRH + 2 * (kSmallRH + kSmallCW)) + kSmallCW * tx + kSmallRH * ty + 2) *
+           sizeof(float);
+}
+
+template <class S, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
+    using St = Stor<S>;
+    constexpr int RH = kSmallRH, CW = kSmallCW;
+    extern __shared__ float4 sm4[];
+    const int TX = blockDim.x, TY = blockDim.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int NB = TY * RH * TX;                  // float4 slots per array
+    float4* spx = sm4;                            // [TY * RH][TX]
+    float4* spy = spx + NB;
+    float4* gs = spy + NB;
+    float* evx = reinterpret_cast<float*>(gs + NB);   // [TY * RH][TX]
+    float* evy = evx + TY * RH * TX;                  // [TY][CW][TX]
+    float* ezx = evy + TY * CW * TX;                  // [TY * RH][TX]
+    float* ezy = ezx + TY * RH * TX;                  // [TY][CW][TX]
+    float* sthx = ezy + TY * CW * TX;             // theta_x of columns xa - 1 .. xa + 4 TX - 1
+    float* sthy = sthx + CW * TX + 1;             // theta_y of rows y0 - 1 .. y0 + 4 TY - 1
+
+    const int N2 = a.ay.N, N1 = a.ax.N;
+    const int sub = blockIdx.x;
+    const int my = sub / a.ax.M, mx = sub - my * a.ax.M;
+    const int y0 = a.ay.start(my), y1 = a.ay.end(my);
+    const int x0 = a.ax.start(mx), x1 = a.ax.end(mx);
+    const int xa = x0 & ~3;
+    const int ib = y0 + ty * RH, jb = xa + tx * CW;
+    const int zy1 = min(y1 + 1, N2), zx1 = min(x1 + 1, N1);   // z region: [y0, zy1) x [x0, zx1)
+    const float t = a.t;
+    {
+        const int tid = ty * TX + tx, nt = TX * TY;
+        for (int c = tid; c <= CW * TX; c += nt) {
+            const int j = xa - 1 + c;
+            sthx[c] = (j >= x0 && j < x1) ? a.ax.theta(mx, j) : 0.0f;
+        }
+        for (int r = tid; r <= RH * TY; r += nt) {
+            const int i = y0 - 1 + r;
+            sthy[r] = (i >= y0 && i < y1) ? a.ay.theta(my, i) : 0.0f;
         }
     }
-    const size_t o = (size_t)i * pitch + j;
-    pout[o] = (1.0f - ah) * pin[o] + ah * sx;
-    pout[plane + o] = (1.0f - ah) * pin[plane + o] + ah * sy;
+    __syncthreads();
+
+    float thy[RH], thx[CW];                       // theta factors, 0 outside Gamma_m
+#pragma unroll
+    for (int r = 0; r < RH; ++r) thy[r] = sthy[ty * RH + r + 1];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) thx[c] = sthx[tx * CW + c + 1];
+
+    // ---- p^n, frozen data g_m (shared memory) ----------------------------
+    {
+        const S* __restrict__ px = a.p;
+        const S* __restrict__ py = a.p + a.plane;
+        const bool vec = jb + CW <= N1;           // the thread's 4 columns lie inside the image
+        // (1 - theta_m) p^n with the D^- zero-extension rule
+        const float thxl = sthx[tx * CW];         // column left of the block
+        const float thyu = sthy[ty * RH];         // row above the block
+        float wyu[CW];                            // w_y of the row above
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const int i = ib - 1, j = jb + c;
+            wyu[c] = (i >= 0 && i <= N2 - 2 && j < N1)
+                         ? (1.0f - thyu * thx[c]) * St::ld1(py + (size_t)i * a.pitch + j) : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int i = ib + r;
+            const bool row_ok = i < zy1;
+            float vpx[CW] = {0.f, 0.f, 0.f, 0.f}, vpy[CW] = {0.f, 0.f, 0.f, 0.f}, vf[CW] = {0.f, 0.f, 0.f, 0.f};
+            if (row_ok) {
+                const size_t o = (size_t)i * a.pitch + jb;
+                if (vec) {
+                    const float4 u = St::ld4(px + o);
+                    const float4 w = St::ld4(py + o);
+                    const float4 f = __ldg(reinterpret_cast<const float4*>(a.f2 + o));
+                    vpx[0] = u.x; vpx[1] = u.y; vpx[2] = u.z; vpx[3] = u.w;
+                    vpy[0] = w.x; vpy[1] = w.y; vpy[2] = w.z; vpy[3] = w.w;
+                    vf[0] = f.x; vf[1] = f.y; vf[2] = f.z; vf[3] = f.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CW; ++c)
+                        if (jb + c < N1) {
+                            vpx[c] = St::ld1(px + o + c);
+                            vpy[c] = St::ld1(py + o + c);
+                            vf[c] = __ldg(a.f2 + o + c);
+                        }
+                }
+            }
+            spx[(ty * RH + r) * TX + tx] = make_float4(vpx[0], vpx[1], vpx[2], vpx[3]);
+            spy[(ty * RH + r) * TX + tx] = make_float4(vpy[0], vpy[1], vpy[2], vpy[3]);
+            float wl = 0.0f;
+            if (row_ok && jb >= 1 && jb - 1 <= N1 - 2)
+                wl = (1.0f - thy[r] * thxl) * St::ld1(px + (size_t)i * a.pitch + jb - 1);
+            float gr[CW];
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                const int j = jb + c;
+                float gv = 0.0f, wyc = 0.0f;
+                if (row_ok && j < N1) {
+                    const float th = thy[r] * thx[c];
+                    const float wxc = (j <= N1 - 2) ? (1.0f - th) * vpx[c] : 0.0f;
+                    wyc = (i <= N2 - 2) ? (1.0f - th) * vpy[c] : 0.0f;
+                    if (j >= x0 && j < zx1) gv = vf[c] - ((wxc - wl) + (wyc - wyu[c]));
+                    wl = wxc;
+                }
+                gr[c] = gv;
+                wyu[c] = wyc;
+            }
+            gs[(ty * RH + r) * TX + tx] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+        }
+    }
+
+    // ---- warm start q_m ---------------------------------------------------
+    float vx[RH][CW], vy[RH][CW];
+    S* qx = a.q + (size_t)sub * 2 * a.hmax * a.qp;
+    S* qy = qx + (size_t)a.hmax * a.qp;
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+        float4 ux = make_float4(0.f, 0.f, 0.f, 0.f), uy = ux;
+        if (ib + r < y1) {
+            const size_t qo = (size_t)(ib + r - y0) * a.qp + tx * CW;
+            ux = St::ld4c(qx + qo);
+            uy = St::ld4c(qy + qo);
+        }
+        const float ax4[CW] = {ux.x, ux.y, ux.z, ux.w}, ay4[CW] = {uy.x, uy.y, uy.z, uy.w};
+        // D^- reads v_x as zero in the last column and v_y in the last row;
+        // there the update keeps v at zero (psi has no component across the
+        // boundary), so zeroing them once lets div v skip the masks.
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const bool in = thy[r] > 0.0f && thx[c] > 0.0f;
+            vx[r][c] = (in && jb + c <= N1 - 2) ? ax4[c] : 0.0f;
+            vy[r][c] = (in && ib + r <= N2 - 2) ? ay4[c] : 0.0f;
+        }
+    }
+    // t / theta as a product of per-row and per-column factors (0 outside Gamma_m)
+    float try_[RH], rthx[CW];
+#pragma unroll
+    for (int r = 0; r < RH; ++r) try_[r] = thy[r] > 0.0f ? t / thy[r] : 0.0f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) rthx[c] = thx[c] > 0.0f ? 1.0f / thx[c] : 0.0f;
+
+    // ---- k inner updates on chip (Algorithm 3) --------------------------
+    for (int it = 0; it < a.k; ++it) {
+#pragma unroll
+        for (int r = 0; r < RH; ++r) evx[(ty * RH + r) * TX + tx] = vx[r][CW - 1];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) evy[(ty * CW + c) * TX + tx] = vy[RH - 1][c];
+        __syncthreads();
+        float z[RH][CW];
+        {
+            float vxl[RH], vyu[CW];
+#pragma unroll
+            for (int r = 0; r < RH; ++r) vxl[r] = tx > 0 ? evx[(ty * RH + r) * TX + tx - 1] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < CW; ++c) vyu[c] = ty > 0 ? evy[((ty - 1) * CW + c) * TX + tx] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < RH; ++r) {
+                const float4 g4 = gs[(ty * RH + r) * TX + tx];
+                const float gr[CW] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    const float left = c > 0 ? vx[r][c - 1] : vxl[r];
+                    const float up = r > 0 ? vy[r - 1][c] : vyu[c];
+                    // outside the z region z is never read by an update of Gamma_m
+                    z[r][c] = ((vx[r][c] - left) + (vy[r][c] - up)) - gr[c];
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RH; ++r) ezx[(ty * RH + r) * TX + tx] = z[r][0];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) ezy[(ty * CW + c) * TX + tx] = z[0][c];
+        __syncthreads();
+        {
+            float zr[RH], zd[CW];
+#pragma unroll
+            for (int r = 0; r < RH; ++r) zr[r] = tx + 1 < TX ? ezx[(ty * RH + r) * TX + tx + 1] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < CW; ++c) zd[c] = ty + 1 < TY ? ezy[((ty + 1) * CW + c) * TX + tx] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < RH; ++r)
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    const float zc = z[r][c];
+                    const float right = c + 1 < CW ? z[r][c + 1] : zr[r];
+                    const float down = r + 1 < RH ? z[r + 1][c] : zd[c];
+                    const float gx = (jb + c < N1 - 1) ? right - zc : 0.0f;   // D^+ zero at the last column
+                    const float gy = (ib + r < N2 - 1) ? down - zc : 0.0f;    // and the last row
+                    const float s2 = gx * gx + gy * gy;
+                    const float ng = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;     // |psi|
+                    const float inv = __fdividef(1.0f, fmaf(try_[r] * rthx[c], ng, 1.0f));
+                    if (try_[r] > 0.0f && rthx[c] > 0.0f) {
+                        vx[r][c] = fmaf(t, gx, vx[r][c]) * inv;
+                        vy[r][c] = fmaf(t, gy, vy[r][c]) * inv;
+                    }
+                }
+        }
+    }
+
+    // ---- new warm start q_m; p^{n+1} on the exclusive core -----------------
+#pragma unroll
+    for (int r = 0; r < RH; ++r)
+        if (ib + r < y1) {
+            const size_t qo = (size_t)(ib + r - y0) * a.qp + tx * CW;
+            St::st4(qx + qo, make_float4(vx[r][0], vx[r][1], vx[r][2], vx[r][3]));
+            St::st4(qy + qo, make_float4(vy[r][0], vy[r][1], vy[r][2], vy[r][3]));
+        }
+    const int ey0 = excl_lo(a.ay, my), ey1 = excl_hi(a.ay, my);
+    const int ex0 = excl_lo(a.ax, mx), ex1 = excl_hi(a.ax, mx);
+    const float ah = a.ahat, bh = 1.0f - a.ahat;
+    S* __restrict__ nx = a.pnext;
+    S* __restrict__ ny = a.pnext + a.plane;
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+        const int i = ib + r;
+        if (i < ey0 || i >= ey1) continue;
+        const float4 u = spx[(ty * RH + r) * TX + tx], w = spy[(ty * RH + r) * TX + tx];
+        const float4 ox = make_float4(fmaf(ah, vx[r][0], bh * u.x), fmaf(ah, vx[r][1], bh * u.y),
+                                      fmaf(ah, vx[r][2], bh * u.z), fmaf(ah, vx[r][3], bh * u.w));
+        const float4 oy = make_float4(fmaf(ah, vy[r][0], bh * w.x), fmaf(ah, vy[r][1], bh * w.y),
+                                      fmaf(ah, vy[r][2], bh * w.z), fmaf(ah, vy[r][3], bh * w.w));
+        const size_t o = (size_t)i * a.pitch + jb;
+        if (jb >= ex0 && jb + CW <= ex1) {
+            St::st4(nx + o, ox);
+            St::st4(ny + o, oy);
+        } else {
+            const float sx[CW] = {ox.x, ox.y, ox.z, ox.w}, sy[CW] = {oy.x, oy.y, oy.z, oy.w};
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+                if (jb + c >= ex0 && jb + c < ex1) {
+                    St::st1(nx + o + c, sx[c]);
+                    St::st1(ny + o + c, sy[c]);
+                }
+        }
+    }
+}
+
+// Sum over the subdomains l whose Gamma_l contains (i, j) of q_l(i, j), for a
+// pixel of core (my, mx): only the 3 x 3 subdomains around it can reach it.
+struct QNeighbours {
+    int ys[3], ye[3], xs[3], xa[3], xe[3];
+    __device__ __forceinline__ void init(const Axis& ay, const Axis& ax, int my, int mx) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int a = my - 1 + d, b = mx - 1 + d;
+            const bool va = a >= 0 && a < ay.M, vb = b >= 0 && b < ax.M;
+            ys[d] = va ? ay.start(a) : 0;
+            ye[d] = va ? ay.end(a) : 0;
+            xs[d] = vb ? ax.start(b) : 0;
+            xe[d] = vb ? ax.end(b) : 0;
+            xa[d] = xs[d] & ~3;
+        }
+    }
+    template <class S>
+    __device__ __forceinline__ float2 sum(const S* __restrict__ q, int hmax, int qp, int M1, int my, int mx,
+                                          int i, int j) const {
+        const size_t qplane = (size_t)hmax * qp;
+        float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+        for (int da = 0; da < 3; ++da) {
+            if (i < ys[da] || i >= ye[da]) continue;
+#pragma unroll
+            for (int db = 0; db < 3; ++db) {
+                if (j < xs[db] || j >= xe[db]) continue;
+                const int s2 = (my - 1 + da) * M1 + (mx - 1 + db);
+                const size_t off = ((size_t)s2 * 2 * hmax + (i - ys[da])) * qp + (j - xa[db]);
+                sx += Stor<S>::ld1(q + off);
+                sy += Stor<S>::ld1(q + off + qplane);
+            }
+        }
+        return make_float2(sx, sy);
+    }
+};
+
+// p^{n+1} on the overlap strips of every core (the frame between the core
+// and its exclusive part), after the small-tile kernel wrote the rest.
+template <class S>
+__global__ void __launch_bounds__(128)
+schwarz2_strip_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* __restrict__ q,
+                      int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah) {
+    using St = Stor<S>;
+    const int sub = blockIdx.x;
+    const int my = sub / ax.M, mx = sub - my * ax.M;
+    const int cy0 = ay.core(my), cy1 = my == ay.M - 1 ? ay.L : ay.core(my + 1);
+    const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
+    const int ey0 = excl_lo(ay, my), ey1 = excl_hi(ay, my);
+    const int ex0 = excl_lo(ax, mx), ex1 = excl_hi(ax, mx);
+    const int W = cx1 - cx0;
+    const int top = (ey0 - cy0) * W, bot = (cy1 - ey1) * W;
+    const int midh = ey1 - ey0, lw = ex0 - cx0, rw = cx1 - ex1;
+    const int total = top + bot + midh * (lw + rw);
+    QNeighbours nb;
+    nb.init(ay, ax, my, mx);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int i, j;
+        if (e < top) {
+            i = cy0 + e / W;
+            j = cx0 + e % W;
+        } else if (e < top + bot) {
+            const int f = e - top;
+            i = ey1 + f / W;
+            j = cx0 + f % W;
+        } else {
+            const int f = e - top - bot, w = lw + rw;
+            i = ey0 + f / w;
+            const int c = f % w;
+            j = c < lw ? cx0 + c : ex1 + (c - lw);
+        }
+        const float2 sq = nb.sum(q, hmax, qp, ax.M, my, mx, i, j);
+        const size_t o = (size_t)i * pitch + j;
+        St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x);
+        St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y);
+    }
+}
+
+// p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum over the subdomains l whose
+// Gamma_l contains x of q_l(x), on whole cores (large subdomains).  Grid:
+// (subdomain, row chunk of its core).
+template <class S>
+__global__ void __launch_bounds__(256)
+schwarz2_combine_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* __restrict__ q,
+                        int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah) {
+    using St = Stor<S>;
+    const int sub = blockIdx.x;
+    const int my = sub / ax.M, mx = sub - my * ax.M;
+    const int cy0 = ay.core(my), cy1 = my == ay.M - 1 ? ay.L : ay.core(my + 1);
+    const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
+    const int rows = (cy1 - cy0 + gridDim.y - 1) / gridDim.y;
+    const int r0 = cy0 + blockIdx.y * rows, r1 = min(cy1, r0 + rows);
+    QNeighbours nb;
+    nb.init(ay, ax, my, mx);
+    for (int i = r0 + threadIdx.y; i < r1; i += blockDim.y)
+        for (int j = cx0 + threadIdx.x; j < cx1; j += blockDim.x) {
+            const float2 sq = nb.sum(q, hmax, qp, ax.M, my, mx, i, j);
+            const size_t o = (size_t)i * pitch + j;
+            St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x);
+            St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -248,17 +621,18 @@ tvs_status schwarz2_check(int n2, int n1, const tvs_decomp& dd) {
         if (ax.core(k + 1) - ax.core(k) < (s > 1 ? s : 1)) return TVS_ERR_ARG;
     Schwarz2State st;
     Carver cv(nullptr);
-    schwarz2_carve(cv, n2, n1, dd, round_up(n1, kPitchAlign), st);
+    schwarz2_carve(cv, n2, n1, dd, round_up(n1, kPitchAlign), TVS_F32, st);
     if (st.ncl > 16 || st.smem > kSchwarzSmemMax) return TVS_ERR_UNSUPPORTED;
     return TVS_OK;
 }
 
-void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, Schwarz2State& st) {
+void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, int storage, Schwarz2State& st) {
     (void)pitch;
     st.m2 = dd.m2;
     st.m1 = dd.m1;
     st.s = dd.overlap;
     st.k = dd.k_inner;
+    st.stor = storage;
     st.alpha_hat = dd.alpha_hat > 0.0 ? dd.alpha_hat : colouring(dd.m2, dd.m1);
     Axis ay{n2, dd.m2, dd.overlap, n2}, ax{n1, dd.m1, dd.overlap, n1};
     st.hmax = 0;
@@ -266,6 +640,20 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
     for (int k = 0; k < dd.m2; ++k) st.hmax = std::max(st.hmax, ay.end(k) - ay.start(k));
     for (int k = 0; k < dd.m1; ++k) st.wmax = std::max(st.wmax, ax.end(k) - ax.start(k));
     st.wpad = round_up(st.wmax + 1, 4);
+    // one CTA per subdomain when Gamma_m plus one row and column fit 4 x 4
+    // pixels per thread (the first column may sit up to 3 right of xa)
+    st.tx = (st.wmax + 3 + 1 + kSmallCW - 1) / kSmallCW;
+    st.ty = (st.hmax + 1 + kSmallRH - 1) / kSmallRH;
+    st.small = st.tx * st.ty <= kSmallMaxThreads;
+    st.qp = st.small ? st.tx * kSmallCW : round_up(st.wmax + 3, 4);
+    const size_t qbytes = (size_t)dd.m2 * dd.m1 * 2 * st.hmax * st.qp * storage_bytes(storage);
+    if (st.small) {
+        st.ncl = 1;
+        st.band = st.hmax;
+        st.smem = small_tile_smem_bytes(st.tx, st.ty);
+        st.q = cv.take<char>(qbytes);
+        return;
+    }
     // fewest CTAs per subdomain whose band fits two CTAs per SM; else one CTA per SM
     st.ncl = 0;
     for (size_t budget : {size_t(110 * 1024), kSchwarzSmemMax}) {
@@ -285,26 +673,31 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
         st.band = (st.hmax + 16) / 17;
         st.smem = tile_smem_floats(st.band, st.wpad) * sizeof(float);
     }
-    st.q = cv.take<float>((size_t)dd.m2 * dd.m1 * 2 * st.hmax * st.wpad);
+    st.q = cv.take<char>(qbytes);
 }
 
-size_t schwarz2_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch) {
+size_t schwarz2_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, int storage) {
     Schwarz2State st;
-    schwarz2_carve(cv, n2, n1, dd, pitch, st);
+    schwarz2_carve(cv, n2, n1, dd, pitch, storage, st);
     return cv.used();
 }
 
 cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s) {
-    return cudaMemsetAsync(st.q, 0, (size_t)st.m2 * st.m1 * 2 * st.hmax * st.wpad * sizeof(float), s);
+    return cudaMemsetAsync(st.q, 0, (size_t)st.m2 * st.m1 * 2 * st.hmax * st.qp * storage_bytes(st.stor), s);
 }
 
-cudaError_t schwarz2_iterate(float** cur, float** nxt, const float* f2, int pitch, long plane, int n2, int n1,
-                             const Schwarz2State& st, float t, int n_outer, cudaStream_t s) {
+template <class S>
+static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pitch, long plane, int n2, int n1,
+                                      const Schwarz2State& st, float t, int n_outer, cudaStream_t s) {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(schwarz2_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(schwarz2_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSchwarzSmemMax);
-        cudaFuncSetAttribute(schwarz2_tile_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(schwarz2_tile_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     Axis ay{n2, st.m2, st.s, n2}, ax{n1, st.m1, st.s, n1};
     cudaLaunchConfig_t cfg = {};
@@ -319,27 +712,57 @@ cudaError_t schwarz2_iterate(float** cur, float** nxt, const float* f2, int pitc
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    dim3 cblk(32, 8), cgrd((n1 + 31) / 32, (n2 + 7) / 8);
+    const int nsub = st.m2 * st.m1;
+    const int hcore = (n2 + st.m2 - 1) / st.m2 + 1;
+    const int chunks = std::max(1, std::min(64, hcore / 16));
+    const float ah = (float)st.alpha_hat;
+    S* q = static_cast<S*>(st.q);
     for (int n = 0; n < n_outer; ++n) {
-        TileArgs a{*cur, f2, pitch, plane, st.q, st.hmax, st.wpad, ay, ax, st.band, st.k, t};
         cudaError_t e;
-        {
-            ProfScope ps(kProfSchwarzTile, s);
-            e = cudaLaunchKernelEx(&cfg, schwarz2_tile_kernel, a);
-        }
-        if (e != cudaSuccess) return e;
-        {
-            ProfScope ps(kProfSchwarzCombine, s);
-            schwarz2_combine_kernel<<<cgrd, cblk, 0, s>>>(*cur, *nxt, st.q, pitch, plane, ay, ax, st.hmax,
-                                                           st.wpad, (float)st.alpha_hat);
+        if (st.small) {
+            {
+                ProfScope ps(kProfSchwarzTile, s);
+                SmallTileArgs<S> a{*cur, *nxt, f2, pitch, plane, q, st.hmax, st.qp, ay, ax, st.k, t, ah};
+                if (st.tx * st.ty <= kSmallPairThreads)
+                    schwarz2_small_tile_kernel<S, kSmallPairThreads, 2><<<nsub, dim3(st.tx, st.ty), st.smem, s>>>(a);
+                else
+                    schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1><<<nsub, dim3(st.tx, st.ty), st.smem, s>>>(a);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) return e;
+            if (st.s > 0 && nsub > 1) {
+                ProfScope ps(kProfSchwarzCombine, s);
+                schwarz2_strip_kernel<S><<<nsub, 128, 0, s>>>(*cur, *nxt, q, pitch, plane, ay, ax, st.hmax, st.qp, ah);
+            }
+        } else {
+            {
+                ProfScope ps(kProfSchwarzTile, s);
+                TileArgs<S> a{*cur, f2, pitch, plane, q, st.hmax, st.wpad, st.qp, ay, ax, st.band, st.k, t};
+                e = cudaLaunchKernelEx(&cfg, schwarz2_tile_kernel<S>, a);
+            }
+            if (e != cudaSuccess) return e;
+            {
+                ProfScope ps(kProfSchwarzCombine, s);
+                schwarz2_combine_kernel<S><<<dim3(nsub, chunks), dim3(64, 4), 0, s>>>(*cur, *nxt, q, pitch, plane,
+                                                                                       ay, ax, st.hmax, st.qp, ah);
+            }
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        float* tmp = *cur;
+        S* tmp = *cur;
         *cur = *nxt;
         *nxt = tmp;
     }
     return cudaSuccess;
+}
+
+cudaError_t schwarz2_iterate(void** cur, void** nxt, const float* f2, int pitch, long plane, int n2, int n1,
+                             const Schwarz2State& st, float t, int n_outer, cudaStream_t s) {
+    TVS_STORAGE_SWITCH(st.stor, {
+        return schwarz2_iterate_t<S>(reinterpret_cast<S**>(cur), reinterpret_cast<S**>(nxt), f2, pitch, plane, n2,
+                                     n1, st, t, n_outer, s);
+    })
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace tvs

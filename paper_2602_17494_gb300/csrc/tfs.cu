@@ -186,9 +186,8 @@ tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const
     }
     __syncthreads();
 
-    double acc[kRedSlots];
-#pragma unroll
-    for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+    KSum ks[4];
+    float pmax = 0.0f, dmax = 0.0f;
 #pragma unroll
     for (int rr = ty; rr < kTY; rr += kBY) {
         const int i = i0 + rr, j = j0 + tx;
@@ -220,13 +219,14 @@ tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const
                 const size_t fo = o;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    const double a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
-                    acc[0] += sqrt(a * a + b * b);
-                    acc[1] += a * px + b * py;
-                    acc[2] += (double)zc[k] * (double)zc[k];
-                    const double zf = (double)zc[k] + (double)__ldg(&f1[(size_t)k * plane + fo]);
-                    acc[3] += zf * zf;
-                    acc[4] = fmax(acc[4], sqrt(px * px + py * py));
+                    const float a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
+                    const float ng = sqrtf(a * a + b * b);
+                    ks[0].add(ng);
+                    ks[1].add(ng - (a * px + b * py));
+                    ks[2].add(zc[k] * zc[k]);
+                    const float zf = zc[k] + __ldg(&f1[(size_t)k * plane + fo]);
+                    ks[3].add(zf * zf);
+                    pmax = fmaxf(pmax, sqrtf(px * px + py * py));
                 }
                 // div z with the zero-extension rule of D^- (z_1 read as zero in
                 // the last column, z_2 in the last row)
@@ -234,11 +234,17 @@ tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const
                 const float z1l = (j >= 1) ? sz[0][r][c - 1] : 0.f;
                 const float z2c = (i <= R - 2) ? zc[1] : 0.f;
                 const float z2u = (i >= 1) ? sz[1][r - 1][c] : 0.f;
-                acc[5] = fmax(acc[5], fabs((double)((z1c - z1l) + (z2c - z2u))));
+                dmax = fmaxf(dmax, fabsf((z1c - z1l) + (z2c - z2u)));
             }
         }
     }
-    if (CHECK) block_reduce_store<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
+    if (CHECK) {
+        double acc[kRedSlots];
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k)
+            acc[k] = k < 4 ? ks[k].value() : (k == 4 ? (double)pmax : (k == 5 ? (double)dmax : 0.0));
+        block_reduce_store<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
+    }
 }
 
 int tfs_blocks(int R, int C) { return ((C + kTX - 1) / kTX) * ((R + kTY - 1) / kTY); }

@@ -7,6 +7,9 @@
 
 #include "../../include/tvs.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace tvs {
 
 constexpr int kPitchAlign = 32;        // floats; internal planes start rows on 128-byte lines
@@ -104,6 +107,9 @@ cudaError_t poisson_solve_batched(float* S, int nbatch, long bstride, const int2
 // --------------------------------------------------------------------------
 // Reductions for the gap / energy checks (FP64, deterministic two-pass).
 // --------------------------------------------------------------------------
+// Reduction slots: 0 sum |psi|, 1 sum (|psi| - psi . p) (the duality gap
+// terms, each >= 0 while |p| <= 1), 2 sum z^2, 3 sum (z + f)^2, 4 max |p|,
+// 5 max |div z|; 6, 7 unused.
 constexpr int kRedSlots = 8;
 struct RedBuf {
     double* partial;   // [nblocks][kRedSlots]
@@ -118,6 +124,20 @@ cudaError_t finalize_red(const RedBuf& rb, int nblocks, cudaStream_t s);
 // 6..7 summed.  NT = threads of the block, tid = linear thread index.  The
 // result lands in out[0..kRedSlots) (written by threads 0..kRedSlots-1).
 __device__ __forceinline__ bool red_is_max(int k) { return k == 4 || k == 5; }
+
+// Per-thread compensated (Kahan) FP32 sum: the check kernels add FP32
+// per-pixel terms here and hand the total to FP64 for the cross-thread
+// reduction, so no FP64 arithmetic runs per pixel.
+struct KSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 template <int NT>
 __device__ __forceinline__ void block_reduce_store(double v[kRedSlots], double* out, int tid) {
@@ -147,5 +167,108 @@ __device__ __forceinline__ void block_reduce_store(double v[kRedSlots], double* 
 // --------------------------------------------------------------------------
 void set_error(const char* what, cudaError_t e);
 void set_error_text(const char* msg);
+
+
+// ---------------------------------------------------------------------------
+// Storage formats of the dual fields: values live in HBM as float, bf16 or
+// fp16 and are widened to float for all arithmetic; stores round to nearest.
+// ld* go through the read-only path; ld*c are plain loads for data the same
+// kernel also writes.
+// ---------------------------------------------------------------------------
+template <class S>
+struct Stor;
+template <>
+struct Stor<float> {
+    static __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+    static __device__ __forceinline__ float4 ld4c(const float* p) { return *reinterpret_cast<const float4*>(p); }
+    static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld1c(const float* p) { return *p; }
+    static __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+    static __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
+};
+template <>
+struct Stor<__nv_bfloat16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float4 ld4(const T* p) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        __nv_bfloat162 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    static __device__ __forceinline__ float ld1(const T* p) { return __bfloat162float(p[0]); }
+    static __device__ __forceinline__ float ld1c(const T* p) { return __bfloat162float(p[0]); }
+    static __device__ __forceinline__ float4 ld4c(const T* p) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        __nv_bfloat162 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    static __device__ __forceinline__ void st4(T* p, float4 v) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+    static __device__ __forceinline__ void st1(T* p, float v) { p[0] = __float2bfloat16_rn(v); }
+};
+template <>
+struct Stor<__half> {
+    using T = __half;
+    static __device__ __forceinline__ float4 ld4(const T* p) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        __half2 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    static __device__ __forceinline__ float ld1(const T* p) { return __half2float(p[0]); }
+    static __device__ __forceinline__ float ld1c(const T* p) { return __half2float(p[0]); }
+    static __device__ __forceinline__ float4 ld4c(const T* p) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        __half2 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    static __device__ __forceinline__ void st4(T* p, float4 v) {
+        const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+    static __device__ __forceinline__ void st1(T* p, float v) { p[0] = __float2half_rn(v); }
+};
+
+// Bytes per element of a tvs_storage value (0 if unknown).
+inline size_t storage_bytes(int storage) {
+    return storage == TVS_F32 ? 4 : (storage == TVS_BF16 || storage == TVS_F16) ? 2 : 0;
+}
+
+// Runs the statement (the variadic arguments) with the type S for the
+// runtime storage value v.
+#define TVS_STORAGE_SWITCH(v, ...)           \
+    switch (v) {                             \
+        case TVS_BF16: {                     \
+            using S = __nv_bfloat16;         \
+            __VA_ARGS__;                     \
+        } break;                             \
+        case TVS_F16: {                      \
+            using S = __half;                \
+            __VA_ARGS__;                     \
+        } break;                             \
+        default: {                           \
+            using S = float;                 \
+            __VA_ARGS__;                     \
+        } break;                             \
+    }
+
 
 }  // namespace tvs

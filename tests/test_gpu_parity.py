@@ -172,6 +172,22 @@ def test_schwarz2_matches_oracle(B, n2, n1, m2, m1, s, k, outer):
     assert rel(res.report["primal_E"], rep_o.primal_E) <= EREL
 
 
+@pytest.mark.parametrize("n2,n1,k", [(256, 256, 4), (200, 262, 3)])
+def test_schwarz2_64px_tiles_match_oracle(B, n2, n1, k):
+    # subdomains of about 64 x 64 with overlap 4: one CTA per subdomain
+    m2, m1 = (n2 + 63) // 64, (n1 + 63) // 64
+    d0 = image(n2, n1, 14, texture=True)
+    tau = otvs.tfs(d0, 0.05, 0.125, 20)[0].astype(np.float32).astype(np.float64)
+    f2 = otvs.irv1_data(d0.astype(np.float32).astype(np.float64), otvs.normal_field(tau, n2, n1, 1e-3), 10.0)
+    dd = osch.Decomp(n2, n1, m2, m1, 4, False)
+    d_o, p_o, rep_o = osch.schwarz_irv1(f2, 10.0, dd, 0.125, 6, k)
+    p = torch.zeros((2, n2, n1), dtype=torch.float32, device="cuda")
+    res = B.tvs_schwarz(2, cuda(d0), cuda(tau), 10.0, 1e-3, B.make_decomp(m2, m1, 4, k), B.make_iter(6), p=p)
+    assert np.abs(host(p) - p_o).max() <= TOL
+    assert np.abs(host(res.out) - d_o).max() <= TOL
+    assert rel(res.report["primal_E"], rep_o.primal_E) <= EREL
+
+
 def test_schwarz2_single_subdomain_equals_global(B):
     d0 = image(40, 44, 12)
     tau = cuda(otvs.tfs(d0, 0.05, 0.125, 30)[0])

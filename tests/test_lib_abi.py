@@ -56,7 +56,14 @@ def test_workspace_sizes(lib):
     L = lib.lib()
     assert L.tvs_workspace_bytes(1, 1, 64, None, 0) == 0          # too small
     assert L.tvs_workspace_bytes(1, 8193, 64, None, 0) == 0       # too large
-    assert L.tvs_workspace_bytes(1, 64, 64, None, 1) == 0         # bf16 storage not in this build
+    assert L.tvs_workspace_bytes(1, 64, 64, None, 1) == 0         # step 1 keeps an FP32 dual
+    assert L.tvs_workspace_bytes(2, 64, 64, None, 7) == 0         # no such storage
+    # 16-bit storage halves the two step-2 dual buffers (and the Schwarz warm starts)
+    n = 1024
+    f32, bf16, f16 = (lib.workspace_bytes(2, n, n, storage=s) for s in (0, 1, 2))
+    assert bf16 == f16 and f32 - bf16 >= 2 * 2 * 2 * n * n
+    assert lib.workspace_bytes(2, n, n, dd, storage=1) < lib.workspace_bytes(2, n, n, dd)
+    assert lib.workspace_bytes(0, n, n, dd, storage=2) < lib.workspace_bytes(0, n, n, dd)
 
 
 def test_bad_arguments_rejected_before_any_device_work(lib):
@@ -83,9 +90,14 @@ def test_bad_arguments_rejected_before_any_device_work(lib):
     dd = lib.make_decomp(4, 4, 8, 5)
     assert L.tvs_schwarz(2, fake, fake, 20, 20, 10.0, 1e-3, ctypes.byref(dd), ctypes.byref(it), fake, None, fake,
                          1 << 30, None, ctypes.byref(rep)) == 1
-    # bf16 storage is not in this build
+    # 16-bit storage is a step-2 option; unknown storage values are argument errors
     bf = lib.make_iter(10, storage=1)
     assert L.tvs_step1(fake, 8, 8, 0.05, ctypes.byref(bf), fake, None, fake, 1 << 30, None, ctypes.byref(rep)) == 6
+    assert L.tvs_denoise(fake, 8, 8, 0.05, 10.0, 1e-3, ctypes.byref(bf), ctypes.byref(it), None, None, fake, fake,
+                         1 << 30, None, ctypes.byref(rep)) == 6
+    odd = lib.make_iter(10, storage=9)
+    assert L.tvs_step2(fake, fake, 8, 8, 10.0, 1e-3, ctypes.byref(odd), fake, None, fake, 1 << 30, None,
+                       ctypes.byref(rep)) == 1
 
 
 def test_schwarz1_workspace_and_limits(lib):
