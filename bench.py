@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N, help="image side for --case")
     ap.add_argument("--iters", type=int, default=3, help="updates (or outer iterations) for --case")
     ap.add_argument("--repeat", type=int, default=2, help="calls for --case")
+    ap.add_argument("--storage", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="step-2 dual storage for --case: 0 f32, 1 bf16, 2 f16, 3 16-bit fixed point")
+    ap.add_argument("--tile", type=int, default=256, help="Schwarz core size for --case schwarz2")
     return ap.parse_args()
 
 
@@ -411,6 +414,24 @@ def run_large(args, B, dev, torch):
                                    "frac": achieved / hbm, "avg_launch_us": avg_s * 1e6,
                                    "bytes_per_launch": 20.0 * n * n,
                                    "gpix_iter_per_s": n * n / avg_s / 1e9}
+    # 16-bit dual storage: 12 algorithmic bytes per pixel (p 4 + f2 4 + p 4)
+    for st, name in ((3, "s16"), (2, "f16"), (1, "bf16")):
+        ws16 = B.workspace(2, n, n, device=dev, storage=st)
+        B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(3, T, storage=st), d=d, ws=ws16)
+        torch.cuda.synchronize(dev)
+        B.tvs_profile_enable(True)
+        B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(50, T, storage=st), d=d, ws=ws16)
+        torch.cuda.synchronize(dev)
+        prof = B.tvs_profile_read()
+        B.tvs_profile_enable(False)
+        nl, ms = prof["irv1_update"]
+        avg_s = ms / nl / 1e3
+        a16 = 12.0 * n * n / avg_s / 1e9
+        out[f"irv1_update_roofline_{name}"] = {"bound": "hbm", "achieved": a16, "peak": hbm, "unit": "GB/s",
+                                               "frac": a16 / hbm, "avg_launch_us": avg_s * 1e6,
+                                               "bytes_per_launch": 12.0 * n * n,
+                                               "gpix_iter_per_s": n * n / avg_s / 1e9}
+        del ws16
 
     # time to relative gap 1e-4: global vs Schwarz
     def timed(fn):
@@ -490,21 +511,22 @@ def run_case(args):
     n = args.n
     d0 = torch.from_numpy(noisy_scene(SceneSpec(n, n, 0, SIGMA, True))[1].astype(np.float32)).cuda()
     tau = torch.zeros((2, n + 1, n + 1), dtype=torch.float32, device="cuda")
-    m = max(1, n // 256)
+    m = max(1, n // args.tile)
     dd = B.make_decomp(m, m, OVERLAP if n // m >= 2 * OVERLAP else 4, K_INNER)
     it = B.make_iter(args.iters, T)
+    it2 = B.make_iter(args.iters, T, storage=args.storage)
     t0 = time.perf_counter()
     for _ in range(args.repeat):
         if args.case == "step1":
             r = B.tvs_step1(d0, DELTA, it, tau=tau)
         elif args.case == "step2":
-            r = B.tvs_step2(d0, tau, ALPHA, EPS, it)
+            r = B.tvs_step2(d0, tau, ALPHA, EPS, it2)
         elif args.case == "schwarz2":
-            r = B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, it)
+            r = B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, it2)
         else:
             r = B.tvs_denoise(d0, DELTA, ALPHA, EPS, it, it, dd, tau=tau)
     torch.cuda.synchronize()
-    return {"case": args.case, "n": n, "iters": args.iters, "repeat": args.repeat,
+    return {"case": args.case, "n": n, "iters": args.iters, "repeat": args.repeat, "storage": args.storage,
             "seconds": time.perf_counter() - t0}
 
 

@@ -53,7 +53,11 @@ typedef enum {
     TVS_ERR_UNSUPPORTED = 6     /* size or option not supported by this build   */
 } tvs_status;
 
-typedef enum { TVS_F32 = 0, TVS_BF16 = 1, TVS_F16 = 2 } tvs_storage;
+/* Storage of the step-2 dual between updates (arithmetic is always FP32).
+ * TVS_S16 is 16-bit fixed point on [-1, 1] (code / 32767): every component
+ * of a feasible dual lies there (|p| <= 1), so it spends all 16 bits on that
+ * range.  16-bit formats round stochastically on store (reproducibly). */
+typedef enum { TVS_F32 = 0, TVS_BF16 = 1, TVS_F16 = 2, TVS_S16 = 3 } tvs_storage;
 
 /* Iteration control of one dual solve (Sections 4.2 and 5.2). */
 typedef struct {
@@ -62,11 +66,11 @@ typedef struct {
     double rel_gap_tol;  /* stop once gap/E <= tol (checked every check_every); 0 = never */
     int    check_every;  /* updates between gap checks; <= 0 means only at the end      */
     int    storage;      /* tvs_storage of the dual fields kept between updates:
-                          * TVS_F32 everywhere; TVS_BF16 or TVS_F16 for step 2
-                          * (tvs_step2, tvs_schwarz step 2, tvs_denoise it2),
-                          * where p and the Schwarz warm starts q are stored in
-                          * 16 bits and widened to FP32 for every update (round
-                          * to nearest on store).  The caller's p stays FP32.
+                          * TVS_F32 everywhere; TVS_BF16, TVS_F16 or TVS_S16 for
+                          * step 2 (tvs_step2, tvs_schwarz step 2, tvs_denoise
+                          * it2), where p and the Schwarz warm starts q are
+                          * stored in 16 bits and widened to FP32 for every
+                          * update.  The caller's p stays FP32.
                           * Step 1 with a 16-bit storage: TVS_ERR_UNSUPPORTED;
                           * any other value: TVS_ERR_ARG.                        */
 } tvs_iter;

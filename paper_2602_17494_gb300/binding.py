@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libtvs.so")
 
 TVS_OK = 0
 TVS_ERR_NOT_CONVERGED = 5
-TVS_F32, TVS_BF16, TVS_F16 = 0, 1, 2
+TVS_F32, TVS_BF16, TVS_F16, TVS_S16 = 0, 1, 2, 3
 
 
 class TvsIter(ctypes.Structure):

@@ -116,9 +116,15 @@ static tvs_status check_ws(void* ws, size_t ws_bytes, size_t need) {
 }
 
 static tvs_status read_result(const RedBuf& rb, int nblocks, cudaStream_t s, double out[kRedSlots]) {
+    unsigned err = 0;
     TVS_CUDA(finalize_red(rb, nblocks, s));
     TVS_CUDA(cudaMemcpyAsync(out, rb.result, kRedSlots * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TVS_CUDA(cudaMemcpyAsync(&err, rb.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     TVS_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+        set_error_text("a bounded device-side wait gave up (TMA row load)");
+        return TVS_ERR_TIMEOUT;
+    }
     return TVS_OK;
 }
 
@@ -177,6 +183,7 @@ static cudaError_t p2_zero(const Step2Layout& L, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // f1 = P_K tau0 / delta into L.f1 (uses L.S as scratch).
 static tvs_status tfs_setup(const Step1Layout& L, const float* d0, int n2, int n1, double delta, cudaStream_t s) {
+    TVS_CUDA(cudaMemsetAsync(L.red.err, 0, sizeof(unsigned), s));
     TVS_CUDA(build_poisson(L.pp, s));
     TVS_CUDA(launch_tau0(d0, n1, n2, n1, L.f1, L.P, L.plane, s));
     RowSrcArgs sa{L.f1, L.plane, L.P};
@@ -238,6 +245,7 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
     TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P, s));
     if (p_user) TVS_CUDA(p2_in(L, p_user, s));
     else TVS_CUDA(p2_zero(L, s));
+    TVS_CUDA(cudaMemsetAsync(L.red.err, 0, sizeof(unsigned), s));
     void* cur = L.pa;
     void* nxt = L.pb;
     const int nb = irv1_blocks(L.R, L.C);
@@ -250,7 +258,7 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
         TVS_CUDA(launch_irv1_update(cur, nxt, L.f2, L.R, L.C, L.P, L.plane, t, fa, ck, true, nullptr, 0,
-                                    L.red.partial, L.st, s));
+                                    L.red.partial, L.st, (uint32_t)n + 1u, L.red.err, s));
         std::swap(cur, nxt);
         ++n;
         if (ck) {
@@ -265,7 +273,7 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
         }
     }
     TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, d, n1,
-                                L.red.partial, L.st, s));
+                                L.red.partial, L.st, 0u, L.red.err, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;
@@ -280,6 +288,7 @@ static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, 
                                const tvs_iter& it, float* d, float* p_user, cudaStream_t s, tvs_report* rep) {
     if (p_user) TVS_CUDA(p2_in(L, p_user, s));
     else TVS_CUDA(p2_zero(L, s));
+    TVS_CUDA(cudaMemsetAsync(L.red.err, 0, sizeof(unsigned), s));
     TVS_CUDA(schwarz2_reset(S2, s));
     void* cur = L.pa;
     void* nxt = L.pb;
@@ -293,11 +302,11 @@ static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, 
     tvs_status st;
     while (n < it.max_iter) {
         const int step = chunk < it.max_iter - n ? chunk : it.max_iter - n;
-        TVS_CUDA(schwarz2_iterate(&cur, &nxt, L.f2, L.P, L.plane, n2, n1, S2, t, step, s));
+        TVS_CUDA(schwarz2_iterate(&cur, &nxt, L.f2, L.P, L.plane, n2, n1, S2, t, step, (uint32_t)n, s));
         n += step;
         if (check_loop && n < it.max_iter) {
             TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, nullptr, 0,
-                                        L.red.partial, L.st, s));
+                                        L.red.partial, L.st, 0u, L.red.err, s));
             st = read_result(L.red, nb, s, r);
             if (st != TVS_OK) return st;
             tvs_report tmp;
@@ -309,7 +318,7 @@ static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, 
         }
     }
     TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, d, n1,
-                                L.red.partial, L.st, s));
+                                L.red.partial, L.st, 0u, L.red.err, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;

@@ -10,6 +10,10 @@
 // exactly those zeros, so one stencil covers the interior and the boundary.
 #include "tvs_internal.cuh"
 #include "prof.h"
+#include "tma.cuh"
+
+#include <mutex>
+#include <type_traits>
 
 namespace tvs {
 
@@ -47,12 +51,16 @@ cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long t
 }
 
 // ---------------------------------------------------------------------------
-// Streaming IRV1 update: each warp owns a strip of 128 columns (4 per lane,
-// float4 loads) and walks down a chunk of rows, keeping the previous row's
-// dual and residual in registers.  Left/right neighbours come from warp
-// shuffles; only the strip edges load scalar halo values.  No shared memory
-// and no barriers, so HBM traffic is the 20 algorithmic bytes per pixel plus
-// one extra row per chunk.  Requires pitch % 4 == 0 and 16-byte aligned planes.
+// Streaming IRV1 update: each warp owns a strip of 128 columns (4 per lane)
+// and walks down a chunk of rows, keeping the previous row's dual and
+// residual in registers.  Rows arrive through TMA: lane 0 keeps kStages row
+// loads in flight per warp (p as one 3-D box covering both planes, f2 as a
+// 2-D box), each box spanning the strip plus 16 bytes of halo on either side;
+// reads outside the grid come back as zeros, which is the zero extension of
+// D^- at the left edge.  Left/right neighbours of the computed residual come
+// from warp shuffles.  No block-level barriers; HBM traffic is the 20 (FP32)
+// or 12 (16-bit) algorithmic bytes per pixel plus the halo columns and one
+// extra row per chunk.
 //   CHECK  : per-warp partial sums of the gap/energy terms at the input p
 //   WRITE_P: write the updated dual
 //   WRITE_D: write d = -z / alpha at the input p
@@ -60,34 +68,89 @@ cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long t
 constexpr int kStrip = 128;      // columns per warp
 constexpr int kChunk = 32;       // output rows per warp
 constexpr int kStreamWarps = 4;  // warps per block
+constexpr int kStages = 3;       // row loads in flight per warp
 
-struct Row4 {
-    float4 px, py, f;
+template <class S>
+struct StreamGeom {
+    static constexpr int HP = 16 / (int)sizeof(S);          // halo columns of the p box
+    static constexpr int WP = kStrip + 2 * HP;              // p box width (elements)
+    static constexpr int HF = 4, WF = kStrip + 8;           // f2 box (float)
+    static constexpr int PBYTES = 2 * WP * (int)sizeof(S);  // both planes
+    static constexpr int FBYTES = WF * 4;
+    static constexpr int POFF = 0;
+    static constexpr int FOFF = (PBYTES + 127) / 128 * 128;
+    static constexpr int STAGE = FOFF + (FBYTES + 127) / 128 * 128;
+    static constexpr int WARP_BYTES = kStages * STAGE;
 };
+template <class S>
+constexpr size_t stream_smem_bytes() {
+    return (size_t)kStreamWarps * StreamGeom<S>::WARP_BYTES + (size_t)kStreamWarps * kStages * sizeof(uint64_t) + 128;
+}
+
 __device__ __forceinline__ float comp(const float4& v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+// 4 consecutive elements of a box row in shared memory, widened to float
+template <class S>
+__device__ __forceinline__ float4 sm_ld4(const S* p) {
+    if constexpr (sizeof(S) == 4) return *reinterpret_cast<const float4*>(p);
+    else return Stor<S>::ld4c(p);
+}
+template <class S>
+__device__ __forceinline__ float sm_ld1(const S* p) {
+    if constexpr (sizeof(S) == 4) return *reinterpret_cast<const float*>(p);
+    else return Stor<S>::ld1c(p);
 }
 
 template <class S, bool CHECK, bool WRITE_P, bool WRITE_D>
 __global__ void __launch_bounds__(32 * kStreamWarps, CHECK ? 5 : 8)
-irv1_stream_kernel(const S* __restrict__ pin, S* __restrict__ pout, const float* __restrict__ f2, int R,
-                   int C, int pitch, long plane, float t, float alpha_inv, float* __restrict__ d_out, int d_pitch,
-                   double* __restrict__ partial) {
+irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap fmap,
+                   const S* __restrict__ pin, S* __restrict__ pout, int R, int C, int pitch, long plane, float t,
+                   float alpha_inv, float* __restrict__ d_out, int d_pitch, double* __restrict__ partial,
+                   uint32_t seed, unsigned* __restrict__ err) {
+    using G = StreamGeom<S>;
+    using St = Stor<S>;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // TMA destinations are kept 128-byte aligned
+    unsigned char* smem_raw = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) &
+                                                               ~static_cast<uintptr_t>(127));
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int strip = blockIdx.x;
     const int chunk = blockIdx.y * kStreamWarps + wib;
     const int r0 = chunk * kChunk;
-    const int j0 = strip * kStrip + 4 * lane;     // first column of this lane
+    const int x0 = strip * kStrip;                // first column of the strip
+    const int j0 = x0 + 4 * lane;                 // first column of this lane
     const int r1 = min(r0 + kChunk, R);           // output rows [r0, r1)
-    using St = Stor<S>;
-    const S* __restrict__ px = pin;
-    const S* __restrict__ py = pin + plane;
+    unsigned char* wbase = smem_raw + (size_t)wib * G::WARP_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kStreamWarps * G::WARP_BYTES) + wib * kStages;
     KSum ks[4];
     float pmax = 0.0f;
+    (void)pin;
 
     if (r0 < R) {
-        const int jr = strip * kStrip + kStrip;   // first column right of the strip
+        // rows r0 - 1 .. rend - 1 stream through the ring; item k is row r0 - 1 + k
+        const int rend = min(r1 + 1, R);         // rows whose z is needed
+        const int nitems = rend - r0 + 1;
+        if (lane == 0) {
+            for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+        auto issue = [&](int k) {                 // lane 0 only
+            const int s = k % kStages;
+            unsigned char* st = wbase + s * G::STAGE;
+            const int row = r0 - 1 + k;
+            const uint32_t bytes = (uint32_t)(G::PBYTES + (k > 0 ? G::FBYTES : 0));
+            mbar_expect_tx(&bars[s], bytes);
+            tma_load_3d(st + G::POFF, &pmap, x0 - G::HP, row, 0, &bars[s]);
+            if (k > 0) tma_load_2d(st + G::FOFF, &fmap, x0 - G::HF, row, &bars[s]);
+        };
+        if (lane == 0)
+            for (int k = 0; k < kStages && k < nitems; ++k) issue(k);
+        int issued = min(kStages, nitems);       // items whose load has been issued (same on every lane)
+        int failed = -1;                          // item whose wait gave up
+
         // column masks: D^- reads p_x as zero in the last column and beyond the grid
         float mx[4], mv[4];
 #pragma unroll
@@ -95,50 +158,67 @@ irv1_stream_kernel(const S* __restrict__ pin, S* __restrict__ pout, const float*
             mv[e] = (j0 + e < C) ? 1.f : 0.f;
             mx[e] = (j0 + e <= C - 2) ? 1.f : 0.f;
         }
-        const size_t cbase = (size_t)j0;
-        // row r0 - 1: p_y (for div at row r0)
-        float4 pyu = make_float4(0.f, 0.f, 0.f, 0.f);
-        float pyu_r = 0.f;                         // p_y(r0 - 1, jr) for the right halo (lane 31)
-        if (r0 >= 1 && r0 - 1 <= R - 2) {
-            pyu = St::ld4(py + (size_t)(r0 - 1) * pitch + cbase);
-            if (lane == 31 && jr < C) pyu_r = St::ld1(py + (size_t)(r0 - 1) * pitch + jr);
-        }
-        auto load_row = [&](int i, Row4& rw, float& pxl, float& pxr, float& pyr, float& fr) {
-            const size_t o = (size_t)i * pitch + cbase;
-            rw.px = St::ld4(px + o);
-            rw.py = St::ld4(py + o);
-            rw.f = Stor<float>::ld4(f2 + o);
-            pxl = (lane == 0 && j0 >= 1) ? St::ld1(px + (size_t)i * pitch + j0 - 1) : 0.f;
-            pxr = 0.f;
-            pyr = 0.f;
-            fr = 0.f;
-            if (lane == 31 && jr < C) {
-                pxr = St::ld1(px + (size_t)i * pitch + jr);
-                pyr = St::ld1(py + (size_t)i * pitch + jr);
-                fr = __ldg(&f2[(size_t)i * pitch + jr]);
-            }
-        };
-        Row4 cur, nxt;
-        float cpxl, cpxr, cpyr, cfr, npxl = 0.f, npxr = 0.f, npyr = 0.f, nfr = 0.f;
-        load_row(r0, cur, cpxl, cpxr, cpyr, cfr);
-        float zp[4] = {0.f, 0.f, 0.f, 0.f};        // z of the previous row
-        float zpr = 0.f;                           // z(prev row, jr) on lane 31
+        const int jr = x0 + kStrip;               // first column right of the strip
+        float4 pyu = make_float4(0.f, 0.f, 0.f, 0.f);   // p_y of the row above (masked)
+        float pyu_r = 0.f;                        // p_y(row above, jr) on lane 31
+        float zp[4] = {0.f, 0.f, 0.f, 0.f};       // z of the previous row
+        float zpr = 0.f;                          // z(prev row, jr) on lane 31
         float4 pprevx = make_float4(0.f, 0.f, 0.f, 0.f), pprevy = pprevx;
-        const int rend = min(r1 + 1, R);           // rows whose z is needed
-        for (int i = r0; i <= r1; ++i) {
-            const bool have = i < rend;
-            if (i + 1 < rend) load_row(i + 1, nxt, npxl, npxr, npyr, nfr);
+
+        for (int k = 0; k <= nitems; ++k) {
+            // ---- item k: row i = r0 - 1 + k (k == nitems: past the last row)
+            const int i = r0 - 1 + k;
+            float4 cpx = make_float4(0.f, 0.f, 0.f, 0.f), cpy = cpx, cf = cpx;
+            float cpxl = 0.f, cpxr = 0.f, cpyr = 0.f, cfr = 0.f;
+            const bool have = k < nitems;
+            if (have) {
+                const int s = k % kStages;
+                const bool arrived = mbar_wait(&bars[s], (uint32_t)((k / kStages) & 1));
+                if (!__all_sync(0xffffffffu, arrived)) {
+                    failed = k;
+                    break;
+                }
+                const unsigned char* st = wbase + s * G::STAGE;
+                const S* sp = reinterpret_cast<const S*>(st + G::POFF);
+                const float* sf = reinterpret_cast<const float*>(st + G::FOFF);
+                cpx = sm_ld4<S>(sp + G::HP + 4 * lane);
+                cpy = sm_ld4<S>(sp + G::WP + G::HP + 4 * lane);
+                if (lane == 0) cpxl = sm_ld1<S>(sp + G::HP - 1);
+                if (lane == 31) {
+                    cpxr = sm_ld1<S>(sp + G::HP + kStrip);
+                    cpyr = sm_ld1<S>(sp + G::WP + G::HP + kStrip);
+                }
+                if (k > 0) {
+                    cf = *reinterpret_cast<const float4*>(sf + G::HF + 4 * lane);
+                    if (lane == 31) cfr = sf[G::HF + kStrip];
+                }
+                __syncwarp();
+                if (issued < nitems) {
+                    if (lane == 0) {
+                        fence_proxy_async();      // this warp's reads of stage s precede its refill
+                        issue(issued);
+                    }
+                    ++issued;
+                }
+            }
+            if (k == 0) {
+                // row r0 - 1 supplies p_y above the first row (zero outside the grid or in the last row)
+                const float ymask = (i >= 0 && i <= R - 2) ? 1.f : 0.f;
+                pyu = make_float4(cpy.x * ymask, cpy.y * ymask, cpy.z * ymask, cpy.w * ymask);
+                pyu_r = (jr < C) ? cpyr * ymask : 0.f;
+                continue;
+            }
             float zc[4] = {0.f, 0.f, 0.f, 0.f};
             float zcr = 0.f;
             if (have) {
                 // z = div p - f2 at row i (zero-extension rule of D^-)
                 const float ymask = (i <= R - 2) ? 1.f : 0.f;
-                float pxs[4] = {cur.px.x * mx[0], cur.px.y * mx[1], cur.px.z * mx[2], cur.px.w * mx[3]};
+                float pxs[4] = {cpx.x * mx[0], cpx.y * mx[1], cpx.z * mx[2], cpx.w * mx[3]};
                 float left = __shfl_up_sync(0xffffffffu, pxs[3], 1);
                 if (lane == 0) left = (j0 >= 1 && j0 - 1 <= C - 2) ? cpxl : 0.f;
-                const float pyc[4] = {cur.py.x * ymask, cur.py.y * ymask, cur.py.z * ymask, cur.py.w * ymask};
+                const float pyc[4] = {cpy.x * ymask, cpy.y * ymask, cpy.z * ymask, cpy.w * ymask};
                 const float pyp[4] = {pyu.x, pyu.y, pyu.z, pyu.w};
-                const float fv[4] = {cur.f.x, cur.f.y, cur.f.z, cur.f.w};
+                const float fv[4] = {cf.x, cf.y, cf.z, cf.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const float pl = e == 0 ? left : pxs[e - 1];
@@ -154,11 +234,19 @@ irv1_stream_kernel(const S* __restrict__ pin, S* __restrict__ pout, const float*
                     for (int e = 0; e < 4; ++e)
                         if (j0 + e < C) dd[j0 + e] = -zc[e] * alpha_inv;
                 }
+                if (CHECK && i < r1) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (j0 + e < C) {
+                            const float dv = zc[e] + fv[e];   // div p
+                            ks[3].add(dv * dv);
+                        }
+                }
                 pyu = make_float4(pyc[0], pyc[1], pyc[2], pyc[3]);
                 pyu_r = cpyr * ymask;
             }
-            if (i > r0) {
-                // update row i - 1 from z(i-1) (zp), z(i) (zc)
+            if (k >= 2) {
+                // update row i - 1 from z(i-1) (zp) and z(i) (zc)
                 const int ir = i - 1;
                 float zright = __shfl_down_sync(0xffffffffu, zp[0], 1);
                 if (lane == 31) zright = zpr;
@@ -183,42 +271,33 @@ irv1_stream_kernel(const S* __restrict__ pin, S* __restrict__ pout, const float*
                     }
                 }
                 if (WRITE_P) {
-                    const size_t o = (size_t)ir * pitch + cbase;
+                    const size_t o = (size_t)ir * pitch + j0;
                     if (j0 + 3 < C) {
-                        St::st4(pout + o, make_float4(res_x[0], res_x[1], res_x[2], res_x[3]));
-                        St::st4(pout + plane + o, make_float4(res_y[0], res_y[1], res_y[2], res_y[3]));
+                        St::st4(pout + o, make_float4(res_x[0], res_x[1], res_x[2], res_x[3]), rkey(seed, o, 0));
+                        St::st4(pout + plane + o, make_float4(res_y[0], res_y[1], res_y[2], res_y[3]),
+                                rkey(seed, o, 1));
                     } else {
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             if (j0 + e < C) {
-                                St::st1(pout + o + e, res_x[e]);
-                                St::st1(pout + plane + o + e, res_y[e]);
+                                St::st1(pout + o + e, res_x[e], rkey(seed, o + e, 0));
+                                St::st1(pout + plane + o + e, res_y[e], rkey(seed, o + e, 1));
                             }
                     }
                 }
-            }
-            if (CHECK && have && i < r1) {
-                const float fv[4] = {cur.f.x, cur.f.y, cur.f.z, cur.f.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (j0 + e < C) {
-                        const float dv = zc[e] + fv[e];   // div p
-                        ks[3].add(dv * dv);
-                    }
             }
             // rotate
 #pragma unroll
             for (int e = 0; e < 4; ++e) zp[e] = zc[e];
             zpr = zcr;
-            if (have) {
-                pprevx = cur.px;
-                pprevy = cur.py;
-            }
-            cur = nxt;
-            cpxl = npxl;
-            cpxr = npxr;
-            cpyr = npyr;
-            cfr = nfr;
+            pprevx = cpx;
+            pprevy = cpy;
+            if (i >= r1) break;                   // row r1 only supplied z for the update of row r1 - 1
+        }
+        if (failed >= 0) {
+            // a row never arrived: record it and drain this warp's copies still in flight
+            if (lane == 0) atomicOr(err, 1u);
+            for (int k = failed; k < issued; ++k) (void)mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
         }
     }
     if (CHECK) {
@@ -254,28 +333,54 @@ int irv1_blocks(int R, int C) {
     return strips * ((chunks + kStreamWarps - 1) / kStreamWarps) * kStreamWarps;
 }
 
-cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int R, int C, int pitch,
-                               long plane, float t, float alpha, bool check, bool write_p,
-                               float* d_out, int d_pitch, double* partial, int storage, cudaStream_t s) {
+template <class S>
+static cudaError_t launch_irv1_t(const S* pin, S* pout, const float* f2, int R, int C, int pitch, long plane,
+                                 float t, float alpha, bool check, bool write_p, float* d_out, int d_pitch,
+                                 double* partial, uint32_t seed, unsigned* err, cudaStream_t s) {
+    using G = StreamGeom<S>;
+    CUtensorMap pmap, fmap;
+    if (!make_tensor_map(&pmap, pin, std::is_same<S, float>::value ? TVS_F32
+                                     : std::is_same<S, __nv_bfloat16>::value ? TVS_BF16
+                                     : std::is_same<S, __half>::value ? TVS_F16 : TVS_S16,
+                         R, C, pitch, plane, 2, G::WP) ||
+        !make_tensor_map(&fmap, f2, TVS_F32, R, C, pitch, (long)R * pitch, 1, G::WF))
+        return cudaErrorInvalidValue;
     const int strips = (C + kStrip - 1) / kStrip;
     const int chunks = (R + kChunk - 1) / kChunk;
-    dim3 blk(32 * kStreamWarps), grd(strips, (chunks + kStreamWarps - 1) / kStreamWarps);
+    const dim3 blk(32 * kStreamWarps), grd(strips, (chunks + kStreamWarps - 1) / kStreamWarps);
+    const size_t smem = stream_smem_bytes<S>();
     const float ainv = 1.0f / alpha;
     const bool wd = d_out != nullptr;
-    ProfScope ps((check || !write_p) ? kProfIrv1Check : kProfIrv1Update, s);
-#define TVS_IRV1(CK, WP, WD)                                                                              \
-    irv1_stream_kernel<S, CK, WP, WD><<<grd, blk, 0, s>>>(static_cast<const S*>(pin), static_cast<S*>(pout), f2, R, \
-                                                          C, pitch, plane, t, ainv, d_out, d_pitch, partial)
-    TVS_STORAGE_SWITCH(storage, {
-        if (!check && write_p && !wd) TVS_IRV1(false, true, false);
-        else if (check && write_p && !wd) TVS_IRV1(true, true, false);
-        else if (check && !write_p && wd) TVS_IRV1(true, false, true);
-        else if (check && !write_p && !wd) TVS_IRV1(true, false, false);
-        else if (!check && !write_p && wd) TVS_IRV1(false, false, true);
-        else TVS_IRV1(true, true, true);
-    })
+#define TVS_IRV1(CK, WP, WD)                                                                                   \
+    do {                                                                                                       \
+        static std::once_flag once;                                                                           \
+        std::call_once(once, [] {                                                                             \
+            cudaFuncSetAttribute(irv1_stream_kernel<S, CK, WP, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)stream_smem_bytes<S>());                                               \
+        });                                                                                                    \
+        irv1_stream_kernel<S, CK, WP, WD><<<grd, blk, smem, s>>>(pmap, fmap, pin, pout, R, C, pitch, plane, t,   \
+                                                                 ainv, d_out, d_pitch, partial, seed, err);    \
+    } while (0)
+    if (!check && write_p && !wd) TVS_IRV1(false, true, false);
+    else if (check && write_p && !wd) TVS_IRV1(true, true, false);
+    else if (check && !write_p && wd) TVS_IRV1(true, false, true);
+    else if (check && !write_p && !wd) TVS_IRV1(true, false, false);
+    else if (!check && !write_p && wd) TVS_IRV1(false, false, true);
+    else TVS_IRV1(true, true, true);
 #undef TVS_IRV1
     return cudaGetLastError();
+}
+
+cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int R, int C, int pitch,
+                               long plane, float t, float alpha, bool check, bool write_p,
+                               float* d_out, int d_pitch, double* partial, int storage, uint32_t seed,
+                               unsigned* err, cudaStream_t s) {
+    ProfScope ps((check || !write_p) ? kProfIrv1Check : kProfIrv1Update, s);
+    TVS_STORAGE_SWITCH(storage, {
+        return launch_irv1_t<S>(static_cast<const S*>(pin), static_cast<S*>(pout), f2, R, C, pitch, plane, t, alpha,
+                                check, write_p, d_out, d_pitch, partial, seed, err, s);
+    })
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -289,7 +394,8 @@ __global__ void convert_planes_kernel(SD* __restrict__ dst, int dpitch, long dpl
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= rows || j >= cols) return;
     const float v = Stor<SS>::ld1(src + (size_t)blockIdx.z * splane + (size_t)i * spitch + j);
-    Stor<SD>::st1(dst + (size_t)blockIdx.z * dplane + (size_t)i * dpitch + j, v);
+    const size_t o = (size_t)i * dpitch + j;
+    Stor<SD>::st1(dst + (size_t)blockIdx.z * dplane + o, v, rkey(0x2545f491U, o, blockIdx.z));
 }
 
 cudaError_t convert_planes(void* dst, int dst_storage, int dpitch, long dplane, const void* src, int src_storage,

@@ -28,9 +28,11 @@ inline cudaError_t tfs_phi(const float* p, float* S, int R, int C, int pitch, lo
 cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long tplane, int tpitch, int R, int C,
                          float alpha, float eps, float* f2, int fpitch, cudaStream_t s);
 // p (pin, pout) is stored as `storage` (tvs_storage); everything else is float.
+// seed: update counter for the stochastic rounding of 16-bit stores; err:
+// device word that gets bit 0 set if a bounded wait inside the kernel gave up.
 cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int R, int C, int pitch, long plane,
                                float t, float alpha, bool check, bool write_p, float* d_out, int d_pitch,
-                               double* partial, int storage, cudaStream_t s);
+                               double* partial, int storage, uint32_t seed, unsigned* err, cudaStream_t s);
 int irv1_blocks(int R, int C);
 // Copy `planes` planes of rows x cols between layouts and storage formats
 // (element pitches and plane strides in elements of each side's format).
@@ -56,8 +58,9 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
 cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s);
 // n_outer outer iterations of Algorithm 2: p^{n+1} from p^n = *cur, swapping
 // *cur and *nxt after each iteration.
+// seed0: outer iterations done so far (seeds the stochastic rounding of 16-bit stores).
 cudaError_t schwarz2_iterate(void** cur, void** nxt, const float* f2, int pitch, long plane, int n2, int n1,
-                             const Schwarz2State& st, float t, int n_outer, cudaStream_t s);
+                             const Schwarz2State& st, float t, int n_outer, uint32_t seed0, cudaStream_t s);
 
 // schwarz1.cu -- Algorithm 2 with the localized Algorithm 5 for TFS on the extended grid
 struct Schwarz1State {

@@ -47,6 +47,7 @@ struct TileArgs {
     Axis ay, ax;
     int band, k;
     float t;
+    uint32_t seed;
 };
 
 // Shared memory of one CTA (floats):
@@ -206,8 +207,9 @@ schwarz2_tile_kernel(TileArgs<S> a) {
     for (int idx = threadIdx.x; idx < nown * w; idx += nt) {
         const int r = idx / w, c = idx - r * w;
         const size_t qo = (size_t)(r_lo - y0 + r) * a.qp + c;
-        St::st1(qx + qo, vx[(size_t)(r + 1) * WP + c]);
-        St::st1(qy + qo, vy[(size_t)(r + 1) * WP + c]);
+        const size_t qi = (size_t)sub * a.hmax * a.qp + qo;
+        St::st1(qx + qo, vx[(size_t)(r + 1) * WP + c], rkey(a.seed, qi, 0));
+        St::st1(qy + qo, vy[(size_t)(r + 1) * WP + c], rkey(a.seed, qi, 1));
     }
     cl.sync();   // no CTA leaves while a neighbour could still address its shared memory
 }
@@ -232,6 +234,7 @@ struct SmallTileArgs {
     Axis ay, ax;
     int k;
     float t, ahat;
+    uint32_t seed;
 };
 
 // Rows of core k that no other subdomain's Gamma reaches: [excl_lo, excl_hi).
@@ -465,12 +468,14 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     for (int r = 0; r < RH; ++r)
         if (ib + r < y1) {
             const size_t qo = (size_t)(ib + r - y0) * a.qp + tx * CW;
-            St::st4(qx + qo, make_float4(vx[r][0], vx[r][1], vx[r][2], vx[r][3]));
-            St::st4(qy + qo, make_float4(vy[r][0], vy[r][1], vy[r][2], vy[r][3]));
+            const size_t qi = (size_t)sub * a.hmax * a.qp + qo;
+            St::st4(qx + qo, make_float4(vx[r][0], vx[r][1], vx[r][2], vx[r][3]), rkey(a.seed, qi, 0));
+            St::st4(qy + qo, make_float4(vy[r][0], vy[r][1], vy[r][2], vy[r][3]), rkey(a.seed, qi, 1));
         }
     const int ey0 = excl_lo(a.ay, my), ey1 = excl_hi(a.ay, my);
     const int ex0 = excl_lo(a.ax, mx), ex1 = excl_hi(a.ax, mx);
     const float ah = a.ahat, bh = 1.0f - a.ahat;
+    const uint32_t pseed = a.seed ^ 0xa511e9b3U;   // p^{n+1}: the same keys as the strip kernel's
     S* __restrict__ nx = a.pnext;
     S* __restrict__ ny = a.pnext + a.plane;
 #pragma unroll
@@ -484,15 +489,15 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                                       fmaf(ah, vy[r][2], bh * w.z), fmaf(ah, vy[r][3], bh * w.w));
         const size_t o = (size_t)i * a.pitch + jb;
         if (jb >= ex0 && jb + CW <= ex1) {
-            St::st4(nx + o, ox);
-            St::st4(ny + o, oy);
+            St::st4(nx + o, ox, rkey(pseed, o, 0));
+            St::st4(ny + o, oy, rkey(pseed, o, 1));
         } else {
             const float sx[CW] = {ox.x, ox.y, ox.z, ox.w}, sy[CW] = {oy.x, oy.y, oy.z, oy.w};
 #pragma unroll
             for (int c = 0; c < CW; ++c)
                 if (jb + c >= ex0 && jb + c < ex1) {
-                    St::st1(nx + o + c, sx[c]);
-                    St::st1(ny + o + c, sy[c]);
+                    St::st1(nx + o + c, sx[c], rkey(pseed, o + c, 0));
+                    St::st1(ny + o + c, sy[c], rkey(pseed, o + c, 1));
                 }
         }
     }
@@ -540,7 +545,7 @@ struct QNeighbours {
 template <class S>
 __global__ void __launch_bounds__(128)
 schwarz2_strip_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* __restrict__ q,
-                      int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah) {
+                      int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah, uint32_t seed) {
     using St = Stor<S>;
     const int sub = blockIdx.x;
     const int my = sub / ax.M, mx = sub - my * ax.M;
@@ -571,8 +576,9 @@ schwarz2_strip_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* 
         }
         const float2 sq = nb.sum(q, hmax, qp, ax.M, my, mx, i, j);
         const size_t o = (size_t)i * pitch + j;
-        St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x);
-        St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y);
+        const uint32_t pseed = seed ^ 0xa511e9b3U;
+        St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x, rkey(pseed, o, 0));
+        St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y, rkey(pseed, o, 1));
     }
 }
 
@@ -582,7 +588,8 @@ schwarz2_strip_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* 
 template <class S>
 __global__ void __launch_bounds__(256)
 schwarz2_combine_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* __restrict__ q,
-                        int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah) {
+                        int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah, uint32_t seed) {
+    const uint32_t pseed = seed ^ 0xa511e9b3U;
     using St = Stor<S>;
     const int sub = blockIdx.x;
     const int my = sub / ax.M, mx = sub - my * ax.M;
@@ -596,8 +603,8 @@ schwarz2_combine_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S
         for (int j = cx0 + threadIdx.x; j < cx1; j += blockDim.x) {
             const float2 sq = nb.sum(q, hmax, qp, ax.M, my, mx, i, j);
             const size_t o = (size_t)i * pitch + j;
-            St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x);
-            St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y);
+            St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x, rkey(pseed, o, 0));
+            St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y, rkey(pseed, o, 1));
         }
 }
 
@@ -688,7 +695,8 @@ cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s) {
 
 template <class S>
 static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pitch, long plane, int n2, int n1,
-                                      const Schwarz2State& st, float t, int n_outer, cudaStream_t s) {
+                                      const Schwarz2State& st, float t, int n_outer, uint32_t seed0,
+                                      cudaStream_t s) {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(schwarz2_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -719,10 +727,11 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
     S* q = static_cast<S*>(st.q);
     for (int n = 0; n < n_outer; ++n) {
         cudaError_t e;
+        const uint32_t seed = hash32(seed0 + (uint32_t)n + 1u);
         if (st.small) {
             {
                 ProfScope ps(kProfSchwarzTile, s);
-                SmallTileArgs<S> a{*cur, *nxt, f2, pitch, plane, q, st.hmax, st.qp, ay, ax, st.k, t, ah};
+                SmallTileArgs<S> a{*cur, *nxt, f2, pitch, plane, q, st.hmax, st.qp, ay, ax, st.k, t, ah, seed};
                 if (st.tx * st.ty <= kSmallPairThreads)
                     schwarz2_small_tile_kernel<S, kSmallPairThreads, 2><<<nsub, dim3(st.tx, st.ty), st.smem, s>>>(a);
                 else
@@ -732,19 +741,20 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
             if (e != cudaSuccess) return e;
             if (st.s > 0 && nsub > 1) {
                 ProfScope ps(kProfSchwarzCombine, s);
-                schwarz2_strip_kernel<S><<<nsub, 128, 0, s>>>(*cur, *nxt, q, pitch, plane, ay, ax, st.hmax, st.qp, ah);
+                schwarz2_strip_kernel<S><<<nsub, 128, 0, s>>>(*cur, *nxt, q, pitch, plane, ay, ax, st.hmax, st.qp, ah,
+                                                              seed);
             }
         } else {
             {
                 ProfScope ps(kProfSchwarzTile, s);
-                TileArgs<S> a{*cur, f2, pitch, plane, q, st.hmax, st.wpad, st.qp, ay, ax, st.band, st.k, t};
+                TileArgs<S> a{*cur, f2, pitch, plane, q, st.hmax, st.wpad, st.qp, ay, ax, st.band, st.k, t, seed};
                 e = cudaLaunchKernelEx(&cfg, schwarz2_tile_kernel<S>, a);
             }
             if (e != cudaSuccess) return e;
             {
                 ProfScope ps(kProfSchwarzCombine, s);
                 schwarz2_combine_kernel<S><<<dim3(nsub, chunks), dim3(64, 4), 0, s>>>(*cur, *nxt, q, pitch, plane,
-                                                                                       ay, ax, st.hmax, st.qp, ah);
+                                                                                       ay, ax, st.hmax, st.qp, ah, seed);
             }
         }
         e = cudaGetLastError();
@@ -757,10 +767,10 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
 }
 
 cudaError_t schwarz2_iterate(void** cur, void** nxt, const float* f2, int pitch, long plane, int n2, int n1,
-                             const Schwarz2State& st, float t, int n_outer, cudaStream_t s) {
+                             const Schwarz2State& st, float t, int n_outer, uint32_t seed0, cudaStream_t s) {
     TVS_STORAGE_SWITCH(st.stor, {
         return schwarz2_iterate_t<S>(reinterpret_cast<S**>(cur), reinterpret_cast<S**>(nxt), f2, pitch, plane, n2,
-                                     n1, st, t, n_outer, s);
+                                     n1, st, t, n_outer, seed0, s);
     })
     return cudaErrorInvalidValue;
 }

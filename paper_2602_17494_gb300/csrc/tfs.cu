@@ -290,6 +290,7 @@ void carve_red(Carver& cv, RedBuf& rb, int cap) {
     rb.cap = cap;
     rb.partial = cv.take<double>((size_t)cap * kRedSlots);
     rb.result = cv.take<double>(kRedSlots);
+    rb.err = cv.take<unsigned>(1);
 }
 
 cudaError_t finalize_red(const RedBuf& rb, int nblocks, cudaStream_t s) {

@@ -114,6 +114,7 @@ constexpr int kRedSlots = 8;
 struct RedBuf {
     double* partial;   // [nblocks][kRedSlots]
     double* result;    // [kRedSlots]
+    unsigned* err;     // bit 0: a bounded device-side wait gave up
     int cap;           // capacity in blocks
 };
 void carve_red(Carver& cv, RedBuf& rb, int cap);
@@ -170,11 +171,58 @@ void set_error_text(const char* msg);
 
 
 // ---------------------------------------------------------------------------
-// Storage formats of the dual fields: values live in HBM as float, bf16 or
-// fp16 and are widened to float for all arithmetic; stores round to nearest.
+// Storage formats of the dual fields: values live in HBM as float, bf16,
+// fp16 or 16-bit fixed point on [-1, 1] and are widened to float for all
+// arithmetic.  16-bit stores round stochastically: the value rounds up with
+// probability equal to the discarded fraction, so updates smaller than one
+// unit in the last place are kept in expectation instead of being lost (with
+// round-to-nearest the iteration stalls at a duality gap of 1e-3 (fp16) or
+// 1e-2 (bf16)).  The random bits come from a counter-based hash of (update
+// seed, element index, plane), so runs are reproducible bit for bit.
 // ld* go through the read-only path; ld*c are plain loads for data the same
 // kernel also writes.
 // ---------------------------------------------------------------------------
+
+// lowbias32 integer hash (C. Wellons, "Prospecting for hash functions", 2018).
+__host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+// Random key of the element at index o of plane pl for update `seed`.
+__device__ __forceinline__ uint32_t rkey(uint32_t seed, size_t o, int pl) {
+    return hash32(seed ^ hash32((uint32_t)o * 2u + (uint32_t)pl));
+}
+// 16 random bits for each of the 4 elements of a vector store with key k.
+__device__ __forceinline__ void rbits4(uint32_t k, uint32_t r[4]) {
+    const uint32_t a = hash32(k), b = hash32(k ^ 0x9e3779b9U);
+    r[0] = a & 0xffffU;
+    r[1] = a >> 16;
+    r[2] = b & 0xffffU;
+    r[3] = b >> 16;
+}
+
+__device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, uint32_t r16) {
+    uint32_t b = __float_as_uint(x);
+    if ((b & 0x7f800000U) == 0x7f800000U) return __float2bfloat16_rn(x);
+    b += r16 & 0xffffU;                                   // a carry rounds the magnitude up
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+__device__ __forceinline__ __half f16_sr(float x, uint32_t r16) {
+    const float ax = fabsf(x);
+    if (!(ax >= 6.103515625e-05f && ax < 32768.0f)) return __float2half_rn(x);   // outside the normal range
+    const uint32_t b = (__float_as_uint(x) + (r16 & 0x1fffU)) & ~0x1fffU;     // 10 mantissa bits remain
+    return __float2half_rz(__uint_as_float(b));
+}
+constexpr float kS16Scale = 32767.0f;   // fixed point: value = code / 32767, |code| <= 32767
+__device__ __forceinline__ int16_t s16_sr(float x, uint32_t r16) {
+    const float y = fmaf(x, kS16Scale, (float)(r16 & 0xffffU) * (1.0f / 65536.0f));
+    return (int16_t)fminf(fmaxf(floorf(y), -kS16Scale), kS16Scale);
+}
+
 template <class S>
 struct Stor;
 template <>
@@ -183,73 +231,57 @@ struct Stor<float> {
     static __device__ __forceinline__ float4 ld4c(const float* p) { return *reinterpret_cast<const float4*>(p); }
     static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ float ld1c(const float* p) { return *p; }
-    static __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-    static __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ void st4(float* p, float4 v, uint32_t) { *reinterpret_cast<float4*>(p) = v; }
+    static __device__ __forceinline__ void st1(float* p, float v, uint32_t) { *p = v; }
 };
-template <>
-struct Stor<__nv_bfloat16> {
-    using T = __nv_bfloat16;
-    static __device__ __forceinline__ float4 ld4(const T* p) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-        __nv_bfloat162 a, b;
-        memcpy(&a, &u.x, 4);
-        memcpy(&b, &u.y, 4);
-        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
+
+// Shared code of the 16-bit formats: D supplies to_f(uint16) and from_f(float, rbits).
+template <class T, class D>
+struct Stor16 {
+    static __device__ __forceinline__ float4 unpack(uint2 u) {
+        return make_float4(D::to_f((uint16_t)(u.x & 0xffffU)), D::to_f((uint16_t)(u.x >> 16)),
+                           D::to_f((uint16_t)(u.y & 0xffffU)), D::to_f((uint16_t)(u.y >> 16)));
     }
-    static __device__ __forceinline__ float ld1(const T* p) { return __bfloat162float(p[0]); }
-    static __device__ __forceinline__ float ld1c(const T* p) { return __bfloat162float(p[0]); }
-    static __device__ __forceinline__ float4 ld4c(const T* p) {
-        const uint2 u = *reinterpret_cast<const uint2*>(p);
-        __nv_bfloat162 a, b;
-        memcpy(&a, &u.x, 4);
-        memcpy(&b, &u.y, 4);
-        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    static __device__ __forceinline__ float4 ld4(const T* p) { return unpack(__ldg(reinterpret_cast<const uint2*>(p))); }
+    static __device__ __forceinline__ float4 ld4c(const T* p) { return unpack(*reinterpret_cast<const uint2*>(p)); }
+    static __device__ __forceinline__ float ld1(const T* p) {
+        return D::to_f(__ldg(reinterpret_cast<const unsigned short*>(p)));
     }
-    static __device__ __forceinline__ void st4(T* p, float4 v) {
-        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    static __device__ __forceinline__ float ld1c(const T* p) { return D::to_f(*reinterpret_cast<const uint16_t*>(p)); }
+    static __device__ __forceinline__ void st4(T* p, float4 v, uint32_t k) {
+        uint32_t r[4];
+        rbits4(k, r);
         uint2 u;
-        memcpy(&u.x, &a, 4);
-        memcpy(&u.y, &b, 4);
+        u.x = (uint32_t)D::from_f(v.x, r[0]) | ((uint32_t)D::from_f(v.y, r[1]) << 16);
+        u.y = (uint32_t)D::from_f(v.z, r[2]) | ((uint32_t)D::from_f(v.w, r[3]) << 16);
         *reinterpret_cast<uint2*>(p) = u;
     }
-    static __device__ __forceinline__ void st1(T* p, float v) { p[0] = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st1(T* p, float v, uint32_t k) {
+        *reinterpret_cast<uint16_t*>(p) = D::from_f(v, hash32(k) & 0xffffU);
+    }
+};
+struct Bf16Bits {
+    static __device__ __forceinline__ float to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return __bfloat16_as_ushort(bf16_sr(x, r)); }
+};
+struct F16Bits {
+    static __device__ __forceinline__ float to_f(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return __half_as_ushort(f16_sr(x, r)); }
+};
+struct S16Bits {
+    static __device__ __forceinline__ float to_f(uint16_t b) { return (float)(int16_t)b * (1.0f / kS16Scale); }
+    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return (uint16_t)s16_sr(x, r); }
 };
 template <>
-struct Stor<__half> {
-    using T = __half;
-    static __device__ __forceinline__ float4 ld4(const T* p) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-        __half2 a, b;
-        memcpy(&a, &u.x, 4);
-        memcpy(&b, &u.y, 4);
-        const float2 fa = __half22float2(a), fb = __half22float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-    static __device__ __forceinline__ float ld1(const T* p) { return __half2float(p[0]); }
-    static __device__ __forceinline__ float ld1c(const T* p) { return __half2float(p[0]); }
-    static __device__ __forceinline__ float4 ld4c(const T* p) {
-        const uint2 u = *reinterpret_cast<const uint2*>(p);
-        __half2 a, b;
-        memcpy(&a, &u.x, 4);
-        memcpy(&b, &u.y, 4);
-        const float2 fa = __half22float2(a), fb = __half22float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-    static __device__ __forceinline__ void st4(T* p, float4 v) {
-        const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
-        uint2 u;
-        memcpy(&u.x, &a, 4);
-        memcpy(&u.y, &b, 4);
-        *reinterpret_cast<uint2*>(p) = u;
-    }
-    static __device__ __forceinline__ void st1(T* p, float v) { p[0] = __float2half_rn(v); }
-};
+struct Stor<__nv_bfloat16> : Stor16<__nv_bfloat16, Bf16Bits> {};
+template <>
+struct Stor<__half> : Stor16<__half, F16Bits> {};
+template <>
+struct Stor<int16_t> : Stor16<int16_t, S16Bits> {};
 
 // Bytes per element of a tvs_storage value (0 if unknown).
 inline size_t storage_bytes(int storage) {
-    return storage == TVS_F32 ? 4 : (storage == TVS_BF16 || storage == TVS_F16) ? 2 : 0;
+    return storage == TVS_F32 ? 4 : (storage == TVS_BF16 || storage == TVS_F16 || storage == TVS_S16) ? 2 : 0;
 }
 
 // Runs the statement (the variadic arguments) with the type S for the
@@ -262,6 +294,10 @@ inline size_t storage_bytes(int storage) {
         } break;                             \
         case TVS_F16: {                      \
             using S = __half;                \
+            __VA_ARGS__;                     \
+        } break;                             \
+        case TVS_S16: {                      \
+            using S = int16_t;               \
             __VA_ARGS__;                     \
         } break;                             \
         default: {                           \

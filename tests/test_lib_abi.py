@@ -58,6 +58,7 @@ def test_workspace_sizes(lib):
     assert L.tvs_workspace_bytes(1, 8193, 64, None, 0) == 0       # too large
     assert L.tvs_workspace_bytes(1, 64, 64, None, 1) == 0         # step 1 keeps an FP32 dual
     assert L.tvs_workspace_bytes(2, 64, 64, None, 7) == 0         # no such storage
+    assert L.tvs_workspace_bytes(2, 64, 64, None, 3) == lib.workspace_bytes(2, 64, 64, storage=1)
     # 16-bit storage halves the two step-2 dual buffers (and the Schwarz warm starts)
     n = 1024
     f32, bf16, f16 = (lib.workspace_bytes(2, n, n, storage=s) for s in (0, 1, 2))
