@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gap-runs", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving sections")
+    ap.add_argument("--batch-count", type=int, default=256, help="images of the batched section")
+    ap.add_argument("--serve-count", type=int, default=32, help="requests per arrival rate (serving section)")
     ap.add_argument("--large-n", type=int, default=8192,
                     help="side of the large-image measurements (0 = skip them)")
     ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise"], default=None,
@@ -330,6 +333,10 @@ def run_gpu(args):
     large = None
     if rank == 0 and args.large_n > 0:
         large = run_large(args, B, dev, torch)
+    batched = serving = None
+    if rank == 0 and not args.no_serving:
+        batched = run_batched(args, B, dev, torch)
+        serving = run_serving(args, B, dev, torch)
 
     line = None
     if rank == 0:
@@ -347,6 +354,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": N * N * 4},
             "time_to_rel_gap_1e-4": gap,
             "large": large,
+            "batched": batched,
+            "serving": serving,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(d0_np)
@@ -473,6 +482,144 @@ def run_large(args, B, dev, torch):
                                                          "rel_gap": r_s.report["rel_gap"]}
         del wss
         torch.cuda.empty_cache()
+    return out
+
+
+ENGINE_TILE, ENGINE_OVERLAP, ENGINE_K = 64, 4, 16
+
+
+def _engine_cfg(B, storage, tol=1e-4, max_live=256, tile=ENGINE_TILE, overlap=ENGINE_OVERLAP, k=ENGINE_K):
+    return B.make_engine_config(DELTA, ALPHA, EPS, B.make_iter(20000, T, tol, 10),
+                                B.make_iter(5000, T, tol, 2, storage=storage), tile, overlap, k, max_live)
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def run_batched(args, B, dev, torch):
+    """Many uneven images, each to relative gap 1e-4 in both steps.
+
+    Sides log-uniform in [128, 1024] (independently per axis), sigma U[0.05,
+    0.15]; all images are submitted to the engine at once: step 2 of every
+    resident image runs in shared Schwarz launches (64-pixel cores, overlap
+    4, k = 16).  Compared with a sequential loop of per-image global FP32
+    tvs_denoise calls on the same images.
+    """
+    from synth import SceneSpec, noisy_scene, mixed_batch_sizes
+    sizes = mixed_batch_sizes(args.batch_count, 128, 1024, seed=1000)
+    imgs = [torch.from_numpy(noisy_scene(SceneSpec(r, c, 1000 + i, sg, True))[1].astype(np.float32)).to(dev)
+            for i, (r, c, sg) in enumerate(sizes)]
+    mpx = sum(r * c for r, c, _ in sizes) / 1e6
+    out = {"images": len(sizes), "mpixel": mpx, "sides": "log-uniform [128, 1024] per axis",
+           "rel_gap_tol": 1e-4}
+    # autotune (tile, overlap, k) on the image of median area
+    med = sorted(range(len(sizes)), key=lambda i: sizes[i][0] * sizes[i][1])[len(sizes) // 2]
+    t0 = time.perf_counter()
+    tau_med = B.tvs_step1(imgs[med], DELTA, B.make_iter(20000, T, 1e-4, 10)).out
+    (tile, ov, kk), tms = B.tvs_tune_schwarz2(imgs[med], tau_med, ALPHA, EPS, B.make_iter(5000, T, 1e-4, 2))
+    out["autotune"] = {"image": list(sizes[med][:2]), "tile": tile, "overlap": ov, "k": kk, "best_ms": tms,
+                       "candidates": "tile {32,48,64} x overlap {2,4,8} x k {4,8,16}",
+                       "seconds": time.perf_counter() - t0}
+    for storage, name in ((0, "f32"), (3, "s16")):
+        c = _engine_cfg(B, storage, tile=tile, overlap=ov, k=kk)
+        eng = B.Engine(c, 64 << 30, dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i, im in enumerate(imgs):
+            eng.submit(i, im)
+        steps, worst = 0, 0.0
+        while eng.pending():
+            for rid, d, r1, r2 in eng.step():
+                worst = max(worst, r1["rel_gap"], r2["rel_gap"])
+            steps += 1
+        torch.cuda.synchronize(dev)
+        sec = time.perf_counter() - t0
+        eng.close()
+        del eng
+        out[f"engine_{name}"] = {"seconds": sec, "images_per_s": len(imgs) / sec, "ms_per_mpixel": sec * 1e3 / mpx,
+                                 "engine_steps": steps, "max_rel_gap": worst}
+    # sequential per-image global FP32
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for im in imgs:
+        B.tvs_denoise(im, DELTA, ALPHA, EPS, B.make_iter(20000, T, 1e-4, 10), B.make_iter(50000, T, 1e-4, 10))
+    torch.cuda.synchronize(dev)
+    sec = time.perf_counter() - t0
+    out["sequential_global_f32"] = {"seconds": sec, "images_per_s": len(imgs) / sec, "ms_per_mpixel": sec * 1e3 / mpx}
+    return out
+
+
+def run_serving(args, B, dev, torch):
+    """Poisson arrivals of denoise requests served by the engine.
+
+    Sides log-uniform in [256, 4096] per axis, sigma U[0.05, 0.15]; each
+    request runs to relative gap 1e-4 in both steps with its state resident on
+    the device; admission by a 64 GB HBM budget.  The request payload is copied
+    from pinned host memory at arrival and d is copied back when done, both
+    inside the measured latency.  The rate is swept as a fraction of the
+    engine's measured closed-loop capacity, and the same arrivals are served
+    by a sequential per-request global FP32 server (tvs_denoise) for
+    comparison.  Latency = completion time - arrival time.
+    """
+    from synth import SceneSpec, noisy_scene, mixed_batch_sizes, poisson_arrivals
+    n = args.serve_count
+    sizes = mixed_batch_sizes(n, 256, 4096, seed=3000)
+    host = [torch.from_numpy(noisy_scene(SceneSpec(r, c, 3000 + i, sg, True))[1].astype(np.float32)).pin_memory()
+            for i, (r, c, sg) in enumerate(sizes)]
+    mpx = sum(r * c for r, c, _ in sizes) / 1e6
+    c = _engine_cfg(B, 0, max_live=64)
+
+    def serve_engine(arr):
+        eng = B.Engine(c, 64 << 30, dev)
+        outs = [torch.empty(h.shape, dtype=torch.float32).pin_memory() for h in host]
+        lat, nxt, done = [], 0, 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        while done < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arr[nxt] <= now:
+                eng.submit(nxt, host[nxt].to(dev, non_blocking=True))
+                nxt += 1
+            if eng.pending() == 0:
+                continue
+            for rid, d, r1, r2 in eng.step():
+                outs[rid].copy_(d)                        # synchronous device -> host copy of the result
+                lat.append(time.perf_counter() - t0 - arr[rid])
+                done += 1
+        sec = time.perf_counter() - t0
+        eng.close()
+        return lat, sec
+
+    def serve_sequential(arr):
+        lat = []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(n):
+            while time.perf_counter() - t0 < arr[i]:
+                pass
+            d0 = host[i].to(dev, non_blocking=True)
+            d, _, _, _ = B.tvs_denoise(d0, DELTA, ALPHA, EPS, B.make_iter(20000, T, 1e-4, 10),
+                                       B.make_iter(50000, T, 1e-4, 10))
+            d.cpu()
+            lat.append(time.perf_counter() - t0 - arr[i])
+        return lat, time.perf_counter() - t0
+
+    # closed-loop capacity: everything arrives at t = 0
+    lat0, sec0 = serve_engine(np.zeros(n))
+    cap = n / sec0
+    out = {"requests_per_rate": n, "mpixel_per_request_mean": mpx / n, "sides": "log-uniform [256, 4096] per axis",
+           "hbm_budget_gb": 64, "engine": "tile 64, overlap 4, k 16, FP32",
+           "closed_loop": {"images_per_s": cap, "p50_s": _pct(lat0, 50), "p99_s": _pct(lat0, 99)}, "rates": []}
+    for frac in (0.5, 0.9):
+        rate = frac * cap
+        arr = poisson_arrivals(n, rate, seed=4000)
+        le, se = serve_engine(arr)
+        ls, ss = serve_sequential(arr)
+        out["rates"].append({"rate_per_s": rate, "fraction_of_capacity": frac,
+                             "engine": {"p50_s": _pct(le, 50), "p99_s": _pct(le, 99), "images_per_s": n / se},
+                             "sequential_global_f32": {"p50_s": _pct(ls, 50), "p99_s": _pct(ls, 99),
+                                                       "images_per_s": n / ss}})
     return out
 
 

@@ -194,6 +194,78 @@ typedef struct {
 int tvs_profile_enable(int on);
 int tvs_profile_read(tvs_kernel_time* out, int cap);
 
+/* ---------------------------------------------------------------------------
+ * Batching and serving engine.  The paper has no counterpart (it denoises one
+ * image at a time); this is the request loop around the two steps above.
+ *   - Requests of any size (n2, n1 in [2, 8192]) are queued by
+ *     tvs_engine_submit and admitted first-in first-out while their state
+ *     (tvs_engine_request_bytes) fits the free part of the caller's device
+ *     pool and fewer than max_live requests are resident.
+ *   - Each tvs_engine_step advances every resident request: step 1 (TFS) by
+ *     it1.check_every updates per request, step 2 (IRV1 under the Schwarz
+ *     decomposition with cores of at most `tile` pixels, overlap `overlap`,
+ *     k_inner inner updates) by it2.check_every outer iterations in launches
+ *     shared by all resident step-2 requests.  It then synchronizes `stream`
+ *     once, moves requests whose relative duality gap reached the step's
+ *     rel_gap_tol (or whose max_iter passed; a chunk may pass it by less than
+ *     check_every) to the next step, writes d of finished requests and
+ *     releases their pool blocks.
+ *   - All request state stays on the device between steps.  d0 and d are the
+ *     caller's device buffers (n2 x n1 dense float); d0 must stay valid until
+ *     the request is returned as done.
+ *   - The pool is a caller-owned 256-byte-aligned device buffer; the engine
+ *     allocates no device memory itself (pinned host memory and CUDA streams
+ *     are created at tvs_engine_create).  Not thread-safe: one host thread
+ *     drives an engine.
+ * ------------------------------------------------------------------------- */
+typedef struct tvs_engine tvs_engine;
+typedef struct {
+    double   delta, alpha, eps;   /* model weights, as for tvs_denoise                    */
+    tvs_iter it1;                 /* step 1: t, rel_gap_tol, max_iter, check_every >= 1  */
+    tvs_iter it2;                 /* step 2 (outer iterations), storage as for tvs_step2 */
+    int      tile, overlap, k_inner;   /* step-2 subdomains; tile >= 16, 2 overlap < tile */
+    int      max_live;            /* requests resident at once                           */
+} tvs_engine_config;
+
+/* Pool bytes one request of n2 x n1 needs (0: invalid size or config). */
+size_t tvs_engine_request_bytes(const tvs_engine_config* cfg, int n2, int n1);
+/* Pool bytes the engine keeps for itself (descriptor arrays). */
+size_t tvs_engine_pool_overhead(const tvs_engine_config* cfg);
+/* TVS_ERR_UNSUPPORTED: tile + overlap too large for one CTA per subdomain. */
+tvs_status tvs_engine_create(const tvs_engine_config* cfg, void* pool, size_t pool_bytes,
+                             cudaStream_t stream, tvs_engine** out);
+/* Queue a request.  TVS_ERR_UNSUPPORTED if it could never fit the pool. */
+tvs_status tvs_engine_submit(tvs_engine* e, long long id, const float* d0, int n2, int n1, float* d);
+/* One engine step (see above).  Up to `cap` finished requests are returned
+ * in done_ids (and, if done_reports is not NULL, their step-1 and step-2
+ * reports at done_reports[2k], done_reports[2k+1]); more wait for the next
+ * call. */
+tvs_status tvs_engine_step(tvs_engine* e, long long* done_ids, tvs_report* done_reports, int cap,
+                           int* n_done);
+/* Requests queued, resident or finished but not yet returned. */
+int tvs_engine_pending(const tvs_engine* e);
+void tvs_engine_destroy(tvs_engine* e);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner of the step-2 Schwarz decomposition.  The paper leaves the
+ * subdomain size, the overlap and the number of inner updates free
+ * (Sec. 6.1-6.3); this measures them.  Every candidate (core size tiles[a]:
+ * m = ceil(n / tile) subdomains per axis, overlap overlaps[b], k = ks[c]) runs
+ * tvs_schwarz step 2 on (d0, tau) from a zero dual until it->rel_gap_tol
+ * (> 0, checked every it->check_every >= 1 outer iterations, at most
+ * it->max_iter), timed with CUDA events on `stream` (the call synchronizes
+ * it).  Candidates whose cores are narrower than the overlap are skipped.
+ *   best    : out, {tile, overlap, k} of the fastest candidate that reached the
+ *             tolerance; best_ms (may be NULL) its time in milliseconds.
+ *   returns : TVS_ERR_NOT_CONVERGED if no candidate reached the tolerance.
+ *   ws      : tvs_tune_workspace_bytes(...) bytes. */
+size_t tvs_tune_workspace_bytes(int n2, int n1, const int* tiles, int ntiles, const int* overlaps,
+                                int noverlaps, int storage);
+tvs_status tvs_tune_schwarz2(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
+                             const tvs_iter* it, const int* tiles, int ntiles, const int* overlaps,
+                             int noverlaps, const int* ks, int nks, void* ws, size_t ws_bytes,
+                             cudaStream_t stream, int* best, float* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

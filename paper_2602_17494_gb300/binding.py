@@ -40,6 +40,12 @@ class TvsDecomp(ctypes.Structure):
                 ("k_inner", ctypes.c_int), ("alpha_hat", ctypes.c_double)]
 
 
+class TvsEngineConfig(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("eps", ctypes.c_double),
+                ("it1", TvsIter), ("it2", TvsIter), ("tile", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("k_inner", ctypes.c_int), ("max_live", ctypes.c_int)]
+
+
 class TvsError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = _lib.tvs_status_string(status).decode()
@@ -78,6 +84,28 @@ def _load() -> ctypes.CDLL:
     lib.tvs_profile_enable.argtypes = [I]
     lib.tvs_profile_read.restype = I
     lib.tvs_profile_read.argtypes = [ctypes.POINTER(TvsKernelTime), I]
+    E = ctypes.POINTER(TvsEngineConfig)
+    lib.tvs_engine_request_bytes.restype = S
+    lib.tvs_engine_request_bytes.argtypes = [E, I, I]
+    lib.tvs_engine_pool_overhead.restype = S
+    lib.tvs_engine_pool_overhead.argtypes = [E]
+    lib.tvs_engine_create.restype = I
+    lib.tvs_engine_create.argtypes = [E, P, S, P, ctypes.POINTER(P)]
+    lib.tvs_engine_submit.restype = I
+    lib.tvs_engine_submit.argtypes = [P, ctypes.c_longlong, P, I, I, P]
+    lib.tvs_engine_step.restype = I
+    lib.tvs_engine_step.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(TvsReport), I,
+                                    ctypes.POINTER(I)]
+    lib.tvs_engine_pending.restype = I
+    lib.tvs_engine_pending.argtypes = [P]
+    lib.tvs_engine_destroy.restype = None
+    lib.tvs_engine_destroy.argtypes = [P]
+    IP = ctypes.POINTER(I)
+    lib.tvs_tune_workspace_bytes.restype = S
+    lib.tvs_tune_workspace_bytes.argtypes = [I, I, IP, I, IP, I, I]
+    lib.tvs_tune_schwarz2.restype = I
+    lib.tvs_tune_schwarz2.argtypes = [P, P, I, I, D, D, ctypes.POINTER(TvsIter), IP, I, IP, I, IP, I, P, S, P, IP,
+                                      ctypes.POINTER(ctypes.c_float)]
     return lib
 
 
@@ -88,8 +116,11 @@ class TvsKernelTime(ctypes.Structure):
 _lib = _load()
 
 # Every symbol that include/tvs.h declares.
-EXPORTED = ["tvs_denoise", "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
-            "tvs_project_noalloc", "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2", "tvs_version",
+EXPORTED = ["tvs_denoise", "tvs_engine_create", "tvs_engine_destroy", "tvs_engine_pending",
+            "tvs_engine_pool_overhead", "tvs_engine_request_bytes", "tvs_engine_step", "tvs_engine_submit",
+            "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
+            "tvs_project_noalloc", "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2",
+            "tvs_tune_schwarz2", "tvs_tune_workspace_bytes", "tvs_version",
             "tvs_workspace_bytes"]
 
 
@@ -234,3 +265,85 @@ def tvs_profile_read() -> dict:
     buf = (TvsKernelTime * 16)()
     n = _lib.tvs_profile_read(buf, 16)
     return {buf[i].name.decode(): (buf[i].launches, buf[i].ms) for i in range(n)}
+
+
+# ---------------------------------------------------------------------------
+# batching / serving engine (tvs_engine_*)
+# ---------------------------------------------------------------------------
+def make_engine_config(delta: float, alpha: float, eps: float, it1: TvsIter, it2: TvsIter, tile: int = 64,
+                       overlap: int = 4, k_inner: int = 16, max_live: int = 64) -> TvsEngineConfig:
+    return TvsEngineConfig(float(delta), float(alpha), float(eps), it1, it2, int(tile), int(overlap), int(k_inner),
+                           int(max_live))
+
+
+class Engine:
+    """Owns a device pool and a tvs_engine; requests are torch tensors on that device."""
+
+    def __init__(self, cfg: TvsEngineConfig, pool_bytes: int, device=None):
+        self.cfg = cfg
+        self.device = torch.device(device or "cuda")
+        over = _lib.tvs_engine_pool_overhead(ctypes.byref(cfg))
+        if over == 0:
+            raise ValueError("invalid engine configuration")
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=self.device)
+        self.handle = ctypes.c_void_p()
+        st = _lib.tvs_engine_create(ctypes.byref(cfg), ctypes.c_void_p(self.pool.data_ptr()), self.pool.numel(),
+                                    _stream(self.device), ctypes.byref(self.handle))
+        _check(st, "tvs_engine_create", False)
+        self.requests = {}
+
+    def request_bytes(self, n2: int, n1: int) -> int:
+        return int(_lib.tvs_engine_request_bytes(ctypes.byref(self.cfg), n2, n1))
+
+    def submit(self, rid: int, d0: torch.Tensor, d: torch.Tensor | None = None) -> torch.Tensor:
+        n2, n1 = d0.shape
+        d = torch.empty_like(d0) if d is None else d
+        st = _lib.tvs_engine_submit(self.handle, int(rid), _ptr(d0), n2, n1, _ptr(d))
+        _check(st, "tvs_engine_submit", False)
+        self.requests[int(rid)] = (d0, d)     # keep the buffers alive until done
+        return d
+
+    def step(self, cap: int = 256):
+        ids = (ctypes.c_longlong * max(cap, 1))()
+        reps = (TvsReport * (2 * max(cap, 1)))()
+        n = ctypes.c_int()
+        st = _lib.tvs_engine_step(self.handle, ids, reps, cap, ctypes.byref(n))
+        _check(st, "tvs_engine_step", False)
+        out = []
+        for k in range(n.value):
+            d0, d = self.requests.pop(ids[k])
+            out.append((ids[k], d, reps[2 * k].as_dict(), reps[2 * k + 1].as_dict()))
+        return out
+
+    def pending(self) -> int:
+        return int(_lib.tvs_engine_pending(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.tvs_engine_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tvs_tune_schwarz2(d0: torch.Tensor, tau: torch.Tensor, alpha: float, eps: float, it: TvsIter,
+                      tiles=(32, 48, 64), overlaps=(2, 4, 8), ks=(4, 8, 16)):
+    """Fastest (tile, overlap, k) to it.rel_gap_tol on this image, and its milliseconds."""
+    n2, n1 = d0.shape
+    arr = lambda v: (ctypes.c_int * len(v))(*[int(x) for x in v])
+    T, O, K = arr(tiles), arr(overlaps), arr(ks)
+    need = _lib.tvs_tune_workspace_bytes(n2, n1, T, len(tiles), O, len(overlaps), it.storage)
+    if need == 0:
+        raise ValueError("no valid candidate decomposition")
+    ws = torch.empty(int(need), dtype=torch.uint8, device=d0.device)
+    best = (ctypes.c_int * 3)()
+    ms = ctypes.c_float()
+    st = _lib.tvs_tune_schwarz2(_ptr(d0), _ptr(tau), n2, n1, float(alpha), float(eps), ctypes.byref(it), T, len(tiles),
+                                O, len(overlaps), K, len(ks), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                _stream(d0.device), best, ctypes.byref(ms))
+    _check(st, "tvs_tune_schwarz2", False)
+    return (best[0], best[1], best[2]), ms.value

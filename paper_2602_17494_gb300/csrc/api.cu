@@ -1,8 +1,7 @@
 // C ABI of libtvs (declared in include/tvs.h): argument checks, workspace
 // layout and the host-side iteration drivers.  All arithmetic of the method
 // runs in the kernels of dct.cu, tfs.cu, irv.cu and schwarz.cu.
-#include "tvs_internal.cuh"
-#include "launchers.h"
+#include "drivers.h"
 
 #include <cmath>
 #include <cstdio>
@@ -22,29 +21,7 @@ void set_error(const char* what, cudaError_t e) {
 
 void set_error_text(const char* msg) { g_last_error = msg; }
 
-constexpr int kMaxSide = 8192;   // transform length <= 8193 keeps one FFT line in shared memory
-
-#define TVS_CUDA(call)                                       \
-    do {                                                     \
-        cudaError_t e_ = (call);                             \
-        if (e_ != cudaSuccess) {                             \
-            set_error(#call, e_);                            \
-            return TVS_ERR_CUDA;                             \
-        }                                                    \
-    } while (0)
-
-// ---------------------------------------------------------------------------
-// Workspace layouts
-// ---------------------------------------------------------------------------
-struct Step1Layout {
-    int R, C, P;
-    long plane;
-    PoissonPlans pp;
-    float *pa, *pb, *f1, *S;
-    RedBuf red;
-};
-
-static size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
+size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
     L.R = n2 + 1;
     L.C = n1 + 1;
     L.P = round_up(L.C, kPitchAlign);
@@ -58,16 +35,8 @@ static size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
     return cv.used();
 }
 
-struct Step2Layout {
-    int R, C, P;
-    long plane;
-    int st;            // tvs_storage of the dual p (pa, pb)
-    void *pa, *pb;
-    float* f2;
-    RedBuf red;
-};
 
-static size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int storage) {
+size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int storage) {
     L.R = n2;
     L.C = n1;
     L.P = round_up(L.C, kPitchAlign);
@@ -80,14 +49,8 @@ static size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int stora
     return cv.used();
 }
 
-struct ProjLayout {
-    int P;
-    long plane;
-    PoissonPlans pp;
-    float *u, *S;
-};
 
-static size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
+size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
     L.P = round_up(cols, kPitchAlign);
     L.plane = (long)rows * L.P;
     carve_poisson(cv, L.pp, rows, cols);
@@ -99,10 +62,10 @@ static size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
 // ---------------------------------------------------------------------------
 // Checks
 // ---------------------------------------------------------------------------
-static bool side_ok(int n) { return n >= 2 && n <= kMaxSide; }
+bool side_ok(int n) { return n >= 2 && n <= kMaxSide; }
 
 // step 1 keeps its dual in FP32; step 2 also stores it as bf16 or fp16
-static tvs_status check_iter(const tvs_iter* it, bool narrow_ok) {
+tvs_status check_iter(const tvs_iter* it, bool narrow_ok) {
     if (!it) return TVS_ERR_ARG;
     if (it->max_iter < 0 || !(it->t > 0.0) || it->t > 0.125 || it->rel_gap_tol < 0.0) return TVS_ERR_ARG;
     if (storage_bytes(it->storage) == 0) return TVS_ERR_ARG;
@@ -110,12 +73,12 @@ static tvs_status check_iter(const tvs_iter* it, bool narrow_ok) {
     return TVS_OK;
 }
 
-static tvs_status check_ws(void* ws, size_t ws_bytes, size_t need) {
+tvs_status check_ws(void* ws, size_t ws_bytes, size_t need) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need) return TVS_ERR_WORKSPACE;
     return TVS_OK;
 }
 
-static tvs_status read_result(const RedBuf& rb, int nblocks, cudaStream_t s, double out[kRedSlots]) {
+tvs_status read_result(const RedBuf& rb, int nblocks, cudaStream_t s, double out[kRedSlots]) {
     unsigned err = 0;
     TVS_CUDA(finalize_red(rb, nblocks, s));
     TVS_CUDA(cudaMemcpyAsync(out, rb.result, kRedSlots * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -128,7 +91,7 @@ static tvs_status read_result(const RedBuf& rb, int nblocks, cudaStream_t s, dou
     return TVS_OK;
 }
 
-static void report_tfs(const double r[kRedSlots], double delta, int iters, tvs_report* rep) {
+void report_tfs(const double r[kRedSlots], double delta, int iters, tvs_report* rep) {
     const double tv = delta * r[0];
     const double e = tv + 0.5 * delta * r[3];
     const double gap = delta * r[1];
@@ -141,7 +104,7 @@ static void report_tfs(const double r[kRedSlots], double delta, int iters, tvs_r
     rep->max_p = r[4];
 }
 
-static void report_irv1(const double r[kRedSlots], double alpha, int iters, tvs_report* rep) {
+void report_irv1(const double r[kRedSlots], double alpha, int iters, tvs_report* rep) {
     const double tv = r[0] / alpha;
     const double e = tv + r[3] / (2.0 * alpha);
     const double gap = r[1] / alpha;
@@ -155,26 +118,26 @@ static void report_irv1(const double r[kRedSlots], double alpha, int iters, tvs_
 }
 
 // Copy `planes` dense planes of rows x cols into / out of pitched storage.
-static cudaError_t to_pitched(float* dst, int dpitch, const float* src, int rows, int cols, int planes,
+cudaError_t to_pitched(float* dst, int dpitch, const float* src, int rows, int cols, int planes,
                              cudaStream_t s) {
     return cudaMemcpy2DAsync(dst, (size_t)dpitch * sizeof(float), src, (size_t)cols * sizeof(float),
                              (size_t)cols * sizeof(float), (size_t)rows * planes, cudaMemcpyDeviceToDevice, s);
 }
-static cudaError_t from_pitched(float* dst, const float* src, int spitch, int rows, int cols, int planes,
+cudaError_t from_pitched(float* dst, const float* src, int spitch, int rows, int cols, int planes,
                                cudaStream_t s) {
     return cudaMemcpy2DAsync(dst, (size_t)cols * sizeof(float), src, (size_t)spitch * sizeof(float),
                              (size_t)cols * sizeof(float), (size_t)rows * planes, cudaMemcpyDeviceToDevice, s);
 }
 // The caller's dense float dual into / out of the step-2 state (any storage).
-static cudaError_t p2_in(const Step2Layout& L, const float* src, cudaStream_t s) {
+cudaError_t p2_in(const Step2Layout& L, const float* src, cudaStream_t s) {
     if (L.st == TVS_F32) return to_pitched(static_cast<float*>(L.pa), L.P, src, L.R, L.C, 2, s);
     return convert_planes(L.pa, L.st, L.P, L.plane, src, TVS_F32, L.C, (long)L.R * L.C, L.R, L.C, 2, s);
 }
-static cudaError_t p2_out(const Step2Layout& L, float* dst, const void* cur, cudaStream_t s) {
+cudaError_t p2_out(const Step2Layout& L, float* dst, const void* cur, cudaStream_t s) {
     if (L.st == TVS_F32) return from_pitched(dst, static_cast<const float*>(cur), L.P, L.R, L.C, 2, s);
     return convert_planes(dst, TVS_F32, L.C, (long)L.R * L.C, cur, L.st, L.P, L.plane, L.R, L.C, 2, s);
 }
-static cudaError_t p2_zero(const Step2Layout& L, cudaStream_t s) {
+cudaError_t p2_zero(const Step2Layout& L, cudaStream_t s) {
     return cudaMemsetAsync(L.pa, 0, 2 * (size_t)L.plane * storage_bytes(L.st), s);
 }
 
@@ -182,7 +145,7 @@ static cudaError_t p2_zero(const Step2Layout& L, cudaStream_t s) {
 // Drivers
 // ---------------------------------------------------------------------------
 // f1 = P_K tau0 / delta into L.f1 (uses L.S as scratch).
-static tvs_status tfs_setup(const Step1Layout& L, const float* d0, int n2, int n1, double delta, cudaStream_t s) {
+tvs_status tfs_setup(const Step1Layout& L, const float* d0, int n2, int n1, double delta, cudaStream_t s) {
     TVS_CUDA(cudaMemsetAsync(L.red.err, 0, sizeof(unsigned), s));
     TVS_CUDA(build_poisson(L.pp, s));
     TVS_CUDA(launch_tau0(d0, n1, n2, n1, L.f1, L.P, L.plane, s));
@@ -284,7 +247,7 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
     return TVS_OK;
 }
 
-static tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1, double alpha,
+tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1, double alpha,
                                const tvs_iter& it, float* d, float* p_user, cudaStream_t s, tvs_report* rep) {
     if (p_user) TVS_CUDA(p2_in(L, p_user, s));
     else TVS_CUDA(p2_zero(L, s));

@@ -1,0 +1,469 @@
+// Batching and serving engine (include/tvs.h, tvs_engine_*).  The paper
+// denoises one image at a time; this host runtime keeps many requests of
+// different sizes resident on the device and advances them together:
+//   * admission: FIFO, a request is admitted when its state fits the free
+//     part of the caller's device pool and a slot is free;
+//   * step 1 (TFS, Algorithm 1): each request runs its own chunk of updates,
+//     spread over a few side streams so that small images overlap;
+//   * step 2 (IRV1 under Algorithm 2 with Algorithm 3): all live step-2
+//     requests share every launch -- one small-subdomain tile launch and one
+//     strip launch per outer iteration cover the subdomains of all of them;
+//   * every engine step ends with one stream synchronization; requests whose
+//     relative duality gap reached the tolerance move on (or finish: d is
+//     written to the caller's buffer and the pool block is released).
+// All state stays on the device between steps; the host keeps only indices
+// and the per-request reduction results.
+#include "drivers.h"
+
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <map>
+#include <vector>
+
+namespace tvs {
+
+namespace {
+
+constexpr int kSideStreams = 8;
+
+// First-fit allocator over [0, size) of the caller's pool (256-byte units).
+class PoolAlloc {
+public:
+    explicit PoolAlloc(size_t size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = round_up_sz(bytes, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_[*off] = bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off) {
+        auto u = used_.find(off);
+        if (u == used_.end()) return;
+        size_t start = off, len = u->second;
+        used_.erase(u);
+        auto next = free_.lower_bound(start);
+        if (next != free_.end() && next->first == start + len) {
+            len += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == start) {
+                start = prev->first;
+                len += prev->second;
+                free_.erase(prev);
+            }
+        }
+        free_[start] = len;
+    }
+
+private:
+    std::map<size_t, size_t> free_, used_;
+};
+
+struct Request {
+    long long id;
+    int n2, n1;
+    const float* d0;
+    float* d;
+    size_t off = 0;
+    int stage = 0;          // 1: step 1, 2: step 2
+    int it1 = 0, it2 = 0;   // updates / outer iterations done
+    Step1Layout L1;
+    Step2Layout L2;
+    Schwarz2State S2;
+    float* tau = nullptr;
+    float *cur1 = nullptr, *nxt1 = nullptr;
+    void *cur2 = nullptr, *nxt2 = nullptr;
+    int side = 0;           // side stream of step 1
+    int slot = 0;           // row of the pinned result array
+    bool checked = false;   // a check was enqueued this engine step
+    tvs_report rep[2] = {};
+};
+
+// Step-2 decomposition of an image under the engine's tile policy.
+tvs_decomp tile_decomp(const tvs_engine_config& c, int n2, int n1) {
+    tvs_decomp dd{};
+    dd.m2 = std::max(1, (n2 + c.tile - 1) / c.tile);   // cores of at most tile pixels
+    dd.m1 = std::max(1, (n1 + c.tile - 1) / c.tile);
+    dd.overlap = c.overlap;
+    dd.k_inner = c.k_inner;
+    dd.alpha_hat = 0.0;
+    return dd;
+}
+
+// Carves a request's state: the tvs_denoise layout (step 1, tau, step 2 with
+// its Schwarz warm starts).  Returns the bytes used.
+size_t carve_request(Carver& cv, const tvs_engine_config& c, int n2, int n1, Request* r) {
+    Step1Layout L1;
+    layout_step1(cv, n2, n1, L1);
+    float* tau = cv.take<float>(2 * (size_t)(n2 + 1) * (n1 + 1));
+    Step2Layout L2;
+    layout_step2(cv, n2, n1, L2, c.it2.storage);
+    Schwarz2State S2;
+    const tvs_decomp dd = tile_decomp(c, n2, n1);
+    schwarz2_carve(cv, n2, n1, dd, L2.P, c.it2.storage, S2);
+    if (r) {
+        r->L1 = L1;
+        r->tau = tau;
+        r->L2 = L2;
+        r->S2 = S2;
+    }
+    return cv.used();
+}
+
+}  // namespace
+
+struct EngineImpl {
+    tvs_engine_config cfg;
+    char* pool;
+    size_t pool_bytes;
+    PoolAlloc alloc;
+    cudaStream_t stream;
+    cudaStream_t side[kSideStreams];
+    cudaEvent_t ev_main, ev_side[kSideStreams];
+    std::deque<Request*> queue;
+    std::vector<Request*> live;
+    std::vector<Request*> done;
+    double* host_red = nullptr;       // pinned [max_live][kRedSlots]
+    TileImg* host_imgs = nullptr;     // pinned [2 * max_live]
+    TileImg* dev_imgs = nullptr;      // head of the pool
+    std::vector<int> free_slots;
+    int next_side = 0;
+
+    explicit EngineImpl(size_t n) : alloc(n) {}
+};
+
+}  // namespace tvs
+
+struct tvs_engine {
+    tvs::EngineImpl* impl;
+};
+
+using namespace tvs;
+
+static tvs_status engine_check_cfg(const tvs_engine_config* c) {
+    if (!c || !(c->delta > 0.0) || !(c->alpha > 0.0) || !(c->eps > 0.0)) return TVS_ERR_ARG;
+    tvs_status st = check_iter(&c->it1, false);
+    if (st != TVS_OK) return st;
+    st = check_iter(&c->it2, true);
+    if (st != TVS_OK) return st;
+    if (c->it1.check_every < 1 || c->it2.check_every < 1 || c->it1.max_iter < 1 || c->it2.max_iter < 1)
+        return TVS_ERR_ARG;
+    if (c->tile < 16 || c->overlap < 0 || 2 * c->overlap >= c->tile || c->k_inner < 1 || c->max_live < 1)
+        return TVS_ERR_ARG;
+    int tx, ty, qp;
+    size_t smem;
+    if (!small_tile_shape(c->tile + c->overlap, c->tile + c->overlap, &tx, &ty, &qp, &smem))
+        return TVS_ERR_UNSUPPORTED;   // subdomains must fit the one-CTA-per-subdomain kernel
+    return TVS_OK;
+}
+
+static size_t engine_header_bytes(const tvs_engine_config* c) {
+    return round_up_sz(2 * (size_t)c->max_live * sizeof(TileImg), 256);
+}
+
+extern "C" {
+
+size_t tvs_engine_request_bytes(const tvs_engine_config* cfg, int n2, int n1) {
+    if (engine_check_cfg(cfg) != TVS_OK || !side_ok(n2) || !side_ok(n1)) return 0;
+    const tvs_decomp dd = tile_decomp(*cfg, n2, n1);
+    if (schwarz2_check(n2, n1, dd) != TVS_OK) return 0;
+    Carver cv(nullptr);
+    return carve_request(cv, *cfg, n2, n1, nullptr);
+}
+
+size_t tvs_engine_pool_overhead(const tvs_engine_config* cfg) {
+    if (engine_check_cfg(cfg) != TVS_OK) return 0;
+    return engine_header_bytes(cfg);
+}
+
+tvs_status tvs_engine_create(const tvs_engine_config* cfg, void* pool, size_t pool_bytes, cudaStream_t stream,
+                             tvs_engine** out) {
+    if (!out) return TVS_ERR_ARG;
+    *out = nullptr;
+    tvs_status st = engine_check_cfg(cfg);
+    if (st != TVS_OK) return st;
+    const size_t head = engine_header_bytes(cfg);
+    if (!pool || (reinterpret_cast<uintptr_t>(pool) & 255u) || pool_bytes <= head) return TVS_ERR_WORKSPACE;
+    auto* e = new EngineImpl(pool_bytes - head);
+    e->cfg = *cfg;
+    e->pool = static_cast<char*>(pool) + head;
+    e->pool_bytes = pool_bytes - head;
+    e->stream = stream;
+    e->dev_imgs = static_cast<TileImg*>(pool);
+    bool ok = cudaHostAlloc(reinterpret_cast<void**>(&e->host_red), (size_t)cfg->max_live * kRedSlots * sizeof(double),
+                            cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(reinterpret_cast<void**>(&e->host_imgs), 2 * (size_t)cfg->max_live * sizeof(TileImg),
+                            cudaHostAllocDefault) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->ev_main, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < kSideStreams; ++i)
+        ok = cudaStreamCreateWithFlags(&e->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->ev_side[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        set_error_text("tvs_engine_create: host allocation or stream creation failed");
+        auto* h = new tvs_engine{e};
+        tvs_engine_destroy(h);
+        return TVS_ERR_CUDA;
+    }
+    for (int i = cfg->max_live - 1; i >= 0; --i) e->free_slots.push_back(i);
+    *out = new tvs_engine{e};
+    return TVS_OK;
+}
+
+tvs_status tvs_engine_submit(tvs_engine* h, long long id, const float* d0, int n2, int n1, float* d) {
+    if (!h || !d0 || !d || !side_ok(n2) || !side_ok(n1)) return TVS_ERR_ARG;
+    EngineImpl* e = h->impl;
+    const size_t need = tvs_engine_request_bytes(&e->cfg, n2, n1);
+    if (need == 0) return TVS_ERR_UNSUPPORTED;
+    if (need > e->pool_bytes) return TVS_ERR_UNSUPPORTED;   // could never be admitted
+    auto* r = new Request();
+    r->id = id;
+    r->n2 = n2;
+    r->n1 = n1;
+    r->d0 = d0;
+    r->d = d;
+    e->queue.push_back(r);
+    return TVS_OK;
+}
+
+int tvs_engine_pending(const tvs_engine* h) {
+    if (!h) return 0;
+    return (int)(h->impl->queue.size() + h->impl->live.size() + h->impl->done.size());
+}
+
+void tvs_engine_destroy(tvs_engine* h) {
+    if (!h) return;
+    EngineImpl* e = h->impl;
+    if (e) {
+        cudaStreamSynchronize(e->stream);
+        for (int i = 0; i < kSideStreams; ++i) {
+            if (e->side[i]) {
+                cudaStreamSynchronize(e->side[i]);
+                cudaStreamDestroy(e->side[i]);
+            }
+            if (e->ev_side[i]) cudaEventDestroy(e->ev_side[i]);
+        }
+        if (e->ev_main) cudaEventDestroy(e->ev_main);
+        if (e->host_red) cudaFreeHost(e->host_red);
+        if (e->host_imgs) cudaFreeHost(e->host_imgs);
+        for (Request* r : e->queue) delete r;
+        for (Request* r : e->live) delete r;
+        for (Request* r : e->done) delete r;
+        delete e;
+    }
+    delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One engine step
+// ---------------------------------------------------------------------------
+static tvs_status admit(EngineImpl* e) {
+    while (!e->queue.empty() && !e->free_slots.empty()) {
+        Request* r = e->queue.front();
+        Carver cv0(nullptr);
+        const size_t need = carve_request(cv0, e->cfg, r->n2, r->n1, nullptr);
+        size_t off;
+        if (!e->alloc.alloc(need, &off)) break;   // FIFO: wait until the head fits
+        e->queue.pop_front();
+        r->off = off;
+        Carver cv(e->pool + off);
+        carve_request(cv, e->cfg, r->n2, r->n1, r);
+        r->slot = e->free_slots.back();
+        e->free_slots.pop_back();
+        r->side = e->next_side;
+        e->next_side = (e->next_side + 1) % kSideStreams;
+        cudaStream_t s = e->side[r->side];
+        tvs_status st = tfs_setup(r->L1, r->d0, r->n2, r->n1, e->cfg.delta, s);
+        if (st != TVS_OK) return st;
+        TVS_CUDA(cudaMemsetAsync(r->L1.pa, 0, 4 * (size_t)r->L1.plane * sizeof(float), s));
+        r->cur1 = r->L1.pa;
+        r->nxt1 = r->L1.pb;
+        r->stage = 1;
+        e->live.push_back(r);
+    }
+    return TVS_OK;
+}
+
+// Step-1 chunk of one request on its side stream; the last update of the
+// chunk also evaluates the gap at its input iterate.
+static tvs_status step1_chunk(EngineImpl* e, Request* r) {
+    const Step1Layout& L = r->L1;
+    cudaStream_t s = e->side[r->side];
+    const float t = (float)e->cfg.it1.t, fd = (float)e->cfg.delta;
+    const int n = std::min(e->cfg.it1.check_every, e->cfg.it1.max_iter - r->it1);
+    for (int j = 0; j < n; ++j) {
+        const bool ck = j == n - 1;
+        TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+        TVS_CUDA(launch_tfs_update(r->cur1, r->nxt1, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
+                                   L.red.partial, s));
+        std::swap(r->cur1, r->nxt1);
+    }
+    r->it1 += n;
+    TVS_CUDA(finalize_red(L.red, tfs_blocks(L.R, L.C), s));
+    TVS_CUDA(cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    r->checked = true;
+    return TVS_OK;
+}
+
+// tau of the finished step 1, then the step-2 data f2 and a zero dual (on the
+// main stream, which runs the request's step 2 from the next engine step on).
+static tvs_status step1_to_step2(EngineImpl* e, Request* r) {
+    const Step1Layout& L = r->L1;
+    cudaStream_t s = e->stream;
+    const int n2 = r->n2, n1 = r->n1, R = n2 + 1, C = n1 + 1;
+    TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+    TVS_CUDA(launch_tfs_update(r->cur1, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, (float)e->cfg.it1.t,
+                               (float)e->cfg.delta, false, false, r->tau, C, (long)R * C, L.red.partial, s));
+    TVS_CUDA(launch_xi_f2(r->d0, n1, r->tau, (long)R * C, C, n2, n1, (float)e->cfg.alpha, (float)e->cfg.eps,
+                          r->L2.f2, r->L2.P, s));
+    TVS_CUDA(p2_zero(r->L2, s));
+    TVS_CUDA(cudaMemsetAsync(r->L2.red.err, 0, sizeof(unsigned), s));
+    TVS_CUDA(schwarz2_reset(r->S2, s));
+    r->cur2 = r->L2.pa;
+    r->nxt2 = r->L2.pb;
+    r->stage = 2;
+    return TVS_OK;
+}
+
+// All live step-2 requests: check_every outer iterations in shared launches,
+// then one check per request.
+static tvs_status step2_chunk(EngineImpl* e, std::vector<Request*>& rs) {
+    if (rs.empty()) return TVS_OK;
+    const tvs_engine_config& c = e->cfg;
+    const int nimg = (int)rs.size();
+    int nsub = 0, tx = 1, ty = 1;
+    // every request advances check_every outer iterations (its cap may be
+    // passed by less than one chunk)
+    const int n = c.it2.check_every;
+    uint32_t seed = 0;
+    for (Request* r : rs) seed = hash32(seed ^ (uint32_t)r->it2 ^ (uint32_t)r->id);
+    for (int i = 0; i < nimg; ++i) {
+        Request* r = rs[i];
+        const Schwarz2State& S2 = r->S2;
+        Axis ay{r->n2, S2.m2, S2.s, r->n2}, ax{r->n1, S2.m1, S2.s, r->n1};
+        TileImg a{r->cur2, r->nxt2, r->L2.f2, S2.q, r->L2.P, r->L2.plane, S2.hmax, S2.qp, ay, ax,
+                  (float)S2.alpha_hat, nsub};
+        TileImg b = a;                        // odd outer iterations: buffers swapped
+        b.p = r->nxt2;
+        b.pnext = r->cur2;
+        e->host_imgs[i] = a;
+        e->host_imgs[nimg + i] = b;
+        nsub += S2.m2 * S2.m1;
+        tx = std::max(tx, S2.tx);
+        ty = std::max(ty, S2.ty);
+    }
+    TVS_CUDA(cudaMemcpyAsync(e->dev_imgs, e->host_imgs, 2 * (size_t)nimg * sizeof(TileImg), cudaMemcpyHostToDevice,
+                             e->stream));
+    // the host array is rewritten next step, after this step's synchronization
+    TVS_CUDA(schwarz2_iterate_multi(c.it2.storage, e->dev_imgs, nimg, nsub, tx, ty, c.k_inner, (float)c.it2.t, n,
+                                    seed, e->stream));
+    for (Request* r : rs) {
+        if (n & 1) std::swap(r->cur2, r->nxt2);
+        r->it2 += n;
+        const Step2Layout& L = r->L2;
+        TVS_CUDA(launch_irv1_update(r->cur2, nullptr, L.f2, L.R, L.C, L.P, L.plane, (float)c.it2.t, (float)c.alpha,
+                                    true, false, nullptr, 0, L.red.partial, L.st, 0u, L.red.err, e->stream));
+        TVS_CUDA(finalize_red(L.red, irv1_blocks(L.R, L.C), e->stream));
+        TVS_CUDA(cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
+                                 cudaMemcpyDeviceToHost, e->stream));
+        r->checked = true;
+    }
+    return TVS_OK;
+}
+
+extern "C" tvs_status tvs_engine_step(tvs_engine* h, long long* done_ids, tvs_report* done_reports, int cap,
+                                      int* n_done) {
+    if (!h || !n_done || cap < 0 || (cap > 0 && !done_ids)) return TVS_ERR_ARG;
+    EngineImpl* e = h->impl;
+    const tvs_engine_config& c = e->cfg;
+    *n_done = 0;
+    // side streams start after everything already on the main stream
+    TVS_CUDA(cudaEventRecord(e->ev_main, e->stream));
+    for (int i = 0; i < kSideStreams; ++i) TVS_CUDA(cudaStreamWaitEvent(e->side[i], e->ev_main, 0));
+    tvs_status st = admit(e);
+    if (st != TVS_OK) return st;
+    std::vector<Request*> s2;
+    for (Request* r : e->live) {
+        r->checked = false;
+        if (r->stage == 1) {
+            st = step1_chunk(e, r);
+            if (st != TVS_OK) return st;
+        } else if (r->stage == 2) {
+            s2.push_back(r);
+        }
+    }
+    // all live step-2 requests share the launches of this engine step
+    st = step2_chunk(e, s2);
+    if (st != TVS_OK) return st;
+    for (int i = 0; i < kSideStreams; ++i) {
+        TVS_CUDA(cudaEventRecord(e->ev_side[i], e->side[i]));
+        TVS_CUDA(cudaStreamWaitEvent(e->stream, e->ev_side[i], 0));
+    }
+    TVS_CUDA(cudaStreamSynchronize(e->stream));
+    // transitions
+    std::vector<Request*> finished;
+    for (Request* r : e->live) {
+        if (!r->checked) continue;
+        const double* red = e->host_red + (size_t)r->slot * kRedSlots;
+        if (r->stage == 1) {
+            report_tfs(red, c.delta, r->it1 - 1, &r->rep[0]);
+            if (r->rep[0].rel_gap <= c.it1.rel_gap_tol || r->it1 >= c.it1.max_iter) {
+                st = step1_to_step2(e, r);
+                if (st != TVS_OK) return st;
+            }
+        } else {
+            report_irv1(red, c.alpha, r->it2, &r->rep[1]);
+            if (r->rep[1].rel_gap <= c.it2.rel_gap_tol || r->it2 >= c.it2.max_iter) finished.push_back(r);
+        }
+    }
+    if (!finished.empty()) {
+        for (Request* r : finished) {
+            const Step2Layout& L = r->L2;
+            TVS_CUDA(launch_irv1_update(r->cur2, nullptr, L.f2, L.R, L.C, L.P, L.plane, (float)c.it2.t,
+                                        (float)c.alpha, true, false, r->d, r->n1, L.red.partial, L.st, 0u, L.red.err,
+                                        e->stream));
+        }
+        TVS_CUDA(cudaStreamSynchronize(e->stream));
+        for (Request* r : finished) {
+            unsigned err = 0;
+            TVS_CUDA(cudaMemcpy(&err, r->L2.red.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+            if (err) {
+                set_error_text("a bounded device-side wait gave up (TMA row load)");
+                return TVS_ERR_TIMEOUT;
+            }
+            e->alloc.release(r->off);
+            e->free_slots.push_back(r->slot);
+            e->live.erase(std::find(e->live.begin(), e->live.end(), r));
+            e->done.push_back(r);
+        }
+    }
+    // hand back finished requests
+    int k = 0;
+    while (k < cap && !e->done.empty()) {
+        Request* r = e->done.front();
+        e->done.erase(e->done.begin());
+        done_ids[k] = r->id;
+        if (done_reports) {
+            done_reports[2 * k] = r->rep[0];
+            done_reports[2 * k + 1] = r->rep[1];
+        }
+        delete r;
+        ++k;
+    }
+    *n_done = k;
+    return TVS_OK;
+}

@@ -68,15 +68,16 @@ cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long t
 constexpr int kStrip = 128;      // columns per warp
 constexpr int kChunk = 32;       // output rows per warp
 constexpr int kStreamWarps = 4;  // warps per block
-constexpr int kStages = 3;       // row loads in flight per warp
+constexpr int kRows = 2;         // rows per TMA load (item)
+constexpr int kStages = 2;       // items in flight per warp
 
 template <class S>
 struct StreamGeom {
-    static constexpr int HP = 16 / (int)sizeof(S);          // halo columns of the p box
-    static constexpr int WP = kStrip + 2 * HP;              // p box width (elements)
-    static constexpr int HF = 4, WF = kStrip + 8;           // f2 box (float)
-    static constexpr int PBYTES = 2 * WP * (int)sizeof(S);  // both planes
-    static constexpr int FBYTES = WF * 4;
+    static constexpr int HP = 16 / (int)sizeof(S);                  // halo columns of the p box
+    static constexpr int WP = kStrip + 2 * HP;                      // p box width (elements)
+    static constexpr int HF = 4, WF = kStrip + 8;                   // f2 box (float)
+    static constexpr int PBYTES = 2 * kRows * WP * (int)sizeof(S);  // [plane][row][WP]
+    static constexpr int FBYTES = kRows * WF * 4;                   // [row][WF]
     static constexpr int POFF = 0;
     static constexpr int FOFF = (PBYTES + 127) / 128 * 128;
     static constexpr int STAGE = FOFF + (FBYTES + 127) / 128 * 128;
@@ -89,6 +90,13 @@ constexpr size_t stream_smem_bytes() {
 
 __device__ __forceinline__ float comp(const float4& v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+// sqrt(a^2 + b^2) through the hardware reciprocal square root (about 2 ulp);
+// the 1e-30 keeps rsqrt finite at 0 and is below the resolution of any
+// nonzero a^2 + b^2 that matters here.
+__device__ __forceinline__ float fast_norm(float a, float b) {
+    const float s2 = fmaf(a, a, fmaf(b, b, 1e-30f));
+    return s2 * rsqrtf(s2);
 }
 // 4 consecutive elements of a box row in shared memory, widened to float
 template <class S>
@@ -111,9 +119,9 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
     using G = StreamGeom<S>;
     using St = Stor<S>;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    // TMA destinations are kept 128-byte aligned
-    unsigned char* smem_raw = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) &
-                                                               ~static_cast<uintptr_t>(127));
+    // TMA destinations are kept 128-byte aligned; offsetting the array (not an
+    // integer copy of its address) keeps the accesses in the shared space
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int strip = blockIdx.x;
@@ -129,9 +137,11 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
     (void)pin;
 
     if (r0 < R) {
-        // rows r0 - 1 .. rend - 1 stream through the ring; item k is row r0 - 1 + k
+        // Rows r0 - 1 .. r1 are visited in order (row r0 - 1 only for p_y above
+        // the first row, row r1 only for z below the last); item k holds rows
+        // r0 - 1 + kRows k + h.  Rows at or past R arrive as zeros.
         const int rend = min(r1 + 1, R);         // rows whose z is needed
-        const int nitems = rend - r0 + 1;
+        const int nitems = (r1 - r0 + 2 + kRows - 1) / kRows;
         if (lane == 0) {
             for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
             mbar_init_fence();
@@ -140,164 +150,180 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
         auto issue = [&](int k) {                 // lane 0 only
             const int s = k % kStages;
             unsigned char* st = wbase + s * G::STAGE;
-            const int row = r0 - 1 + k;
-            const uint32_t bytes = (uint32_t)(G::PBYTES + (k > 0 ? G::FBYTES : 0));
-            mbar_expect_tx(&bars[s], bytes);
+            const int row = r0 - 1 + kRows * k;
+            mbar_expect_tx(&bars[s], (uint32_t)(G::PBYTES + G::FBYTES));
             tma_load_3d(st + G::POFF, &pmap, x0 - G::HP, row, 0, &bars[s]);
-            if (k > 0) tma_load_2d(st + G::FOFF, &fmap, x0 - G::HF, row, &bars[s]);
+            tma_load_2d(st + G::FOFF, &fmap, x0 - G::HF, row, &bars[s]);
         };
         if (lane == 0)
             for (int k = 0; k < kStages && k < nitems; ++k) issue(k);
         int issued = min(kStages, nitems);       // items whose load has been issued (same on every lane)
         int failed = -1;                          // item whose wait gave up
 
-        // column masks: D^- reads p_x as zero in the last column and beyond the grid
-        float mx[4], mv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            mv[e] = (j0 + e < C) ? 1.f : 0.f;
-            mx[e] = (j0 + e <= C - 2) ? 1.f : 0.f;
-        }
+        // Only the strip holding column C - 1 needs column masks (D^- reads p_x
+        // as zero there; D^+ is zero across it); columns left of 0 and right of
+        // C - 1 arrive as zeros.  z beyond the grid is never used.
+        const bool edge_col = x0 + kStrip > C - 1;     // warp-uniform
         const int jr = x0 + kStrip;               // first column right of the strip
         float4 pyu = make_float4(0.f, 0.f, 0.f, 0.f);   // p_y of the row above (masked)
         float pyu_r = 0.f;                        // p_y(row above, jr) on lane 31
         float zp[4] = {0.f, 0.f, 0.f, 0.f};       // z of the previous row
         float zpr = 0.f;                          // z(prev row, jr) on lane 31
         float4 pprevx = make_float4(0.f, 0.f, 0.f, 0.f), pprevy = pprevx;
+        bool finished = false;
 
-        for (int k = 0; k <= nitems; ++k) {
-            // ---- item k: row i = r0 - 1 + k (k == nitems: past the last row)
-            const int i = r0 - 1 + k;
-            float4 cpx = make_float4(0.f, 0.f, 0.f, 0.f), cpy = cpx, cf = cpx;
-            float cpxl = 0.f, cpxr = 0.f, cpyr = 0.f, cfr = 0.f;
-            const bool have = k < nitems;
-            if (have) {
-                const int s = k % kStages;
-                const bool arrived = mbar_wait(&bars[s], (uint32_t)((k / kStages) & 1));
-                if (!__all_sync(0xffffffffu, arrived)) {
-                    failed = k;
-                    break;
-                }
-                const unsigned char* st = wbase + s * G::STAGE;
-                const S* sp = reinterpret_cast<const S*>(st + G::POFF);
-                const float* sf = reinterpret_cast<const float*>(st + G::FOFF);
-                cpx = sm_ld4<S>(sp + G::HP + 4 * lane);
-                cpy = sm_ld4<S>(sp + G::WP + G::HP + 4 * lane);
-                if (lane == 0) cpxl = sm_ld1<S>(sp + G::HP - 1);
+        for (int k = 0; k < nitems && !finished; ++k) {
+            const int s = k % kStages;
+            const bool arrived = mbar_wait(&bars[s], (uint32_t)((k / kStages) & 1));
+            if (!__all_sync(0xffffffffu, arrived)) {
+                failed = k;
+                break;
+            }
+            const unsigned char* st = wbase + s * G::STAGE;
+            const S* sp0 = reinterpret_cast<const S*>(st + G::POFF);
+            const float* sf0 = reinterpret_cast<const float*>(st + G::FOFF);
+#pragma unroll
+            for (int h = 0; h < kRows; ++h) {
+                const int i = r0 - 1 + kRows * k + h;
+                if (i > r1) break;
+                const S* spx = sp0 + h * G::WP;                 // p_x of row i
+                const S* spy = sp0 + (kRows + h) * G::WP;       // p_y of row i
+                const float* sf = sf0 + h * G::WF;
+                const float4 cpx = sm_ld4<S>(spx + G::HP + 4 * lane);
+                const float4 cpy = sm_ld4<S>(spy + G::HP + 4 * lane);
+                float cpxl = 0.f, cpxr = 0.f, cpyr = 0.f, cfr = 0.f;
+                if (lane == 0) cpxl = sm_ld1<S>(spx + G::HP - 1);
                 if (lane == 31) {
-                    cpxr = sm_ld1<S>(sp + G::HP + kStrip);
-                    cpyr = sm_ld1<S>(sp + G::WP + G::HP + kStrip);
+                    cpxr = sm_ld1<S>(spx + G::HP + kStrip);
+                    cpyr = sm_ld1<S>(spy + G::HP + kStrip);
+                    cfr = sf[G::HF + kStrip];
                 }
-                if (k > 0) {
-                    cf = *reinterpret_cast<const float4*>(sf + G::HF + 4 * lane);
-                    if (lane == 31) cfr = sf[G::HF + kStrip];
-                }
-                __syncwarp();
-                if (issued < nitems) {
-                    if (lane == 0) {
-                        fence_proxy_async();      // this warp's reads of stage s precede its refill
-                        issue(issued);
+                const float4 cf = *reinterpret_cast<const float4*>(sf + G::HF + 4 * lane);
+                if (i == r0 - 1) {
+                    // row r0 - 1 supplies p_y above the first row (zero outside the grid or in the last row)
+                    if (i <= R - 2) {
+                        pyu = cpy;
+                        pyu_r = cpyr;
                     }
-                    ++issued;
+                    continue;
                 }
-            }
-            if (k == 0) {
-                // row r0 - 1 supplies p_y above the first row (zero outside the grid or in the last row)
-                const float ymask = (i >= 0 && i <= R - 2) ? 1.f : 0.f;
-                pyu = make_float4(cpy.x * ymask, cpy.y * ymask, cpy.z * ymask, cpy.w * ymask);
-                pyu_r = (jr < C) ? cpyr * ymask : 0.f;
-                continue;
-            }
-            float zc[4] = {0.f, 0.f, 0.f, 0.f};
-            float zcr = 0.f;
-            if (have) {
-                // z = div p - f2 at row i (zero-extension rule of D^-)
-                const float ymask = (i <= R - 2) ? 1.f : 0.f;
-                float pxs[4] = {cpx.x * mx[0], cpx.y * mx[1], cpx.z * mx[2], cpx.w * mx[3]};
-                float left = __shfl_up_sync(0xffffffffu, pxs[3], 1);
-                if (lane == 0) left = (j0 >= 1 && j0 - 1 <= C - 2) ? cpxl : 0.f;
-                const float pyc[4] = {cpy.x * ymask, cpy.y * ymask, cpy.z * ymask, cpy.w * ymask};
-                const float pyp[4] = {pyu.x, pyu.y, pyu.z, pyu.w};
-                const float fv[4] = {cf.x, cf.y, cf.z, cf.w};
+                const bool have = i < rend;
+                float zc[4] = {0.f, 0.f, 0.f, 0.f};
+                float zcr = 0.f;
+                if (have) {
+                    // z = div p - f2 at row i (zero-extension rule of D^-)
+                    float pxs[4] = {cpx.x, cpx.y, cpx.z, cpx.w};
+                    if (edge_col) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float pl = e == 0 ? left : pxs[e - 1];
-                    zc[e] = ((pxs[e] - pl) + (pyc[e] - pyp[e]) - fv[e]) * mv[e];
-                }
-                if (lane == 31 && jr < C) {
-                    const float pxr_m = (jr <= C - 2) ? cpxr : 0.f;
-                    zcr = (pxr_m - pxs[3]) + (cpyr * ymask - pyu_r) - cfr;
-                }
-                if (WRITE_D && i < r1) {
-                    float* dd = d_out + (size_t)i * d_pitch;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (j0 + e < C) dd[j0 + e] = -zc[e] * alpha_inv;
-                }
-                if (CHECK && i < r1) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (j0 + e < C) {
-                            const float dv = zc[e] + fv[e];   // div p
-                            ks[3].add(dv * dv);
-                        }
-                }
-                pyu = make_float4(pyc[0], pyc[1], pyc[2], pyc[3]);
-                pyu_r = cpyr * ymask;
-            }
-            if (k >= 2) {
-                // update row i - 1 from z(i-1) (zp) and z(i) (zc)
-                const int ir = i - 1;
-                float zright = __shfl_down_sync(0xffffffffu, zp[0], 1);
-                if (lane == 31) zright = zpr;
-                float res_x[4], res_y[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float zn = e == 3 ? zright : zp[e + 1];
-                    const float gx = (j0 + e < C - 1) ? zn - zp[e] : 0.f;
-                    const float gy = (ir < R - 1) ? zc[e] - zp[e] : 0.f;
-                    const float pxv = comp(pprevx, e), pyv = comp(pprevy, e);
-                    if (WRITE_P) {
-                        const float den = 1.0f + t * sqrtf(gx * gx + gy * gy);
-                        res_x[e] = (pxv + t * gx) / den;
-                        res_y[e] = (pyv + t * gy) / den;
+                        for (int e = 0; e < 4; ++e)
+                            if (j0 + e > C - 2) pxs[e] = 0.f;
                     }
-                    if (CHECK && j0 + e < C) {
-                        const float ng = sqrtf(gx * gx + gy * gy);
-                        ks[0].add(ng);
-                        ks[1].add(ng - (gx * pxv + gy * pyv));
-                        ks[2].add(zp[e] * zp[e]);
-                        pmax = fmaxf(pmax, sqrtf(pxv * pxv + pyv * pyv));
+                    float left = __shfl_up_sync(0xffffffffu, pxs[3], 1);
+                    if (lane == 0) left = cpxl;               // column x0 - 1 (zero left of the grid)
+                    float pyc[4] = {cpy.x, cpy.y, cpy.z, cpy.w};
+                    float cpyr_m = cpyr;
+                    if (i > R - 2) {                          // last row: D^- reads p_y as zero
+                        pyc[0] = pyc[1] = pyc[2] = pyc[3] = 0.f;
+                        cpyr_m = 0.f;
                     }
-                }
-                if (WRITE_P) {
-                    const size_t o = (size_t)ir * pitch + j0;
-                    if (j0 + 3 < C) {
-                        St::st4(pout + o, make_float4(res_x[0], res_x[1], res_x[2], res_x[3]), rkey(seed, o, 0));
-                        St::st4(pout + plane + o, make_float4(res_y[0], res_y[1], res_y[2], res_y[3]),
-                                rkey(seed, o, 1));
-                    } else {
+                    const float pyp[4] = {pyu.x, pyu.y, pyu.z, pyu.w};
+                    const float fv[4] = {cf.x, cf.y, cf.z, cf.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float pl = e == 0 ? left : pxs[e - 1];
+                        zc[e] = ((pxs[e] - pl) + (pyc[e] - pyp[e])) - fv[e];
+                    }
+                    if (lane == 31 && jr < C) {
+                        const float pxr_m = (jr <= C - 2) ? cpxr : 0.f;
+                        zcr = (pxr_m - pxs[3]) + (cpyr_m - pyu_r) - cfr;
+                    }
+                    if (WRITE_D && i < r1) {
+                        float* dd = d_out + (size_t)i * d_pitch;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (j0 + e < C) dd[j0 + e] = -zc[e] * alpha_inv;
+                    }
+                    if (CHECK && i < r1) {
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             if (j0 + e < C) {
-                                St::st1(pout + o + e, res_x[e], rkey(seed, o + e, 0));
-                                St::st1(pout + plane + o + e, res_y[e], rkey(seed, o + e, 1));
+                                const float dv = zc[e] + fv[e];   // div p
+                                ks[3].add(dv * dv);
                             }
                     }
+                    pyu = make_float4(pyc[0], pyc[1], pyc[2], pyc[3]);
+                    pyu_r = cpyr_m;
                 }
-            }
-            // rotate
+                if (i - 1 >= r0) {
+                    // update row i - 1 from z(i-1) (zp) and z(i) (zc)
+                    const int ir = i - 1;
+                    float zright = __shfl_down_sync(0xffffffffu, zp[0], 1);
+                    if (lane == 31) zright = zpr;
+                    float res_x[4], res_y[4];
+                    const bool last_row = ir >= R - 1;       // D^+ is zero across the last row
 #pragma unroll
-            for (int e = 0; e < 4; ++e) zp[e] = zc[e];
-            zpr = zcr;
-            pprevx = cpx;
-            pprevy = cpy;
-            if (i >= r1) break;                   // row r1 only supplied z for the update of row r1 - 1
+                    for (int e = 0; e < 4; ++e) {
+                        const float zn = e == 3 ? zright : zp[e + 1];
+                        float gx = zn - zp[e];
+                        if (edge_col) {
+                            if (j0 + e >= C - 1) gx = 0.f;
+                        }
+                        const float gy = last_row ? 0.f : zc[e] - zp[e];
+                        const float pxv = comp(pprevx, e), pyv = comp(pprevy, e);
+                        const float ng = fast_norm(gx, gy);  // |psi|
+                        if (WRITE_P) {
+                            // p <- (p + t psi) / (1 + t |psi|)
+                            const float inv = __fdividef(1.0f, fmaf(t, ng, 1.0f));
+                            res_x[e] = fmaf(t, gx, pxv) * inv;
+                            res_y[e] = fmaf(t, gy, pyv) * inv;
+                        }
+                        if (CHECK && j0 + e < C) {
+                            ks[0].add(ng);
+                            ks[1].add(ng - (gx * pxv + gy * pyv));
+                            ks[2].add(zp[e] * zp[e]);
+                            pmax = fmaxf(pmax, fast_norm(pxv, pyv));
+                        }
+                    }
+                    if (WRITE_P) {
+                        const size_t o = (size_t)ir * pitch + j0;
+                        if (j0 + 3 < C) {
+                            St::st4(pout + o, make_float4(res_x[0], res_x[1], res_x[2], res_x[3]), rkey(seed, o, 0));
+                            St::st4(pout + plane + o, make_float4(res_y[0], res_y[1], res_y[2], res_y[3]),
+                                    rkey(seed, o, 1));
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (j0 + e < C) {
+                                    St::st1(pout + o + e, res_x[e], rkey(seed, o + e, 0));
+                                    St::st1(pout + plane + o + e, res_y[e], rkey(seed, o + e, 1));
+                                }
+                        }
+                    }
+                }
+                // rotate
+#pragma unroll
+                for (int e = 0; e < 4; ++e) zp[e] = zc[e];
+                zpr = zcr;
+                pprevx = cpx;
+                pprevy = cpy;
+                if (i >= r1) finished = true;    // row r1 only supplied z for the update of row r1 - 1
+            }
+            __syncwarp();
+            if (issued < nitems && !finished) {
+                if (lane == 0) {
+                    fence_proxy_async();          // this warp's reads of stage s precede its refill
+                    issue(issued);
+                }
+                ++issued;
+            }
         }
         if (failed >= 0) {
             // a row never arrived: record it and drain this warp's copies still in flight
             if (lane == 0) atomicOr(err, 1u);
             for (int k = failed; k < issued; ++k) (void)mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+        } else {
+            // loads issued past the last visited item (none when the chunk ends on an item boundary)
+            for (int k = nitems; k < issued; ++k) (void)mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
         }
     }
     if (CHECK) {
@@ -342,8 +368,8 @@ static cudaError_t launch_irv1_t(const S* pin, S* pout, const float* f2, int R, 
     if (!make_tensor_map(&pmap, pin, std::is_same<S, float>::value ? TVS_F32
                                      : std::is_same<S, __nv_bfloat16>::value ? TVS_BF16
                                      : std::is_same<S, __half>::value ? TVS_F16 : TVS_S16,
-                         R, C, pitch, plane, 2, G::WP) ||
-        !make_tensor_map(&fmap, f2, TVS_F32, R, C, pitch, (long)R * pitch, 1, G::WF))
+                         R, C, pitch, plane, 2, G::WP, kRows) ||
+        !make_tensor_map(&fmap, f2, TVS_F32, R, C, pitch, (long)R * pitch, 1, G::WF, kRows))
         return cudaErrorInvalidValue;
     const int strips = (C + kStrip - 1) / kStrip;
     const int chunks = (R + kChunk - 1) / kChunk;

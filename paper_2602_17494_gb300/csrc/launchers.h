@@ -2,6 +2,7 @@
 #pragma once
 
 #include "tvs_internal.cuh"
+#include "decomp.cuh"
 
 namespace tvs {
 
@@ -58,6 +59,31 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
 cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s);
 // n_outer outer iterations of Algorithm 2: p^{n+1} from p^n = *cur, swapping
 // *cur and *nxt after each iteration.
+// One image of a small-subdomain Schwarz step-2 launch.  A launch covers the
+// subdomains of one image or of several images (sorted by `first`): CTA b
+// runs subdomain b - first of the image with the largest first <= b.
+struct TileImg {
+    const void* p;    // p^n, 2 planes (storage of the launch)
+    void* pnext;      // p^{n+1}, written on the exclusive part of the core
+    const float* f2;
+    void* q;          // [sub][2][hmax][qp], columns from start & ~3
+    int pitch;
+    long plane;
+    int hmax, qp;
+    Axis ay, ax;
+    float ahat;       // damping of Algorithm 2
+    int first;        // launch-wide index of the image's first subdomain
+};
+// n_outer outer iterations over several images, small subdomains only: per
+// outer iteration one small-tile launch and one strip launch over all
+// subdomains.  imgs_dev holds 2 * nimg descriptors in device memory: [0, nimg)
+// for even outer iterations, [nimg, 2 nimg) for odd ones (p and pnext
+// swapped).  tx, ty: thread block covering the largest subdomain.
+cudaError_t schwarz2_iterate_multi(int storage, const TileImg* imgs_dev, int nimg, int nsub_total, int tx, int ty,
+                                   int k, float t, int n_outer, uint32_t seed0, cudaStream_t s);
+// Block shape of the small-subdomain kernel for subdomains up to hmax x wmax
+// (0 if they need the cluster kernel); q row pitch and shared memory bytes.
+int small_tile_shape(int hmax, int wmax, int* tx, int* ty, int* qp, size_t* smem);
 // seed0: outer iterations done so far (seeds the stochastic rounding of 16-bit stores).
 cudaError_t schwarz2_iterate(void** cur, void** nxt, const float* f2, int pitch, long plane, int n2, int n1,
                              const Schwarz2State& st, float t, int n_outer, uint32_t seed0, cudaStream_t s);

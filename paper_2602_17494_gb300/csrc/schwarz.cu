@@ -224,18 +224,25 @@ constexpr int kSmallPairThreads = 336;   // up to this many threads two CTAs sha
 
 template <class S>
 struct SmallTileArgs {
-    const S* p;       // p^n, 2 planes
-    S* pnext;         // p^{n+1}, written on the exclusive part of the core
-    const float* f2;
-    int pitch;
-    long plane;
-    S* q;             // [sub][2][hmax][qp], columns from start & ~3
-    int hmax, qp;
-    Axis ay, ax;
+    TileImg one;
+    const TileImg* imgs;      // nullptr: single image
+    int nimg;
     int k;
-    float t, ahat;
+    float t;
     uint32_t seed;
 };
+
+template <bool MULTI, class S>
+__device__ __forceinline__ const TileImg& tile_image(const SmallTileArgs<S>& a) {
+    if (!MULTI) return a.one;   // parameter space: no indirection
+    int lo = 0, hi = a.nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.imgs[mid].first <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return a.imgs[lo];
+}
 
 // Rows of core k that no other subdomain's Gamma reaches: [excl_lo, excl_hi).
 __host__ __device__ __forceinline__ int excl_lo(const Axis& A, int k) { return k == 0 ? 0 : A.core(k) + A.s / 2; }
@@ -265,7 +272,7 @@ __host__ __device__ __forceinline__ size_t small_tile_smem_bytes(int tx, int ty)
            sizeof(float);
 }
 
-template <class S, int MAXT, int MINB>
+template <class S, int MAXT, int MINB, bool MULTI>
 __global__ void __launch_bounds__(MAXT, MINB)
 schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     using St = Stor<S>;
@@ -284,11 +291,12 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     float* sthx = ezy + TY * CW * TX;             // theta_x of columns xa - 1 .. xa + 4 TX - 1
     float* sthy = sthx + CW * TX + 1;             // theta_y of rows y0 - 1 .. y0 + 4 TY - 1
 
-    const int N2 = a.ay.N, N1 = a.ax.N;
-    const int sub = blockIdx.x;
-    const int my = sub / a.ax.M, mx = sub - my * a.ax.M;
-    const int y0 = a.ay.start(my), y1 = a.ay.end(my);
-    const int x0 = a.ax.start(mx), x1 = a.ax.end(mx);
+    const TileImg& im = tile_image<MULTI>(a);
+    const int N2 = im.ay.N, N1 = im.ax.N;
+    const int sub = blockIdx.x - im.first;
+    const int my = sub / im.ax.M, mx = sub - my * im.ax.M;
+    const int y0 = im.ay.start(my), y1 = im.ay.end(my);
+    const int x0 = im.ax.start(mx), x1 = im.ax.end(mx);
     const int xa = x0 & ~3;
     const int ib = y0 + ty * RH, jb = xa + tx * CW;
     const int zy1 = min(y1 + 1, N2), zx1 = min(x1 + 1, N1);   // z region: [y0, zy1) x [x0, zx1)
@@ -297,11 +305,11 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         const int tid = ty * TX + tx, nt = TX * TY;
         for (int c = tid; c <= CW * TX; c += nt) {
             const int j = xa - 1 + c;
-            sthx[c] = (j >= x0 && j < x1) ? a.ax.theta(mx, j) : 0.0f;
+            sthx[c] = (j >= x0 && j < x1) ? im.ax.theta(mx, j) : 0.0f;
         }
         for (int r = tid; r <= RH * TY; r += nt) {
             const int i = y0 - 1 + r;
-            sthy[r] = (i >= y0 && i < y1) ? a.ay.theta(my, i) : 0.0f;
+            sthy[r] = (i >= y0 && i < y1) ? im.ay.theta(my, i) : 0.0f;
         }
     }
     __syncthreads();
@@ -314,8 +322,8 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
 
     // ---- p^n, frozen data g_m (shared memory) ----------------------------
     {
-        const S* __restrict__ px = a.p;
-        const S* __restrict__ py = a.p + a.plane;
+        const S* __restrict__ px = static_cast<const S*>(im.p);
+        const S* __restrict__ py = px + im.plane;
         const bool vec = jb + CW <= N1;           // the thread's 4 columns lie inside the image
         // (1 - theta_m) p^n with the D^- zero-extension rule
         const float thxl = sthx[tx * CW];         // column left of the block
@@ -325,7 +333,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         for (int c = 0; c < CW; ++c) {
             const int i = ib - 1, j = jb + c;
             wyu[c] = (i >= 0 && i <= N2 - 2 && j < N1)
-                         ? (1.0f - thyu * thx[c]) * St::ld1(py + (size_t)i * a.pitch + j) : 0.0f;
+                         ? (1.0f - thyu * thx[c]) * St::ld1(py + (size_t)i * im.pitch + j) : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
@@ -333,11 +341,11 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
             const bool row_ok = i < zy1;
             float vpx[CW] = {0.f, 0.f, 0.f, 0.f}, vpy[CW] = {0.f, 0.f, 0.f, 0.f}, vf[CW] = {0.f, 0.f, 0.f, 0.f};
             if (row_ok) {
-                const size_t o = (size_t)i * a.pitch + jb;
+                const size_t o = (size_t)i * im.pitch + jb;
                 if (vec) {
                     const float4 u = St::ld4(px + o);
                     const float4 w = St::ld4(py + o);
-                    const float4 f = __ldg(reinterpret_cast<const float4*>(a.f2 + o));
+                    const float4 f = __ldg(reinterpret_cast<const float4*>(im.f2 + o));
                     vpx[0] = u.x; vpx[1] = u.y; vpx[2] = u.z; vpx[3] = u.w;
                     vpy[0] = w.x; vpy[1] = w.y; vpy[2] = w.z; vpy[3] = w.w;
                     vf[0] = f.x; vf[1] = f.y; vf[2] = f.z; vf[3] = f.w;
@@ -347,7 +355,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                         if (jb + c < N1) {
                             vpx[c] = St::ld1(px + o + c);
                             vpy[c] = St::ld1(py + o + c);
-                            vf[c] = __ldg(a.f2 + o + c);
+                            vf[c] = __ldg(im.f2 + o + c);
                         }
                 }
             }
@@ -355,7 +363,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
             spy[(ty * RH + r) * TX + tx] = make_float4(vpy[0], vpy[1], vpy[2], vpy[3]);
             float wl = 0.0f;
             if (row_ok && jb >= 1 && jb - 1 <= N1 - 2)
-                wl = (1.0f - thy[r] * thxl) * St::ld1(px + (size_t)i * a.pitch + jb - 1);
+                wl = (1.0f - thy[r] * thxl) * St::ld1(px + (size_t)i * im.pitch + jb - 1);
             float gr[CW];
 #pragma unroll
             for (int c = 0; c < CW; ++c) {
@@ -377,13 +385,13 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
 
     // ---- warm start q_m ---------------------------------------------------
     float vx[RH][CW], vy[RH][CW];
-    S* qx = a.q + (size_t)sub * 2 * a.hmax * a.qp;
-    S* qy = qx + (size_t)a.hmax * a.qp;
+    S* qx = static_cast<S*>(im.q) + (size_t)sub * 2 * im.hmax * im.qp;
+    S* qy = qx + (size_t)im.hmax * im.qp;
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
         float4 ux = make_float4(0.f, 0.f, 0.f, 0.f), uy = ux;
-        if (ib + r < y1) {
-            const size_t qo = (size_t)(ib + r - y0) * a.qp + tx * CW;
+        if (ib + r < y1 && tx * CW < im.qp) {   // (a multi-image block may be wider than this image's rows)
+            const size_t qo = (size_t)(ib + r - y0) * im.qp + tx * CW;
             ux = St::ld4c(qx + qo);
             uy = St::ld4c(qy + qo);
         }
@@ -466,18 +474,18 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     // ---- new warm start q_m; p^{n+1} on the exclusive core -----------------
 #pragma unroll
     for (int r = 0; r < RH; ++r)
-        if (ib + r < y1) {
-            const size_t qo = (size_t)(ib + r - y0) * a.qp + tx * CW;
-            const size_t qi = (size_t)sub * a.hmax * a.qp + qo;
+        if (ib + r < y1 && tx * CW < im.qp) {
+            const size_t qo = (size_t)(ib + r - y0) * im.qp + tx * CW;
+            const size_t qi = (size_t)sub * im.hmax * im.qp + qo;
             St::st4(qx + qo, make_float4(vx[r][0], vx[r][1], vx[r][2], vx[r][3]), rkey(a.seed, qi, 0));
             St::st4(qy + qo, make_float4(vy[r][0], vy[r][1], vy[r][2], vy[r][3]), rkey(a.seed, qi, 1));
         }
-    const int ey0 = excl_lo(a.ay, my), ey1 = excl_hi(a.ay, my);
-    const int ex0 = excl_lo(a.ax, mx), ex1 = excl_hi(a.ax, mx);
-    const float ah = a.ahat, bh = 1.0f - a.ahat;
+    const int ey0 = excl_lo(im.ay, my), ey1 = excl_hi(im.ay, my);
+    const int ex0 = excl_lo(im.ax, mx), ex1 = excl_hi(im.ax, mx);
+    const float ah = im.ahat, bh = 1.0f - im.ahat;
     const uint32_t pseed = a.seed ^ 0xa511e9b3U;   // p^{n+1}: the same keys as the strip kernel's
-    S* __restrict__ nx = a.pnext;
-    S* __restrict__ ny = a.pnext + a.plane;
+    S* __restrict__ nx = static_cast<S*>(im.pnext);
+    S* __restrict__ ny = nx + im.plane;
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
         const int i = ib + r;
@@ -487,7 +495,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                                       fmaf(ah, vx[r][2], bh * u.z), fmaf(ah, vx[r][3], bh * u.w));
         const float4 oy = make_float4(fmaf(ah, vy[r][0], bh * w.x), fmaf(ah, vy[r][1], bh * w.y),
                                       fmaf(ah, vy[r][2], bh * w.z), fmaf(ah, vy[r][3], bh * w.w));
-        const size_t o = (size_t)i * a.pitch + jb;
+        const size_t o = (size_t)i * im.pitch + jb;
         if (jb >= ex0 && jb + CW <= ex1) {
             St::st4(nx + o, ox, rkey(pseed, o, 0));
             St::st4(ny + o, oy, rkey(pseed, o, 1));
@@ -542,12 +550,20 @@ struct QNeighbours {
 
 // p^{n+1} on the overlap strips of every core (the frame between the core
 // and its exclusive part), after the small-tile kernel wrote the rest.
-template <class S>
+template <class S, bool MULTI>
 __global__ void __launch_bounds__(128)
-schwarz2_strip_kernel(const S* __restrict__ pin, S* __restrict__ pout, const S* __restrict__ q,
-                      int pitch, long plane, Axis ay, Axis ax, int hmax, int qp, float ah, uint32_t seed) {
+schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     using St = Stor<S>;
-    const int sub = blockIdx.x;
+    const TileImg& im = tile_image<MULTI>(a);
+    const S* __restrict__ pin = static_cast<const S*>(im.p);
+    S* __restrict__ pout = static_cast<S*>(im.pnext);
+    const S* __restrict__ q = static_cast<const S*>(im.q);
+    const int pitch = im.pitch, hmax = im.hmax, qp = im.qp;
+    const long plane = im.plane;
+    const Axis ay = im.ay, ax = im.ax;
+    const float ah = im.ahat;
+    const uint32_t seed = a.seed;
+    const int sub = blockIdx.x - im.first;
     const int my = sub / ax.M, mx = sub - my * ax.M;
     const int cy0 = ay.core(my), cy1 = my == ay.M - 1 ? ay.L : ay.core(my + 1);
     const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
@@ -617,6 +633,73 @@ static double colouring(int m2, int m1) {
     return 0.25;
 }
 
+int small_tile_shape(int hmax, int wmax, int* tx, int* ty, int* qp, size_t* smem) {
+    // one CTA per subdomain when Gamma_m plus one row and column fit 4 x 4
+    // pixels per thread (the first column may sit up to 3 right of xa)
+    *tx = (wmax + 3 + 1 + kSmallCW - 1) / kSmallCW;
+    *ty = (hmax + 1 + kSmallRH - 1) / kSmallRH;
+    *qp = *tx * kSmallCW;
+    *smem = small_tile_smem_bytes(*tx, *ty);
+    return *tx * *ty <= kSmallMaxThreads ? 1 : 0;
+}
+
+template <class S, bool MULTI>
+static void small_tile_attrs() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+}
+
+template <class S, bool MULTI>
+static cudaError_t launch_small_tiles(const SmallTileArgs<S>& a, int nsub, int tx, int ty, cudaStream_t s) {
+    small_tile_attrs<S, MULTI>();
+    const size_t smem = small_tile_smem_bytes(tx, ty);
+    if (tx * ty <= kSmallPairThreads)
+        schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI><<<nsub, dim3(tx, ty), smem, s>>>(a);
+    else
+        schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI><<<nsub, dim3(tx, ty), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t schwarz2_iterate_multi_t(const TileImg* imgs, int nimg, int nsub, int tx, int ty, int k, float t,
+                                            int n_outer, uint32_t seed0, cudaStream_t s) {
+    for (int n = 0; n < n_outer; ++n) {
+        SmallTileArgs<S> a{};
+        a.imgs = imgs + (n & 1) * nimg;
+        a.nimg = nimg;
+        a.k = k;
+        a.t = t;
+        a.seed = hash32(seed0 + (uint32_t)n + 1u);
+        cudaError_t e;
+        {
+            ProfScope ps(kProfSchwarzTile, s);
+            e = launch_small_tiles<S, true>(a, nsub, tx, ty, s);
+        }
+        if (e != cudaSuccess) return e;
+        {
+            ProfScope ps(kProfSchwarzCombine, s);
+            schwarz2_strip_kernel<S, true><<<nsub, 128, 0, s>>>(a);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t schwarz2_iterate_multi(int storage, const TileImg* imgs_dev, int nimg, int nsub_total, int tx, int ty,
+                                   int k, float t, int n_outer, uint32_t seed0, cudaStream_t s) {
+    if (tx * ty > kSmallMaxThreads || nimg < 1) return cudaErrorInvalidValue;
+    TVS_STORAGE_SWITCH(storage, {
+        return schwarz2_iterate_multi_t<S>(imgs_dev, nimg, nsub_total, tx, ty, k, t, n_outer, seed0, s);
+    })
+    return cudaErrorInvalidValue;
+}
+
 tvs_status schwarz2_check(int n2, int n1, const tvs_decomp& dd) {
     if (dd.m2 < 1 || dd.m1 < 1 || dd.overlap < 0 || dd.k_inner < 1 || dd.alpha_hat > 1.0) return TVS_ERR_ARG;
     if (dd.m2 > n2 || dd.m1 > n1) return TVS_ERR_ARG;
@@ -647,17 +730,12 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
     for (int k = 0; k < dd.m2; ++k) st.hmax = std::max(st.hmax, ay.end(k) - ay.start(k));
     for (int k = 0; k < dd.m1; ++k) st.wmax = std::max(st.wmax, ax.end(k) - ax.start(k));
     st.wpad = round_up(st.wmax + 1, 4);
-    // one CTA per subdomain when Gamma_m plus one row and column fit 4 x 4
-    // pixels per thread (the first column may sit up to 3 right of xa)
-    st.tx = (st.wmax + 3 + 1 + kSmallCW - 1) / kSmallCW;
-    st.ty = (st.hmax + 1 + kSmallRH - 1) / kSmallRH;
-    st.small = st.tx * st.ty <= kSmallMaxThreads;
-    st.qp = st.small ? st.tx * kSmallCW : round_up(st.wmax + 3, 4);
+    st.small = small_tile_shape(st.hmax, st.wmax, &st.tx, &st.ty, &st.qp, &st.smem);
+    if (!st.small) st.qp = round_up(st.wmax + 3, 4);
     const size_t qbytes = (size_t)dd.m2 * dd.m1 * 2 * st.hmax * st.qp * storage_bytes(storage);
     if (st.small) {
         st.ncl = 1;
         st.band = st.hmax;
-        st.smem = small_tile_smem_bytes(st.tx, st.ty);
         st.q = cv.take<char>(qbytes);
         return;
     }
@@ -702,10 +780,6 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
         cudaFuncSetAttribute(schwarz2_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSchwarzSmemMax);
         cudaFuncSetAttribute(schwarz2_tile_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
-        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     Axis ay{n2, st.m2, st.s, n2}, ax{n1, st.m1, st.s, n1};
     cudaLaunchConfig_t cfg = {};
@@ -731,18 +805,23 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
         if (st.small) {
             {
                 ProfScope ps(kProfSchwarzTile, s);
-                SmallTileArgs<S> a{*cur, *nxt, f2, pitch, plane, q, st.hmax, st.qp, ay, ax, st.k, t, ah, seed};
-                if (st.tx * st.ty <= kSmallPairThreads)
-                    schwarz2_small_tile_kernel<S, kSmallPairThreads, 2><<<nsub, dim3(st.tx, st.ty), st.smem, s>>>(a);
-                else
-                    schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1><<<nsub, dim3(st.tx, st.ty), st.smem, s>>>(a);
-                e = cudaGetLastError();
+                SmallTileArgs<S> a{};
+                a.one = TileImg{*cur, *nxt, f2, q, pitch, plane, st.hmax, st.qp, ay, ax, ah, 0};
+                a.imgs = nullptr;
+                a.nimg = 1;
+                a.k = st.k;
+                a.t = t;
+                a.seed = seed;
+                e = launch_small_tiles<S, false>(a, nsub, st.tx, st.ty, s);
             }
             if (e != cudaSuccess) return e;
             if (st.s > 0 && nsub > 1) {
                 ProfScope ps(kProfSchwarzCombine, s);
-                schwarz2_strip_kernel<S><<<nsub, 128, 0, s>>>(*cur, *nxt, q, pitch, plane, ay, ax, st.hmax, st.qp, ah,
-                                                              seed);
+                SmallTileArgs<S> a{};
+                a.one = TileImg{*cur, *nxt, f2, q, pitch, plane, st.hmax, st.qp, ay, ax, ah, 0};
+                a.nimg = 1;
+                a.seed = seed;
+                schwarz2_strip_kernel<S, false><<<nsub, 128, 0, s>>>(a);
             }
         } else {
             {

@@ -28,7 +28,7 @@ EncodeFn encoder() {
 }  // namespace
 
 bool make_tensor_map(CUtensorMap* map, const void* base, int storage, int rows, int cols, int pitch, long plane,
-                     int planes, int box_x) {
+                     int planes, int box_x, int box_y) {
     EncodeFn enc = encoder();
     if (!enc) return false;
     CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -38,7 +38,7 @@ bool make_tensor_map(CUtensorMap* map, const void* base, int storage, int rows, 
     const size_t es = storage_bytes(storage);
     const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)plane * es};
-    const cuuint32_t box[3] = {(cuuint32_t)box_x, 1u, (cuuint32_t)planes};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)planes};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = enc(map, dt, planes > 1 ? 3u : 2u, const_cast<void*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -35,14 +35,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
+// One poll; the thread may sleep in hardware until the phase completes or
+// kSuspendNs nanoseconds pass, so a waiting warp does not spin on the issue
+// slots the other warps need.
+constexpr uint32_t kSuspendNs = 1000000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -75,8 +79,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 // Host: tiled tensor map of `planes` planes of rows x cols elements
 // (element pitch `pitch`, plane stride `plane` elements) with a box of
-// box_x x 1 x planes.  Returns false if the driver rejects it.
+// box_x x box_y x planes.  Returns false if the driver rejects it.
 bool make_tensor_map(CUtensorMap* map, const void* base, int storage, int rows, int cols, int pitch, long plane,
-                     int planes, int box_x);
+                     int planes, int box_x, int box_y);
 
 }  // namespace tvs

@@ -192,34 +192,35 @@ __host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
-// Random key of the element at index o of plane pl for update `seed`.
+// Random bits for the element at index o of plane pl in update `seed`: one
+// hash of a counter built from the three (a 16-bit store uses 16 of them, a
+// 4-wide store 8 per element).
 __device__ __forceinline__ uint32_t rkey(uint32_t seed, size_t o, int pl) {
-    return hash32(seed ^ hash32((uint32_t)o * 2u + (uint32_t)pl));
-}
-// 16 random bits for each of the 4 elements of a vector store with key k.
-__device__ __forceinline__ void rbits4(uint32_t k, uint32_t r[4]) {
-    const uint32_t a = hash32(k), b = hash32(k ^ 0x9e3779b9U);
-    r[0] = a & 0xffffU;
-    r[1] = a >> 16;
-    r[2] = b & 0xffffU;
-    r[3] = b >> 16;
+    return hash32((uint32_t)o * 0x9e3779b1U + seed * 0x85ebca77U + (uint32_t)pl * 0xc2b2ae3dU);
 }
 
-__device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, uint32_t r16) {
+// Stochastic rounding from float; r is `bits` random bits (8 or 16) and the
+// remaining discarded bits are dithered at their midpoint.
+template <int BITS>
+__device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, uint32_t r) {
     uint32_t b = __float_as_uint(x);
     if ((b & 0x7f800000U) == 0x7f800000U) return __float2bfloat16_rn(x);
-    b += r16 & 0xffffU;                                   // a carry rounds the magnitude up
+    b += (r << (16 - BITS)) + ((1u << (16 - BITS)) >> 1);   // a carry rounds the magnitude up
     return __ushort_as_bfloat16((unsigned short)(b >> 16));
 }
-__device__ __forceinline__ __half f16_sr(float x, uint32_t r16) {
+template <int BITS>
+__device__ __forceinline__ __half f16_sr(float x, uint32_t r) {
     const float ax = fabsf(x);
     if (!(ax >= 6.103515625e-05f && ax < 32768.0f)) return __float2half_rn(x);   // outside the normal range
-    const uint32_t b = (__float_as_uint(x) + (r16 & 0x1fffU)) & ~0x1fffU;     // 10 mantissa bits remain
+    const uint32_t add = BITS >= 13 ? (r & 0x1fffU) : ((r << (13 - BITS)) + ((1u << (13 - BITS)) >> 1));
+    const uint32_t b = (__float_as_uint(x) + add) & ~0x1fffU;                    // 10 mantissa bits remain
     return __float2half_rz(__uint_as_float(b));
 }
 constexpr float kS16Scale = 32767.0f;   // fixed point: value = code / 32767, |code| <= 32767
-__device__ __forceinline__ int16_t s16_sr(float x, uint32_t r16) {
-    const float y = fmaf(x, kS16Scale, (float)(r16 & 0xffffU) * (1.0f / 65536.0f));
+template <int BITS>
+__device__ __forceinline__ int16_t s16_sr(float x, uint32_t r) {
+    const float u = ((float)r + 0.5f) * (1.0f / (float)(1u << BITS));
+    const float y = fmaf(x, kS16Scale, u);
     return (int16_t)fminf(fmaxf(floorf(y), -kS16Scale), kS16Scale);
 }
 
@@ -235,7 +236,7 @@ struct Stor<float> {
     static __device__ __forceinline__ void st1(float* p, float v, uint32_t) { *p = v; }
 };
 
-// Shared code of the 16-bit formats: D supplies to_f(uint16) and from_f(float, rbits).
+// Shared code of the 16-bit formats: D supplies to_f(uint16) and from_f<BITS>(float, random bits).
 template <class T, class D>
 struct Stor16 {
     static __device__ __forceinline__ float4 unpack(uint2 u) {
@@ -249,28 +250,31 @@ struct Stor16 {
     }
     static __device__ __forceinline__ float ld1c(const T* p) { return D::to_f(*reinterpret_cast<const uint16_t*>(p)); }
     static __device__ __forceinline__ void st4(T* p, float4 v, uint32_t k) {
-        uint32_t r[4];
-        rbits4(k, r);
         uint2 u;
-        u.x = (uint32_t)D::from_f(v.x, r[0]) | ((uint32_t)D::from_f(v.y, r[1]) << 16);
-        u.y = (uint32_t)D::from_f(v.z, r[2]) | ((uint32_t)D::from_f(v.w, r[3]) << 16);
+        u.x = (uint32_t)D::template from_f<8>(v.x, k & 0xffU) | ((uint32_t)D::template from_f<8>(v.y, (k >> 8) & 0xffU) << 16);
+        u.y = (uint32_t)D::template from_f<8>(v.z, (k >> 16) & 0xffU) | ((uint32_t)D::template from_f<8>(v.w, k >> 24) << 16);
         *reinterpret_cast<uint2*>(p) = u;
     }
     static __device__ __forceinline__ void st1(T* p, float v, uint32_t k) {
-        *reinterpret_cast<uint16_t*>(p) = D::from_f(v, hash32(k) & 0xffffU);
+        *reinterpret_cast<uint16_t*>(p) = D::template from_f<16>(v, k & 0xffffU);
     }
 };
 struct Bf16Bits {
     static __device__ __forceinline__ float to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
-    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return __bfloat16_as_ushort(bf16_sr(x, r)); }
+    template <int BITS>
+    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) {
+        return __bfloat16_as_ushort(bf16_sr<BITS>(x, r));
+    }
 };
 struct F16Bits {
     static __device__ __forceinline__ float to_f(uint16_t b) { return __half2float(__ushort_as_half(b)); }
-    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return __half_as_ushort(f16_sr(x, r)); }
+    template <int BITS>
+    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return __half_as_ushort(f16_sr<BITS>(x, r)); }
 };
 struct S16Bits {
     static __device__ __forceinline__ float to_f(uint16_t b) { return (float)(int16_t)b * (1.0f / kS16Scale); }
-    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return (uint16_t)s16_sr(x, r); }
+    template <int BITS>
+    static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return (uint16_t)s16_sr<BITS>(x, r); }
 };
 template <>
 struct Stor<__nv_bfloat16> : Stor16<__nv_bfloat16, Bf16Bits> {};

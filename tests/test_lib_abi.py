@@ -107,3 +107,38 @@ def test_schwarz1_workspace_and_limits(lib):
     L = lib.lib()
     big = lib.make_decomp(128, 128, 4, 4)     # 16384 subdomains x full-width rows: beyond the scratch limit
     assert L.tvs_workspace_bytes(1, 8192, 8192, ctypes.byref(big), 0) == 0
+
+
+def test_engine_configuration_checks(lib):
+    L = lib.lib()
+    it = lib.make_iter(100, 0.125, 1e-4, 10)
+    good = lib.make_engine_config(0.05, 10.0, 1e-3, it, it, 64, 4, 16, 8)
+    assert L.tvs_engine_pool_overhead(ctypes.byref(good)) > 0
+    b1 = L.tvs_engine_request_bytes(ctypes.byref(good), 256, 300)
+    b2 = L.tvs_engine_request_bytes(ctypes.byref(good), 1024, 1024)
+    assert 0 < b1 < b2
+    assert L.tvs_engine_request_bytes(ctypes.byref(good), 1, 300) == 0        # too small
+    bad_tile = lib.make_engine_config(0.05, 10.0, 1e-3, it, it, 64, 40, 16, 8)   # 2 overlap >= tile
+    assert L.tvs_engine_pool_overhead(ctypes.byref(bad_tile)) == 0
+    no_check = lib.make_engine_config(0.05, 10.0, 1e-3, lib.make_iter(100), it, 64, 4, 16, 8)
+    assert L.tvs_engine_pool_overhead(ctypes.byref(no_check)) == 0          # check_every must be >= 1
+    h = ctypes.c_void_p()
+    assert L.tvs_engine_create(ctypes.byref(bad_tile), ctypes.c_void_p(0x1000), 1 << 30, None, ctypes.byref(h)) == 1
+    assert L.tvs_engine_create(ctypes.byref(good), None, 1 << 30, None, ctypes.byref(h)) == 2
+    huge = lib.make_engine_config(0.05, 10.0, 1e-3, it, it, 200, 4, 16, 8)      # subdomain beyond one CTA
+    assert L.tvs_engine_create(ctypes.byref(huge), ctypes.c_void_p(0x1000), 1 << 30, None, ctypes.byref(h)) == 6
+
+
+def test_tuner_workspace_and_argument_checks(lib):
+    L = lib.lib()
+    arr = lambda v: (ctypes.c_int * len(v))(*v)
+    T, O = arr([32, 64]), arr([2, 4])
+    a = L.tvs_tune_workspace_bytes(256, 300, T, 2, O, 2, 0)
+    b = L.tvs_tune_workspace_bytes(256, 300, T, 2, O, 2, 3)
+    assert a > b > 0                                    # 16-bit duals need less
+    assert L.tvs_tune_workspace_bytes(256, 300, T, 0, O, 2, 0) == 0
+    best = (ctypes.c_int * 3)()
+    it = lib.make_iter(10, 0.125, 0.0, 2)               # no tolerance: nothing to tune against
+    fake = ctypes.c_void_p(0x1000)
+    assert L.tvs_tune_schwarz2(fake, fake, 64, 64, 10.0, 1e-3, ctypes.byref(it), T, 2, O, 2, arr([4]), 1, fake,
+                               1 << 30, None, best, None) == 1
