@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=32, help="requests per arrival rate (serving section)")
     ap.add_argument("--large-n", type=int, default=8192,
                     help="side of the large-image measurements (0 = skip them)")
-    ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise"], default=None,
+    ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise", "bench_step"], default=None,
                     help="run one API call of this step (profiling target) instead of the benchmark")
     ap.add_argument("--n", type=int, default=N, help="image side for --case")
     ap.add_argument("--iters", type=int, default=3, help="updates (or outer iterations) for --case")
@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--storage", type=int, default=0, choices=[0, 1, 2, 3],
                     help="step-2 dual storage for --case: 0 f32, 1 bf16, 2 f16, 3 16-bit fixed point")
     ap.add_argument("--tile", type=int, default=256, help="Schwarz core size for --case schwarz2")
+    ap.add_argument("--overlap", type=int, default=-1, help="Schwarz overlap for --case schwarz2 (default: 8, or 4)")
     return ap.parse_args()
 
 
@@ -659,7 +660,8 @@ def run_case(args):
     d0 = torch.from_numpy(noisy_scene(SceneSpec(n, n, 0, SIGMA, True))[1].astype(np.float32)).cuda()
     tau = torch.zeros((2, n + 1, n + 1), dtype=torch.float32, device="cuda")
     m = max(1, n // args.tile)
-    dd = B.make_decomp(m, m, OVERLAP if n // m >= 2 * OVERLAP else 4, K_INNER)
+    ov = args.overlap if args.overlap >= 0 else (OVERLAP if n // m >= 2 * OVERLAP else 4)
+    dd = B.make_decomp(m, m, ov, K_INNER)
     it = B.make_iter(args.iters, T)
     it2 = B.make_iter(args.iters, T, storage=args.storage)
     t0 = time.perf_counter()
@@ -670,6 +672,10 @@ def run_case(args):
             r = B.tvs_step2(d0, tau, ALPHA, EPS, it2)
         elif args.case == "schwarz2":
             r = B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, it2)
+        elif args.case == "bench_step":
+            # exactly one timed step of the default benchmark (on an n x n scene)
+            B.tvs_denoise(d0, DELTA, ALPHA, EPS, B.make_iter(ITERS1, T), B.make_iter(OUTER, T),
+                          B.make_decomp(M2, M1, OVERLAP, K_INNER), tau=tau)
         else:
             r = B.tvs_denoise(d0, DELTA, ALPHA, EPS, it, it, dd, tau=tau)
     torch.cuda.synchronize()

@@ -172,9 +172,9 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
     double r[kRedSlots];
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
-        TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+        TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
         TVS_CUDA(launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
-                                   L.red.partial, s));
+                                   L.red.partial, L.red.err, s));
         std::swap(cur, nxt);
         ++n;
         if (ck) {
@@ -188,9 +188,9 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             }
         }
     }
-    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
     TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau, tau_pitch,
-                               tau_plane, L.red.partial, s));
+                               tau_plane, L.red.partial, L.red.err, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;
@@ -311,12 +311,12 @@ static tvs_status run_schwarz1(const Step1Layout& L, Schwarz1State& S1, const fl
     double r[kRedSlots];
     while (n < it.max_iter) {
         const int step = chunk < it.max_iter - n ? chunk : it.max_iter - n;
-        TVS_CUDA(schwarz1_iterate(&cur, &nxt, L.f1, L.S, L.P, n2, n1, L.pp, S1, t, step, s));
+        TVS_CUDA(schwarz1_iterate(&cur, &nxt, L.f1, L.S, L.P, n2, n1, L.pp, S1, t, step, L.red.err, s));
         n += step;
         if (check_loop && n < it.max_iter) {
-            TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+            TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
             TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, nullptr,
-                                       0, 0, L.red.partial, s));
+                                       0, 0, L.red.partial, L.red.err, s));
             st = read_result(L.red, nb, s, r);
             if (st != TVS_OK) return st;
             tvs_report tmp;
@@ -327,9 +327,9 @@ static tvs_status run_schwarz1(const Step1Layout& L, Schwarz1State& S1, const fl
             }
         }
     }
-    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
     TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau, n1 + 1,
-                               (long)(n2 + 1) * (n1 + 1), L.red.partial, s));
+                               (long)(n2 + 1) * (n1 + 1), L.red.partial, L.red.err, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;

@@ -596,9 +596,19 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
 // ---------------------------------------------------------------------------
 // Launchers for one FFT length
 // ---------------------------------------------------------------------------
+// Shared-memory limit and carve-out of a DCT kernel.  The plan tables (twiddles,
+// filter spectrum, chirp, Makhoul twiddles: about 28 M bytes) are read by every
+// CTA through L1; the carve-out is sized for at most four CTAs per SM so that
+// the rest of the unified L1/shared storage can keep them resident.
 template <class K>
-inline void allow_dct_smem(K kernel) {
+inline void allow_dct_smem(K kernel, size_t smem_per_cta = 0) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 16 * 1024);
+    if (smem_per_cta) {
+        const size_t per_sm = 228 * 1024;
+        int pct = (int)((4 * (smem_per_cta + 1024) * 100 + per_sm - 1) / per_sm);
+        pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    }
 }
 
 template <int LM>
@@ -614,11 +624,11 @@ template <int LM>
 cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int pitch, const DctPlan& pl,
                                const RowSrcArgs& sa, const BatchArgs& ba, int nbatch, int maxrows, cudaStream_t s) {
     static std::once_flag once;
-    std::call_once(once, [] {
-        allow_dct_smem(dct_rows_fwd_kernel<RowSource::Plain, LM>);
-        allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivField, LM>);
-    });
     const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    std::call_once(once, [smem] {
+        allow_dct_smem(dct_rows_fwd_kernel<RowSource::Plain, LM>, smem);
+        allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivField, LM>, smem);
+    });
     const dim3 grid((maxrows + 1) / 2, nbatch);
     const int nt = fft_threads(pl.M);
     if (src == RowSource::Plain)
@@ -634,8 +644,8 @@ template <int LM>
 cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                            int nbatch, cudaStream_t s) {
     static std::once_flag once;
-    std::call_once(once, [] { allow_dct_smem(dct_cols_solve_kernel<LM>); });
     const size_t smem = (size_t)(padded_len(pl.M) + rows + 1) * sizeof(float2);
+    std::call_once(once, [] { allow_dct_smem(dct_cols_solve_kernel<LM>, (size_t)(padded_len(1 << LM) + (1 << (LM - 1)) + 2) * sizeof(float2)); });
     const dim3 grid((cols + 1) / 2, nbatch);
     dct_cols_solve_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
     return cudaGetLastError();
@@ -645,8 +655,8 @@ template <int LM>
 cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                                int nbatch, int maxrows, cudaStream_t s) {
     static std::once_flag once;
-    std::call_once(once, [] { allow_dct_smem(dct_rows_inv_kernel<LM>); });
     const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    std::call_once(once, [smem] { allow_dct_smem(dct_rows_inv_kernel<LM>, smem); });
     const dim3 grid((maxrows + 1) / 2, nbatch);
     dct_rows_inv_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
     return cudaGetLastError();

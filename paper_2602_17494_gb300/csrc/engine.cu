@@ -306,9 +306,9 @@ static tvs_status step1_chunk(EngineImpl* e, Request* r) {
     const int n = std::min(e->cfg.it1.check_every, e->cfg.it1.max_iter - r->it1);
     for (int j = 0; j < n; ++j) {
         const bool ck = j == n - 1;
-        TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+        TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
         TVS_CUDA(launch_tfs_update(r->cur1, r->nxt1, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
-                                   L.red.partial, s));
+                                   L.red.partial, L.red.err, s));
         std::swap(r->cur1, r->nxt1);
     }
     r->it1 += n;
@@ -324,10 +324,16 @@ static tvs_status step1_chunk(EngineImpl* e, Request* r) {
 static tvs_status step1_to_step2(EngineImpl* e, Request* r) {
     const Step1Layout& L = r->L1;
     cudaStream_t s = e->stream;
+    unsigned err = 0;   // step 1 finished on a side stream that the last synchronization covered
+    TVS_CUDA(cudaMemcpy(&err, L.red.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) {
+        set_error_text("a bounded device-side wait gave up (TMA tile load)");
+        return TVS_ERR_TIMEOUT;
+    }
     const int n2 = r->n2, n1 = r->n1, R = n2 + 1, C = n1 + 1;
-    TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, s));
+    TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
     TVS_CUDA(launch_tfs_update(r->cur1, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, (float)e->cfg.it1.t,
-                               (float)e->cfg.delta, false, false, r->tau, C, (long)R * C, L.red.partial, s));
+                               (float)e->cfg.delta, false, false, r->tau, C, (long)R * C, L.red.partial, L.red.err, s));
     TVS_CUDA(launch_xi_f2(r->d0, n1, r->tau, (long)R * C, C, n2, n1, (float)e->cfg.alpha, (float)e->cfg.eps,
                           r->L2.f2, r->L2.P, s));
     TVS_CUDA(p2_zero(r->L2, s));

@@ -12,14 +12,17 @@ cudaError_t launch_tau0(const float* d0, int d_pitch, int n2, int n1, float* tau
 cudaError_t launch_grad_sub(const float* u, int upitch, long uplane, const float* phi, int ppitch, int R, int C,
                             float scale, float* out, int opitch, long oplane, cudaStream_t s);
 cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, const float* f1, int R, int C,
-                              int pitch, long plane, float t, float delta, bool check, bool write_p, float* tau_out,
-                              int tau_pitch, long tau_plane, double* partial, cudaStream_t s);
+                              int pitch, long plane, float t, float delta, bool check, bool write_p,
+                              float* tau_out, int tau_pitch, long tau_plane, double* partial, unsigned* err,
+                              cudaStream_t s);
 int tfs_blocks(int R, int C);
-cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, cudaStream_t s);
+// err: device word whose bit 0 is set if a bounded wait on the TMA boxes gave up
+cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, unsigned* err,
+                              cudaStream_t s);
 // S <- Delta^dagger div(vecdiv p) on the extended grid (phi of the TFS iteration)
 inline cudaError_t tfs_phi(const float* p, float* S, int R, int C, int pitch, long plane, const PoissonPlans& pp,
-                           cudaStream_t s) {
-    cudaError_t e = launch_div_vecdiv(p, R, C, pitch, plane, S, s);
+                           unsigned* err, cudaStream_t s) {
+    cudaError_t e = launch_div_vecdiv(p, R, C, pitch, plane, S, err, s);
     if (e != cudaSuccess) return e;
     RowSrcArgs sa{S, 0, pitch};
     return poisson_solve(S, R, C, pitch, pp, RowSource::Plain, sa, s);
@@ -57,8 +60,6 @@ size_t schwarz2_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pit
 void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, int storage, Schwarz2State& st);
 // Zero the warm starts q_m (Algorithm 3 starts every subdomain from 0).
 cudaError_t schwarz2_reset(const Schwarz2State& st, cudaStream_t s);
-// n_outer outer iterations of Algorithm 2: p^{n+1} from p^n = *cur, swapping
-// *cur and *nxt after each iteration.
 // One image of a small-subdomain Schwarz step-2 launch.  A launch covers the
 // subdomains of one image or of several images (sorted by `first`): CTA b
 // runs subdomain b - first of the image with the largest first <= b.
@@ -84,7 +85,9 @@ cudaError_t schwarz2_iterate_multi(int storage, const TileImg* imgs_dev, int nim
 // Block shape of the small-subdomain kernel for subdomains up to hmax x wmax
 // (0 if they need the cluster kernel); q row pitch and shared memory bytes.
 int small_tile_shape(int hmax, int wmax, int* tx, int* ty, int* qp, size_t* smem);
-// seed0: outer iterations done so far (seeds the stochastic rounding of 16-bit stores).
+// n_outer outer iterations of Algorithm 2: p^{n+1} from p^n = *cur, swapping
+// *cur and *nxt after each iteration.  seed0: outer iterations done so far
+// (seeds the stochastic rounding of 16-bit stores).
 cudaError_t schwarz2_iterate(void** cur, void** nxt, const float* f2, int pitch, long plane, int n2, int n1,
                              const Schwarz2State& st, float t, int n_outer, uint32_t seed0, cudaStream_t s);
 
@@ -103,6 +106,7 @@ size_t schwarz1_extend(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pit
 void schwarz1_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch, Schwarz1State& st);
 cudaError_t schwarz1_reset(const Schwarz1State& st, int n2, int n1, cudaStream_t s);
 cudaError_t schwarz1_iterate(float** cur, float** nxt, const float* f1, float* S_glob, int pitch, int n2, int n1,
-                             const PoissonPlans& pp, const Schwarz1State& st, float t, int n_outer, cudaStream_t s);
+                             const PoissonPlans& pp, const Schwarz1State& st, float t, int n_outer, unsigned* err,
+                             cudaStream_t s);
 
 }  // namespace tvs

@@ -264,9 +264,10 @@ __host__ __device__ __forceinline__ int excl_hi(const Axis& A, int k) {
 //   end    : q_m = v; on the part of the core that no other subdomain
 //            reaches, p^{n+1} = (1 - alpha_hat) p^n + alpha_hat q_m directly
 //            (the overlap strips are combined by schwarz2_strip_kernel).
-// Shared memory: p^n_x, p^n_y and g_m as float4 [4 ty + r][tx]; edge arrays
-// (floats) vedge_x [4 ty + r][tx], vedge_y [ty][c][tx], the same two for z;
-// theta_x and theta_y of the block's columns and rows.
+// Shared memory: p^n_x, p^n_y and g_m as float4 [r][ty][tx]; edge arrays
+// (floats) vedge_x [r][ty][tx], vedge_y [c][ty][tx], the same two for z;
+// theta_x and theta_y of the block's columns and rows.  With tx fastest and
+// rows of TX threads, the two thread rows a warp spans hit disjoint banks.
 __host__ __device__ __forceinline__ size_t small_tile_smem_bytes(int tx, int ty) {
     return ((size_t)ty * tx * (12 * kSmallRH + 2 * (kSmallRH + kSmallCW)) + kSmallCW * tx + kSmallRH * ty + 2) *
            sizeof(float);
@@ -281,13 +282,13 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     const int TX = blockDim.x, TY = blockDim.y;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NB = TY * RH * TX;                  // float4 slots per array
-    float4* spx = sm4;                            // [TY * RH][TX]
+    float4* spx = sm4;                            // [RH][TY][TX]
     float4* spy = spx + NB;
     float4* gs = spy + NB;
-    float* evx = reinterpret_cast<float*>(gs + NB);   // [TY * RH][TX]
-    float* evy = evx + TY * RH * TX;                  // [TY][CW][TX]
-    float* ezx = evy + TY * CW * TX;                  // [TY * RH][TX]
-    float* ezy = ezx + TY * RH * TX;                  // [TY][CW][TX]
+    float* evx = reinterpret_cast<float*>(gs + NB);   // [RH][TY][TX]
+    float* evy = evx + TY * RH * TX;                  // [CW][TY][TX]
+    float* ezx = evy + TY * CW * TX;                  // [RH][TY][TX]
+    float* ezy = ezx + TY * RH * TX;                  // [CW][TY][TX]
     float* sthx = ezy + TY * CW * TX;             // theta_x of columns xa - 1 .. xa + 4 TX - 1
     float* sthy = sthx + CW * TX + 1;             // theta_y of rows y0 - 1 .. y0 + 4 TY - 1
 
@@ -359,8 +360,8 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                         }
                 }
             }
-            spx[(ty * RH + r) * TX + tx] = make_float4(vpx[0], vpx[1], vpx[2], vpx[3]);
-            spy[(ty * RH + r) * TX + tx] = make_float4(vpy[0], vpy[1], vpy[2], vpy[3]);
+            spx[(r * TY + ty) * TX + tx] = make_float4(vpx[0], vpx[1], vpx[2], vpx[3]);
+            spy[(r * TY + ty) * TX + tx] = make_float4(vpy[0], vpy[1], vpy[2], vpy[3]);
             float wl = 0.0f;
             if (row_ok && jb >= 1 && jb - 1 <= N1 - 2)
                 wl = (1.0f - thy[r] * thxl) * St::ld1(px + (size_t)i * im.pitch + jb - 1);
@@ -379,7 +380,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                 gr[c] = gv;
                 wyu[c] = wyc;
             }
-            gs[(ty * RH + r) * TX + tx] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+            gs[(r * TY + ty) * TX + tx] = make_float4(gr[0], gr[1], gr[2], gr[3]);
         }
     }
 
@@ -416,20 +417,20 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     // ---- k inner updates on chip (Algorithm 3) --------------------------
     for (int it = 0; it < a.k; ++it) {
 #pragma unroll
-        for (int r = 0; r < RH; ++r) evx[(ty * RH + r) * TX + tx] = vx[r][CW - 1];
+        for (int r = 0; r < RH; ++r) evx[(r * TY + ty) * TX + tx] = vx[r][CW - 1];
 #pragma unroll
-        for (int c = 0; c < CW; ++c) evy[(ty * CW + c) * TX + tx] = vy[RH - 1][c];
+        for (int c = 0; c < CW; ++c) evy[(c * TY + ty) * TX + tx] = vy[RH - 1][c];
         __syncthreads();
         float z[RH][CW];
         {
             float vxl[RH], vyu[CW];
 #pragma unroll
-            for (int r = 0; r < RH; ++r) vxl[r] = tx > 0 ? evx[(ty * RH + r) * TX + tx - 1] : 0.0f;
+            for (int r = 0; r < RH; ++r) vxl[r] = tx > 0 ? evx[(r * TY + ty) * TX + tx - 1] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) vyu[c] = ty > 0 ? evy[((ty - 1) * CW + c) * TX + tx] : 0.0f;
+            for (int c = 0; c < CW; ++c) vyu[c] = ty > 0 ? evy[(c * TY + ty - 1) * TX + tx] : 0.0f;
 #pragma unroll
             for (int r = 0; r < RH; ++r) {
-                const float4 g4 = gs[(ty * RH + r) * TX + tx];
+                const float4 g4 = gs[(r * TY + ty) * TX + tx];
                 const float gr[CW] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
                 for (int c = 0; c < CW; ++c) {
@@ -441,16 +442,16 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
             }
         }
 #pragma unroll
-        for (int r = 0; r < RH; ++r) ezx[(ty * RH + r) * TX + tx] = z[r][0];
+        for (int r = 0; r < RH; ++r) ezx[(r * TY + ty) * TX + tx] = z[r][0];
 #pragma unroll
-        for (int c = 0; c < CW; ++c) ezy[(ty * CW + c) * TX + tx] = z[0][c];
+        for (int c = 0; c < CW; ++c) ezy[(c * TY + ty) * TX + tx] = z[0][c];
         __syncthreads();
         {
             float zr[RH], zd[CW];
 #pragma unroll
-            for (int r = 0; r < RH; ++r) zr[r] = tx + 1 < TX ? ezx[(ty * RH + r) * TX + tx + 1] : 0.0f;
+            for (int r = 0; r < RH; ++r) zr[r] = tx + 1 < TX ? ezx[(r * TY + ty) * TX + tx + 1] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) zd[c] = ty + 1 < TY ? ezy[((ty + 1) * CW + c) * TX + tx] : 0.0f;
+            for (int c = 0; c < CW; ++c) zd[c] = ty + 1 < TY ? ezy[(c * TY + ty + 1) * TX + tx] : 0.0f;
 #pragma unroll
             for (int r = 0; r < RH; ++r)
 #pragma unroll
@@ -490,7 +491,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     for (int r = 0; r < RH; ++r) {
         const int i = ib + r;
         if (i < ey0 || i >= ey1) continue;
-        const float4 u = spx[(ty * RH + r) * TX + tx], w = spy[(ty * RH + r) * TX + tx];
+        const float4 u = spx[(r * TY + ty) * TX + tx], w = spy[(r * TY + ty) * TX + tx];
         const float4 ox = make_float4(fmaf(ah, vx[r][0], bh * u.x), fmaf(ah, vx[r][1], bh * u.y),
                                       fmaf(ah, vx[r][2], bh * u.z), fmaf(ah, vx[r][3], bh * u.w));
         const float4 oy = make_float4(fmaf(ah, vy[r][0], bh * w.x), fmaf(ah, vy[r][1], bh * w.y),

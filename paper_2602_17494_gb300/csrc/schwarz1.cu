@@ -323,7 +323,8 @@ static cudaError_t local_projection(const S1Geom& g, const Schwarz1State& st, co
 }
 
 cudaError_t schwarz1_iterate(float** cur, float** nxt, const float* f1, float* S_glob, int pitch, int n2, int n1,
-                             const PoissonPlans& pp, const Schwarz1State& st, float t, int n_outer, cudaStream_t s) {
+                             const PoissonPlans& pp, const Schwarz1State& st, float t, int n_outer, unsigned* err,
+                             cudaStream_t s) {
     const S1Geom g = make_geom(n2, n1, st, pitch);
     const dim3 blk(32, 8);
     const dim3 gtile((st.wpad + 31) / 32, (st.hbox + 7) / 8, st.ntiles);
@@ -331,7 +332,7 @@ cudaError_t schwarz1_iterate(float** cur, float** nxt, const float* f1, float* S
     cudaError_t e;
     for (int n = 0; n < n_outer; ++n) {
         // Q = P_K vecdiv p^n
-        if ((e = tfs_phi(*cur, S_glob, g.R, g.C, pitch, g.plane, pp, s)) != cudaSuccess) return e;
+        if ((e = tfs_phi(*cur, S_glob, g.R, g.C, pitch, g.plane, pp, err, s)) != cudaSuccess) return e;
         s1_q_kernel<<<gglob, blk, 0, s>>>(g, *cur, S_glob, st.Q);
         // omega_m
         s1_u_kernel<true><<<gtile, blk, 0, s>>>(g, st.V, *cur, st.U);

@@ -8,12 +8,85 @@
 // Arrays live on the extended grid R x C = (N2+1) x (N1+1) with a padded pitch.
 #include "tvs_internal.cuh"
 #include "prof.h"
+#include "tma.cuh"
+
+#include <mutex>
 
 namespace tvs {
 
-constexpr int kTX = 32;
-constexpr int kTY = 16;
-constexpr int kBY = 8;
+constexpr int kTX = 32;   // tile width (outputs)
+constexpr int kTY = 32;   // tile height (outputs)
+constexpr int kBY = 8;    // thread rows; each thread does kTY / kBY output rows
+
+// The tiled stencils below receive their inputs as TMA boxes covering the
+// tile plus a halo: columns j0 - 4 .. j0 + kTX + 3 (16-byte aligned start),
+// rows i0 - 2 .. i0 + kTY + 1.  Reads outside the grid come back as zeros;
+// the D^- rule (x-parts zero in the last column, y-parts in the last row) is
+// applied when the box is read.
+constexpr int kBW = kTX + 8;      // box width
+constexpr int kBH = kTY + 4;      // box height
+constexpr int kBoxC = 4;          // box column of grid column j0
+constexpr int kBoxR = 2;          // box row of grid row i0
+constexpr int kBoxFloats = kBW * kBH;
+
+// Cached tensor maps of one field: rebuilt only when the base, sizes or
+// plane count change.
+struct MapCache {
+    const void* base = nullptr;
+    int R = 0, C = 0, pitch = 0, planes = 0;
+    long plane = 0;
+    CUtensorMap map;
+    bool get(const void* b, int r, int c, int pt, long pl, int np, CUtensorMap* out) {
+        if (b != base || r != R || c != C || pt != pitch || pl != plane || np != planes) {
+            if (!make_tensor_map(&map, b, TVS_F32, r, c, pt, pl, np, kBW, kBH)) return false;
+            base = b; R = r; C = c; pitch = pt; plane = pl; planes = np;
+        }
+        *out = map;
+        return true;
+    }
+};
+thread_local MapCache g_map_p[4], g_map_phi[2], g_map_f1[2];
+thread_local int g_map_next[3];
+
+static MapCache* map_slot(MapCache* c, int n, int* next, const void* base) {
+    for (int i = 0; i < n; ++i)
+        if (c[i].base == base) return &c[i];
+    MapCache* r = &c[*next];
+    *next = (*next + 1) % n;
+    return r;
+}
+
+static bool tile_maps(const float* p, const float* phi, const float* f1, int R, int C, int pitch, long plane,
+                      CUtensorMap* mp, CUtensorMap* mphi, CUtensorMap* mf) {
+    if (!map_slot(g_map_p, 4, &g_map_next[0], p)->get(p, R, C, pitch, plane, 4, mp)) return false;
+    if (phi && !map_slot(g_map_phi, 2, &g_map_next[1], phi)->get(phi, R, C, pitch, (long)R * pitch, 1, mphi))
+        return false;
+    if (f1 && !map_slot(g_map_f1, 2, &g_map_next[2], f1)->get(f1, R, C, pitch, plane, 2, mf)) return false;
+    return true;
+}
+
+// One thread issues the box loads of a tile; every thread waits (bounded).
+// Returns false (after recording the error and draining) if a box never came.
+__device__ __forceinline__ bool tile_load(uint64_t* bar, uint32_t bytes, float* sp, const CUtensorMap* mp,
+                                          float* sphi, const CUtensorMap* mphi, float* sf, const CUtensorMap* mf,
+                                          int x, int y, unsigned* err) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        mbar_expect_tx(bar, bytes);
+        tma_load_3d(sp, mp, x, y, 0, bar);
+        if (sphi) tma_load_2d(sphi, mphi, x, y, bar);
+        if (sf) tma_load_3d(sf, mf, x, y, 0, bar);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(bar, 0);
+    if (__syncthreads_and(ok)) return true;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        atomicOr(err, 1u);
+        (void)mbar_wait(bar, 0);
+    }
+    return false;
+}
 
 // ---------------------------------------------------------------------------
 // tau0 (Neumann backward differences onto the extended grid)
@@ -50,38 +123,46 @@ cudaError_t launch_tau0(const float* d0, int d_pitch, int n2, int n1, float* tau
 
 // ---------------------------------------------------------------------------
 // s = div(vecdiv p) on the extended grid (the source of the Poisson solve in
-// every TFS iteration), tiled: p with a two-point halo, then w = vecdiv p with
-// a one-point halo, then s.  D^- reads its argument as zero in the last
-// column (x-part) or row (y-part) and outside the grid.
+// every TFS iteration): p arrives as one TMA box over its four planes, then
+// w = vecdiv p on a one-point halo, then s.  D^- reads its argument as zero in
+// the last column (x-part) or row (y-part) and outside the grid.
 // ---------------------------------------------------------------------------
+constexpr size_t kDivSmem = (size_t)4 * kBoxFloats * 4 + (size_t)2 * (kTY + 1) * (kTX + 1) * 4 + 256;
+
 __global__ void __launch_bounds__(kTX * kBY)
-div_vecdiv_kernel(const float* __restrict__ p, int R, int C, int pitch, long plane, float* __restrict__ S) {
-    constexpr int PH = kTY + 2, PW = kTX + 2;      // p region: rows i0-2.., cols j0-2..
-    __shared__ float sp[4][PH][PW + 1];
-    __shared__ float sw[2][PH - 1][PW];            // w region: rows i0-1.., cols j0-1..
+div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pitch, float* __restrict__ S,
+                  unsigned* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
+    constexpr int WH = kTY + 1, WW = kTX + 1;      // w region: rows i0-1.., cols j0-1..
+    float* sw = sp + 4 * kBoxFloats;               // [2][WH][WW]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sw + 2 * WH * WW + 1) ;
+    bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(bar) + 7) & ~static_cast<uintptr_t>(7));
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTX + tx;
     constexpr int NT = kTX * kBY;
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
-    for (int q = 0; q < 4; ++q) {
-        const bool xpart = (q & 1) == 0;
-        for (int idx = tid; idx < PH * PW; idx += NT) {
-            const int r = idx / PW, c = idx - r * PW;
-            const int i = i0 - 2 + r, j = j0 - 2 + c;
-            const bool ok = i >= 0 && j >= 0 && i < R && j < C && (xpart ? j <= C - 2 : i <= R - 2);
-            sp[q][r][c] = ok ? __ldg(&p[(size_t)q * plane + (size_t)i * pitch + j]) : 0.f;
-        }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < (PH - 1) * (PW - 1); idx += NT) {
-        const int r = idx / (PW - 1), c = idx - r * (PW - 1);   // w point (i0-1+r, j0-1+c)
+    if (!tile_load(bar, 4 * kBoxFloats * 4, sp, &pmap, nullptr, nullptr, nullptr, nullptr, j0 - kBoxC, i0 - kBoxR,
+                   err))
+        return;
+    // box value of plane q at grid (i, j) with the D^- rule
+    auto P = [&](int q, int i, int j) -> float {
+        const float v = sp[(q * kBH + (i - i0 + kBoxR)) * kBW + (j - j0 + kBoxC)];
+        const bool ok = (q & 1) == 0 ? j <= C - 2 : i <= R - 2;
+        return ok ? v : 0.f;
+    };
+    for (int idx = tid; idx < WH * WW; idx += NT) {
+        const int r = idx / WW, c = idx - r * WW;
         const int i = i0 - 1 + r, j = j0 - 1 + c;
-        const int pr = r + 1, pc = c + 1;                          // same point in the p region
-        const float w1 = (sp[0][pr][pc] - sp[0][pr][pc - 1]) + (sp[1][pr][pc] - sp[1][pr - 1][pc]);
-        const float w2 = (sp[2][pr][pc] - sp[2][pr][pc - 1]) + (sp[3][pr][pc] - sp[3][pr - 1][pc]);
-        const bool in = i >= 0 && j >= 0 && i < R && j < C;
-        sw[0][r][c] = (in && j <= C - 2) ? w1 : 0.f;
-        sw[1][r][c] = (in && i <= R - 2) ? w2 : 0.f;
+        float w1 = 0.f, w2 = 0.f;
+        if (i >= 0 && j >= 0 && i < R && j < C) {
+            w1 = (P(0, i, j) - P(0, i, j - 1)) + (P(1, i, j) - P(1, i - 1, j));
+            w2 = (P(2, i, j) - P(2, i, j - 1)) + (P(3, i, j) - P(3, i - 1, j));
+            if (j > C - 2) w1 = 0.f;
+            if (i > R - 2) w2 = 0.f;
+        }
+        sw[r * WW + c] = w1;
+        sw[(WH + r) * WW + c] = w2;
     }
     __syncthreads();
 #pragma unroll
@@ -89,15 +170,22 @@ div_vecdiv_kernel(const float* __restrict__ p, int R, int C, int pitch, long pla
         const int i = i0 + rr, j = j0 + tx;
         if (i < R && j < C) {
             const int r = rr + 1, c = tx + 1;
-            S[(size_t)i * pitch + j] = (sw[0][r][c] - sw[0][r][c - 1]) + (sw[1][r][c] - sw[1][r - 1][c]);
+            S[(size_t)i * pitch + j] = (sw[r * WW + c] - sw[r * WW + c - 1]) + (sw[(WH + r) * WW + c] - sw[(WH + r - 1) * WW + c]);
         }
     }
 }
 
-cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, cudaStream_t s) {
+cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, unsigned* err,
+                              cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(div_vecdiv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDivSmem);
+    });
+    CUtensorMap mp, unused;
+    if (!tile_maps(p, nullptr, nullptr, R, C, pitch, plane, &mp, &unused, &unused)) return cudaErrorInvalidValue;
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     ProfScope ps(kProfOther, s);
-    div_vecdiv_kernel<<<grd, blk, 0, s>>>(p, R, C, pitch, plane, S);
+    div_vecdiv_kernel<<<grd, blk, kDivSmem, s>>>(mp, R, C, pitch, S, err);
     return cudaGetLastError();
 }
 
@@ -127,62 +215,56 @@ cudaError_t launch_grad_sub(const float* u, int upitch, long uplane, const float
 }
 
 // ---------------------------------------------------------------------------
-// Fused TFS update / check.  The tile computes z on rows i0-1..i0+TY and
-// columns j0-1..j0+TX (the extra leading row/column serves div z for the
-// residual check), psi on the TY x TX outputs.
+// Fused TFS update / check.  p (4 planes), phi and f1 (2 planes) arrive as
+// TMA boxes; the tile computes z on rows i0-1..i0+TY and columns j0-1..j0+TX
+// (the extra leading row/column serves div z for the residual check), psi on
+// the TY x TX outputs.
 // ---------------------------------------------------------------------------
+constexpr int kZH = kTY + 2, kZW = kTX + 2;   // z region: rows i0-1.., cols j0-1..
+constexpr size_t kUpdSmem = (size_t)7 * kBoxFloats * 4 + (size_t)2 * kZH * kZW * 4 + 256;
+
 template <bool CHECK, bool WRITE_P, bool WRITE_TAU>
 __global__ void __launch_bounds__(kTX * kBY)
-tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const float* __restrict__ phi,
-                  const float* __restrict__ f1, int R, int C, int pitch, long plane, float t, float delta,
-                  float* __restrict__ tau_out, int tau_pitch, long tau_plane, double* __restrict__ partial) {
-    constexpr int ZH = kTY + 2, ZW = kTX + 2;     // z region: rows i0-1.., cols j0-1..
-    __shared__ float sxa[2][ZH][ZW + 1];           // p_kx rows i0-1..i0+TY, cols j0-2..j0+TX
-    __shared__ float sya[2][ZH + 1][ZW];           // p_ky rows i0-2..i0+TY, cols j0-1..j0+TX
-    __shared__ float sphi[ZH + 1][ZW + 1];         // phi  rows i0-1..i0+TY+1, cols j0-1..j0+TX+1
-    __shared__ float sz[2][ZH][ZW];
+tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap phimap,
+                  const __grid_constant__ CUtensorMap fmap, float* __restrict__ pout, int R, int C, int pitch,
+                  long plane, float t, float delta, float* __restrict__ tau_out, int tau_pitch, long tau_plane,
+                  double* __restrict__ partial, unsigned* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
+    float* sphi = sp + 4 * kBoxFloats;             // [BH][BW]
+    float* sf = sphi + kBoxFloats;                 // [2][BH][BW]
+    float* sz = sf + 2 * kBoxFloats;               // [2][ZH][ZW]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sz + 2 * kZH * kZW);   // 8-byte aligned (even float count)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTX + tx;
     constexpr int NT = kTX * kBY;
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
+    if (!tile_load(bar, 7 * kBoxFloats * 4, sp, &pmap, sphi, &phimap, sf, &fmap, j0 - kBoxC, i0 - kBoxR, err))
+        return;
+    // box offsets of grid point (i, j)
+    auto B = [&](int i, int j) -> int { return (i - i0 + kBoxR) * kBW + (j - j0 + kBoxC); };
 
-    for (int k = 0; k < 2; ++k) {
-        const float* __restrict__ pkx = pin + (size_t)(2 * k) * plane;
-        const float* __restrict__ pky = pin + (size_t)(2 * k + 1) * plane;
-        for (int idx = tid; idx < ZH * (ZW + 1); idx += NT) {
-            const int r = idx / (ZW + 1), c = idx - r * (ZW + 1);
-            const int i = i0 - 1 + r, j = j0 - 2 + c;
-            sxa[k][r][c] = (i >= 0 && i < R && j >= 0 && j <= C - 2) ? __ldg(&pkx[(size_t)i * pitch + j]) : 0.f;
-        }
-        for (int idx = tid; idx < (ZH + 1) * ZW; idx += NT) {
-            const int r = idx / ZW, c = idx - r * ZW;
-            const int i = i0 - 2 + r, j = j0 - 1 + c;
-            sya[k][r][c] = (i >= 0 && i <= R - 2 && j >= 0 && j < C) ? __ldg(&pky[(size_t)i * pitch + j]) : 0.f;
-        }
-    }
-    for (int idx = tid; idx < (ZH + 1) * (ZW + 1); idx += NT) {
-        const int r = idx / (ZW + 1), c = idx - r * (ZW + 1);
-        const int i = i0 - 1 + r, j = j0 - 1 + c;
-        sphi[r][c] = (i >= 0 && i < R && j >= 0 && j < C) ? __ldg(&phi[(size_t)i * pitch + j]) : 0.f;
-    }
-    __syncthreads();
-    // z = w - grad phi - f1 on the z region (zero outside the grid)
-    for (int idx = tid; idx < ZH * ZW; idx += NT) {
-        const int r = idx / ZW, c = idx - r * ZW;
+    // z = w - grad phi - f1 on the z region (zero outside the grid); w = vecdiv p
+    // with D^- reading x-parts as zero in the last column and y-parts in the last row
+    for (int idx = tid; idx < kZH * kZW; idx += NT) {
+        const int r = idx / kZW, c = idx - r * kZW;
         const int i = i0 - 1 + r, j = j0 - 1 + c;
         float z1 = 0.f, z2 = 0.f;
         if (i >= 0 && i < R && j >= 0 && j < C) {
-            const float w1 = (sxa[0][r][c + 1] - sxa[0][r][c]) + (sya[0][r + 1][c] - sya[0][r][c]);
-            const float w2 = (sxa[1][r][c + 1] - sxa[1][r][c]) + (sya[1][r + 1][c] - sya[1][r][c]);
-            const float pc = sphi[r][c];
-            const float gx = (j < C - 1) ? sphi[r][c + 1] - pc : 0.f;
-            const float gy = (i < R - 1) ? sphi[r + 1][c] - pc : 0.f;
-            const size_t o = (size_t)i * pitch + j;
-            z1 = w1 - gx - __ldg(&f1[o]);
-            z2 = w2 - gy - __ldg(&f1[plane + o]);
+            const int o = B(i, j);
+            const float xm = (j <= C - 2) ? 1.f : 0.f;   // x-part at (i, j) read as zero in the last column
+            const float ym = (i <= R - 2) ? 1.f : 0.f;   // y-part at (i, j) read as zero in the last row
+            const float w1 = (sp[o] * xm - sp[o - 1]) + (sp[kBoxFloats + o] * ym - sp[kBoxFloats + o - kBW]);
+            const float w2 = (sp[2 * kBoxFloats + o] * xm - sp[2 * kBoxFloats + o - 1]) +
+                             (sp[3 * kBoxFloats + o] * ym - sp[3 * kBoxFloats + o - kBW]);
+            const float pc = sphi[o];
+            const float gx = (j < C - 1) ? sphi[o + 1] - pc : 0.f;
+            const float gy = (i < R - 1) ? sphi[o + kBW] - pc : 0.f;
+            z1 = w1 - gx - sf[o];
+            z2 = w2 - gy - sf[kBoxFloats + o];
         }
-        sz[0][r][c] = z1;
-        sz[1][r][c] = z2;
+        sz[r * kZW + c] = z1;
+        sz[(kZH + r) * kZW + c] = z2;
     }
     __syncthreads();
 
@@ -193,16 +275,18 @@ tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const
         const int i = i0 + rr, j = j0 + tx;
         if (i < R && j < C) {
             const int r = rr + 1, c = tx + 1;   // position in the z region
+            const int ob = B(i, j);
             const size_t o = (size_t)i * pitch + j;
             float zc[2], gx[2], gy[2], pv[4];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                zc[k] = sz[k][r][c];
-                gx[k] = (j < C - 1) ? sz[k][r][c + 1] - zc[k] : 0.f;
-                gy[k] = (i < R - 1) ? sz[k][r + 1][c] - zc[k] : 0.f;
+                const float* zk = sz + k * kZH * kZW;
+                zc[k] = zk[r * kZW + c];
+                gx[k] = (j < C - 1) ? zk[r * kZW + c + 1] - zc[k] : 0.f;
+                gy[k] = (i < R - 1) ? zk[(r + 1) * kZW + c] - zc[k] : 0.f;
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) pv[q] = __ldg(&pin[(size_t)q * plane + o]);
+            for (int q = 0; q < 4; ++q) pv[q] = sp[q * kBoxFloats + ob];
             if (WRITE_P) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -216,7 +300,6 @@ tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const
                 tau_out[tau_plane + (size_t)i * tau_pitch + j] = -delta * zc[1];
             }
             if (CHECK) {
-                const size_t fo = o;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const float a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
@@ -224,16 +307,16 @@ tfs_update_kernel(const float* __restrict__ pin, float* __restrict__ pout, const
                     ks[0].add(ng);
                     ks[1].add(ng - (a * px + b * py));
                     ks[2].add(zc[k] * zc[k]);
-                    const float zf = zc[k] + __ldg(&f1[(size_t)k * plane + fo]);
+                    const float zf = zc[k] + sf[k * kBoxFloats + ob];
                     ks[3].add(zf * zf);
                     pmax = fmaxf(pmax, sqrtf(px * px + py * py));
                 }
                 // div z with the zero-extension rule of D^- (z_1 read as zero in
                 // the last column, z_2 in the last row)
                 const float z1c = (j <= C - 2) ? zc[0] : 0.f;
-                const float z1l = (j >= 1) ? sz[0][r][c - 1] : 0.f;
+                const float z1l = (j >= 1) ? sz[r * kZW + c - 1] : 0.f;
                 const float z2c = (i <= R - 2) ? zc[1] : 0.f;
-                const float z2u = (i >= 1) ? sz[1][r - 1][c] : 0.f;
+                const float z2u = (i >= 1) ? sz[(kZH + r - 1) * kZW + c] : 0.f;
                 dmax = fmaxf(dmax, fabsf((z1c - z1l) + (z2c - z2u)));
             }
         }
@@ -251,13 +334,23 @@ int tfs_blocks(int R, int C) { return ((C + kTX - 1) / kTX) * ((R + kTY - 1) / k
 
 cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, const float* f1, int R, int C,
                               int pitch, long plane, float t, float delta, bool check, bool write_p,
-                              float* tau_out, int tau_pitch, long tau_plane, double* partial, cudaStream_t s) {
+                              float* tau_out, int tau_pitch, long tau_plane, double* partial, unsigned* err,
+                              cudaStream_t s) {
+    CUtensorMap mp, mphi, mf;
+    if (!tile_maps(pin, phi, f1, R, C, pitch, plane, &mp, &mphi, &mf)) return cudaErrorInvalidValue;
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     const bool wt = tau_out != nullptr;
     ProfScope ps((check || !write_p) ? kProfTfsCheck : kProfTfsUpdate, s);
-#define TVS_TFS(CK, WP, WT)                                                                              \
-    tfs_update_kernel<CK, WP, WT><<<grd, blk, 0, s>>>(pin, pout, phi, f1, R, C, pitch, plane, t, delta, \
-                                                      tau_out, tau_pitch, tau_plane, partial)
+#define TVS_TFS(CK, WP, WT)                                                                                   \
+    do {                                                                                                      \
+        static std::once_flag once;                                                                          \
+        std::call_once(once, [] {                                                                            \
+            cudaFuncSetAttribute(tfs_update_kernel<CK, WP, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 (int)kUpdSmem);                                                             \
+        });                                                                                                   \
+        tfs_update_kernel<CK, WP, WT><<<grd, blk, kUpdSmem, s>>>(mp, mphi, mf, pout, R, C, pitch, plane, t,    \
+                                                                 delta, tau_out, tau_pitch, tau_plane, partial, err); \
+    } while (0)
     if (!check && write_p && !wt) TVS_TFS(false, true, false);
     else if (check && write_p && !wt) TVS_TFS(true, true, false);
     else if (check && !write_p && wt) TVS_TFS(true, false, true);
