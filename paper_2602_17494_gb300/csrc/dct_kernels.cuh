@@ -178,10 +178,25 @@ __device__ __forceinline__ void dft_all(float2 (&v)[16]) {
     }
 }
 
+// Pointwise step fused into the last pass of an FFT (the outputs are then in
+// natural order, output k of a line at k):
+//   kEpiNone : none
+//   kEpiMul  : X_k *= mul[k]                     (Bluestein's filter spectrum)
+//   kEpiOut  : for k < L, X_k <- chirp_k X_k + peel_g rot_k   (Bluestein's output)
+enum : int { kEpiNone = 0, kEpiMul = 1, kEpiOut = 2 };
+struct FftEpi {
+    const float2* mul;
+    const float2* chirp;
+    const float2* rot;
+    const float2* peel;
+    int L;
+};
+
 // One Stockham pass with everything about the shape known at compile time.
 // A thread "unit" holds UV = min(16, M) points: UV / R butterflies of radix R.
-template <int R, bool INV, int UPT, int M, int NS, int UVMAX>
-__device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+template <int R, bool INV, int UPT, int M, int NS, int UVMAX, int EPI>
+__device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
+                                              const FftEpi& ep) {
     constexpr int UV = M < UVMAX ? M : UVMAX;    // points per unit
     constexpr int B = UV / R;                    // butterflies per unit
     constexpr int U = M / UV;                    // units per transform
@@ -245,7 +260,16 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                 const int jm = j & (NS - 1);
                 const int dst = (j - jm) * R + jm;   // (j / NS) * NS * R + j % NS
 #pragma unroll
-                for (int r = 0; r < R; ++r) x[pidx(dst + r * NS)] = v[q][b * R + r];
+                for (int r = 0; r < R; ++r) {
+                    float2 y = v[q][b * R + r];
+                    if (EPI == kEpiMul) {
+                        y = c_mul(y, __ldg(&ep.mul[dst + r * NS]));
+                    } else if (EPI == kEpiOut) {
+                        const int k = dst + r * NS;
+                        if (k < ep.L) y = c_add(c_mul(__ldg(&ep.chirp[k]), y), c_mul(ep.peel[g], __ldg(&ep.rot[k])));
+                    }
+                    x[pidx(dst + r * NS)] = y;
+                }
             }
         }
     }
@@ -254,13 +278,16 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
 
 // The pass sequence for M = 2^LOGM: radix 16 while at least 16 points remain
 // per sub-transform, then the remaining 8, 4 or 2.
-template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV>
-__device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, int EPI>
+__device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
+                                         const FftEpi& ep) {
     if constexpr (LOGNS < LOGM) {
         constexpr int REM = LOGM - LOGNS;
         constexpr int LR = REM >= LOGUV ? LOGUV : REM;
-        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS), (1 << LOGUV)>(buf, stride, nfft, tw);
-        fft_from<LOGM, LOGNS + LR, INV, UPT, LOGUV>(buf, stride, nfft, tw);
+        constexpr bool LAST = LOGNS + LR == LOGM;
+        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS), (1 << LOGUV), LAST ? EPI : kEpiNone>(
+            buf, stride, nfft, tw, ep);
+        fft_from<LOGM, LOGNS + LR, INV, UPT, LOGUV, EPI>(buf, stride, nfft, tw, ep);
     }
 }
 
@@ -276,9 +303,10 @@ struct FftShape {
     static constexpr int UPT = UNITS > kDctThreads ? 2 : 1;
 };
 
-template <int LOGM, bool INV>
-__device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
-    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT, FftShape<LOGM>::LOGUV>(buf, stride, nfft, tw);
+template <int LOGM, bool INV, int EPI = kEpiNone>
+__device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
+                                             const FftEpi& ep = FftEpi{}) {
+    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT, FftShape<LOGM>::LOGUV, EPI>(buf, stride, nfft, tw, ep);
 }
 
 // Chirp filter spectrum: b[m] = conj(c_m) for lags m in [-(L-2), L-1] stored
@@ -321,23 +349,11 @@ __device__ __forceinline__ size_t row_off(const BatchArgs& ba, int2 rr, int r, i
 // --------------------------------------------------------------------------
 template <int LOGM>
 __device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const DctPlan& pl, const float2* peel) {
-    const int L = pl.L, M = pl.M;
-    fft_stockham<LOGM, false>(buf, stride, G, pl.tw);
-    for (int b = threadIdx.x; b < G * M; b += blockDim.x) {
-        const int g = b >> pl.logM;
-        const int k = b & (M - 1);
-        float2* x = buf + (size_t)g * stride + pidx(k);
-        *x = c_mul(*x, __ldg(&pl.bhat[k]));
-    }
-    __syncthreads();
-    fft_stockham<LOGM, true>(buf, stride, G, pl.tw);
-    for (int b = threadIdx.x; b < G * L; b += blockDim.x) {
-        const int g = b / L;
-        const int k = b - g * L;
-        float2* x = buf + (size_t)g * stride + pidx(k);
-        *x = c_add(c_mul(__ldg(&pl.chirp[k]), *x), c_mul(peel[g], __ldg(&pl.rot[k])));
-    }
-    __syncthreads();
+    const FftEpi ep{pl.bhat, pl.chirp, pl.rot, peel, pl.L};
+    // FFT, times the filter spectrum (fused into the last pass), inverse FFT,
+    // then the chirp and the peeled sample (fused into its last pass)
+    fft_stockham<LOGM, false, kEpiMul>(buf, stride, G, pl.tw, ep);
+    fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, pl.tw, ep);
 }
 
 // Makhoul's reordering: position of input sample j in the reordered line.
@@ -537,8 +553,7 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
     S += (size_t)blockIdx.y * ba.bstride;
     const int L = rows, M = pl.M, stride = padded_len(M);
     float2* buf = sm;
-    float2* ybuf = sm + (size_t)G * stride;       // G x L staged spectra
-    float2* peel = ybuf + (size_t)G * L;
+    float2* peel = sm + (size_t)G * stride;
     const int npairs = (cols + 1) >> 1;
     const float invL = 1.0f / (float)L;
     {
@@ -559,23 +574,39 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
         bluestein<LOGM>(buf, stride, gc, pl, peel);
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int g = b / L;
-            const int k = b - g * L;
+        // Spectrum step in place: one thread per pair (k, L - k) reads both lines'
+        // DCT-II values at k and L - k, multiplies by (tilde Delta)^dagger and
+        // writes the inverse transform's staged inputs back to the same two
+        // positions (position L - 1 goes to the peel slot and is cleared).
+        const int half = L / 2 + 1;
+        for (int b = threadIdx.x; b < gc * half; b += blockDim.x) {
+            const int g = b / half;
+            const int k = b - g * half;
+            const int km = k == 0 ? 0 : L - k;
+            if (k > km) continue;                            // each pair once
             const int c0 = 2 * (base + g);
-            const float2 X = unpack_dct2(buf + (size_t)g * stride, k, L, pl);
-            ybuf[(size_t)g * L + k] = make_float2(X.x * lap_symbol(k, c0, rows, cols),
-                                                  X.y * lap_symbol(k, c0 + 1, rows, cols));
+            float2* bufg = buf + (size_t)g * stride;
+            const float2 Xk = unpack_dct2(bufg, k, L, pl);
+            const float2 Xm = unpack_dct2(bufg, km, L, pl);
+            const float2 Yk = make_float2(Xk.x * lap_symbol(k, c0, rows, cols), Xk.y * lap_symbol(k, c0 + 1, rows, cols));
+            const float2 Ym = make_float2(Xm.x * lap_symbol(km, c0, rows, cols),
+                                          Xm.y * lap_symbol(km, c0 + 1, rows, cols));
+            if (k == 0) {
+                stage_sample(bufg, peel + g, 0, L, pack_dct3(Yk.x, 0.f, Yk.y, 0.f, 0, pl), pl);
+            } else {
+                stage_sample(bufg, peel + g, k, L, pack_dct3(Yk.x, Ym.x, Yk.y, Ym.y, k, pl), pl);
+                if (km != k) stage_sample(bufg, peel + g, km, L, pack_dct3(Ym.x, Yk.x, Ym.y, Yk.y, km, pl), pl);
+            }
+            if (k == 0 ? L == 1 : km == L - 1) bufg[pidx(L - 1)] = make_float2(0.f, 0.f);
         }
-        __syncthreads();
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int g = b / L;
-            const int k = b - g * L;
-            const float2 yk = ybuf[(size_t)g * L + k];
-            const float2 ym = k ? ybuf[(size_t)g * L + L - k] : make_float2(0.f, 0.f);
-            stage_sample(buf + (size_t)g * stride, peel + g, k, L, pack_dct3(yk.x, ym.x, yk.y, ym.y, k, pl), pl);
+        // the rest of the zero tail, [L, M), is read by no thread above
+        {
+            const int tl = M - L;
+            for (int b = threadIdx.x; b < gc * tl; b += blockDim.x) {
+                const int g = b / tl;
+                buf[(size_t)g * stride + pidx(L + (b - g * tl))] = make_float2(0.f, 0.f);
+            }
         }
-        zero_tail(buf, stride, gc, L, M);
         __syncthreads();
         bluestein<LOGM>(buf, stride, gc, pl, peel);
         for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
@@ -644,8 +675,8 @@ template <int LM>
 cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                            int nbatch, cudaStream_t s) {
     static std::once_flag once;
-    const size_t smem = (size_t)(padded_len(pl.M) + rows + 1) * sizeof(float2);
-    std::call_once(once, [] { allow_dct_smem(dct_cols_solve_kernel<LM>, (size_t)(padded_len(1 << LM) + (1 << (LM - 1)) + 2) * sizeof(float2)); });
+    const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    std::call_once(once, [smem] { allow_dct_smem(dct_cols_solve_kernel<LM>, smem); });
     const dim3 grid((cols + 1) / 2, nbatch);
     dct_cols_solve_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
     return cudaGetLastError();
