@@ -110,7 +110,7 @@ const char* tvs_last_error(void);
 /* Bytes of scratch needed by a call.
  *   step = 1: tvs_step1 / tvs_schwarz(step=1); step = 2: tvs_step2 /
  *   tvs_schwarz(step=2); step = 0: tvs_denoise (covers both); step = 3:
- *   tvs_project.  dd = NULL means the global iteration.  storage: the
+ *   tvs_project; step = 4: tvs_quality.  dd = NULL means the global iteration.  storage: the
  *   tvs_iter.storage of the (step-2) call.  Returns 0 for invalid sizes or
  *   a storage the step does not support. */
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage);
@@ -193,6 +193,16 @@ typedef struct {
 } tvs_kernel_time;
 int tvs_profile_enable(int on);
 int tvs_profile_read(tvs_kernel_time* out, int cap);
+
+/* Quality of a reconstruction d against a ground truth gt (Section 5.3),
+ * both n2 x n1 dense float with intensities in [0, 1] (largest value R = 1):
+ *   psnr  = -10 log10(mean (d - gt)^2)          (+infinity if d == gt)
+ *   mssim = single-window structural similarity over the whole image with
+ *           population moments and c1 = (0.01 R)^2, c2 = (0.03 R)^2.
+ * Sums are formed in FP32 per thread (compensated) and reduced in FP64.
+ * ws: tvs_workspace_bytes(4, n2, n1, NULL, 0) bytes.  Synchronizes stream. */
+tvs_status tvs_quality(const float* d, const float* gt, int n2, int n1, void* ws, size_t ws_bytes,
+                       cudaStream_t stream, double* psnr, double* mssim);
 
 /* ---------------------------------------------------------------------------
  * Batching and serving engine.  The paper has no counterpart (it denoises one

@@ -16,7 +16,8 @@ Model" (Langer, Runft, Rahman, Tai, Wu):
                   (Sections 3, 4.2, Appendix A);
 * ``schwarz``  -- partition of unity, Algorithm 2 with Algorithm 3 (both
                   steps), Algorithm 4 and the localized Algorithm 5 with the
-                  block formula for the localized projection (Section 6).
+                  block formula for the localized projection (Section 6);
+* ``quality``  -- PSNR and single-window MSSIM (Section 5.3).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 identities, closed forms, library routines or brute force, except the exact

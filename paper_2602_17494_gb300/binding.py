@@ -100,6 +100,8 @@ def _load() -> ctypes.CDLL:
     lib.tvs_engine_pending.argtypes = [P]
     lib.tvs_engine_destroy.restype = None
     lib.tvs_engine_destroy.argtypes = [P]
+    lib.tvs_quality.restype = I
+    lib.tvs_quality.argtypes = [P, P, I, I, P, S, P, ctypes.POINTER(D), ctypes.POINTER(D)]
     IP = ctypes.POINTER(I)
     lib.tvs_tune_workspace_bytes.restype = S
     lib.tvs_tune_workspace_bytes.argtypes = [I, I, IP, I, IP, I, I]
@@ -119,7 +121,7 @@ _lib = _load()
 EXPORTED = ["tvs_denoise", "tvs_engine_create", "tvs_engine_destroy", "tvs_engine_pending",
             "tvs_engine_pool_overhead", "tvs_engine_request_bytes", "tvs_engine_step", "tvs_engine_submit",
             "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
-            "tvs_project_noalloc", "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2",
+            "tvs_project_noalloc", "tvs_quality", "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2",
             "tvs_tune_schwarz2", "tvs_tune_workspace_bytes", "tvs_version",
             "tvs_workspace_bytes"]
 
@@ -347,3 +349,14 @@ def tvs_tune_schwarz2(d0: torch.Tensor, tau: torch.Tensor, alpha: float, eps: fl
                                 _stream(d0.device), best, ctypes.byref(ms))
     _check(st, "tvs_tune_schwarz2", False)
     return (best[0], best[1], best[2]), ms.value
+
+
+def tvs_quality(d: torch.Tensor, gt: torch.Tensor, ws: torch.Tensor | None = None):
+    """(PSNR, MSSIM) of d against gt (Section 5.3)."""
+    n2, n1 = d.shape
+    ws = workspace(4, max(n2, 2), max(n1, 2), device=d.device) if ws is None else ws
+    ps, ms = ctypes.c_double(), ctypes.c_double()
+    st = _lib.tvs_quality(_ptr(d), _ptr(gt), n2, n1, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d.device),
+                          ctypes.byref(ps), ctypes.byref(ms))
+    _check(st, "tvs_quality", False)
+    return ps.value, ms.value

@@ -388,6 +388,10 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
         if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L.P, storage);
         return b;
     }
+    if (step == 4) {
+        RedBuf rb;
+        return quality_layout(cv, rb);
+    }
     if (step == 0) {
         Step1Layout L1;
         layout_step1(cv, n2, n1, L1);

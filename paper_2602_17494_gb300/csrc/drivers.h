@@ -68,4 +68,7 @@ tvs_status tfs_setup(const Step1Layout& L, const float* d0, int n2, int n1, doub
 tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1, double alpha, const tvs_iter& it,
                         float* d, float* p_user, cudaStream_t s, tvs_report* rep);
 
+// quality.cu: workspace of tvs_quality
+size_t quality_layout(Carver& cv, RedBuf& rb);
+
 }  // namespace tvs

@@ -356,3 +356,19 @@ def test_schwarz2_full_size_reaches_global_minimiser(B, n, k):
     dist = torch.linalg.vector_norm((g.out - s.out).double()).item()
     bound = np.sqrt(2 * g.report["gap"] / 10.0) + np.sqrt(2 * s.report["gap"] / 10.0)
     assert dist <= bound * 1.05 + 1e-6 * n, (dist, bound)   # + FP32 rounding of d
+
+
+# ---------------------------------------------------------------------------
+# quality measures (Section 5.3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n2,n1", [(64, 64), (257, 130), (1024, 1024)])
+def test_quality_matches_oracle(B, n2, n1):
+    import oracle.quality as oq
+    clean, noisy = noisy_scene(SceneSpec(n2, n1, 7, 0.1, True))
+    d = noisy.astype(np.float32)
+    gt = clean.astype(np.float32)
+    ps, ms = B.tvs_quality(cuda(d), cuda(gt))
+    assert ps == pytest.approx(oq.psnr(d, gt), rel=1e-6)
+    assert ms == pytest.approx(oq.mssim(d, gt), rel=1e-6)
+    ps2, ms2 = B.tvs_quality(cuda(gt), cuda(gt))
+    assert ps2 == float("inf") and ms2 == pytest.approx(1.0, abs=1e-6)
