@@ -74,6 +74,23 @@ def work_units() -> float:
     return float((N + 1) * (N + 1) * ITERS1 + N * N * K_INNER * OUTER)
 
 
+def replica_value(local_total_ms: float, world: int, steps: int, dist=None, device=None):
+    """Whole-job throughput of `world` independent replicas.
+
+    Each rank ran `steps` steps on its own image; the job took as long as its
+    slowest rank, so the time is the maximum over ranks (a host-side timing
+    reduction, not part of the data path).  Returns (value in Gpixel-iter/s,
+    max total ms).
+    """
+    total = float(local_total_ms)
+    if world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return work_units() * world * steps / (total / 1e3) / 1e9, total
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -240,13 +257,8 @@ def run_gpu(args):
             torch.cuda.synchronize(dev)
             times.append(e0.elapsed_time(e1))
     clocks = clk.summary()
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = replica_value(float(np.sum(times)), world, args.steps, dist, dev)
     ms_step = total_ms / args.steps
-    value = work_units() * world * args.steps / (total_ms / 1e3) / 1e9
 
     # ---- per-kernel device time (CUDA events around each launch) ----------
     B.tvs_profile_enable(True)
