@@ -214,6 +214,24 @@ schwarz2_tile_kernel(TileArgs<S> a) {
     cl.sync();   // no CTA leaves while a neighbour could still address its shared memory
 }
 
+// Packed f32x2 arithmetic (one instruction for two lanes, each rounded to
+// nearest like its scalar counterpart) and single-instruction approximate
+// reciprocal and reciprocal square root with subnormals flushed to zero.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------------------
 // Small subdomains: one CTA per subdomain, 4 x 4 pixels per thread
 // ---------------------------------------------------------------------------
@@ -264,28 +282,75 @@ __host__ __device__ __forceinline__ int excl_hi(const Axis& A, int k) {
 //   end    : q_m = v; on the part of the core that no other subdomain
 //            reaches, p^{n+1} = (1 - alpha_hat) p^n + alpha_hat q_m directly
 //            (the overlap strips are combined by schwarz2_strip_kernel).
-// Shared memory: p^n_x, p^n_y and g_m as float4 [r][ty][tx]; edge arrays
-// (floats) vedge_x [r][ty][tx], vedge_y [c][ty][tx], the same two for z;
-// theta_x and theta_y of the block's columns and rows.  With tx fastest and
-// rows of TX threads, the two thread rows a warp spans hit disjoint banks.
+// Shared memory: p^n_x, p^n_y as float4 [r][ty][tx]; g_m and t / theta as
+// float4 [q][ty][tx] holding two vertical pixel pairs each; edge arrays v_x
+// of the last column and z of the first column as float2 [pair][ty][tx],
+// v_y of the last row and z of the first row as float4 [ty][tx]; theta_x and
+// theta_y of the block's columns and rows.  With tx fastest and rows of TX
+// threads, a warp's accesses are contiguous.
+// The inner loop works on vertical pixel pairs with f32x2 instructions: the
+// differences along x, the sums and the pointwise update are packed, the
+// differences along y are scalar.  It needs no mask inside the image:
+// t / theta is +inf outside Gamma_m, which sets v = 0 there, and only blocks
+// that reach the last image row or column apply the D^+ boundary rule.
 __host__ __device__ __forceinline__ size_t small_tile_smem_bytes(int tx, int ty) {
-    return ((size_t)ty * tx * (12 * kSmallRH + 2 * (kSmallRH + kSmallCW)) + kSmallCW * tx + kSmallRH * ty + 2) *
+    return ((size_t)ty * tx * (4 * kSmallRH * kSmallCW + 2 * (kSmallRH + kSmallCW)) + kSmallCW * tx + kSmallRH * ty +
+            2) *
            sizeof(float);
+}
+
+__device__ __forceinline__ float& half_of(float2& v, int h) { return h ? v.y : v.x; }
+
+// One pointwise update of Algorithm 3 on the thread's pixels, given z on
+// them, on the column to their right (zr) and the row below (zd):
+// psi = grad z (D^+), v <- (v + t psi) / (1 + (t / theta) |psi|).
+// The 1e-30 keeps the reciprocal square root finite where psi = 0 and is far
+// below the resolution of |psi|.
+template <bool EDGE, int RP, int CW>
+__device__ __forceinline__ void small_tile_update(float2 (&VX)[RP][CW], float2 (&VY)[RP][CW],
+                                                  const float2 (&Z)[RP][CW], const float2 (&zr)[RP],
+                                                  const float (&zd)[CW], const float4* coef, int stride, float t,
+                                                  int jb, int ib, int N1, int N2) {
+    const float2 t2 = make_float2(t, t), one2 = make_float2(1.0f, 1.0f), eps2 = make_float2(1e-30f, 1e-30f);
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const float4 c4 = coef[(rp * (CW / 2) + c / 2) * stride];   // t / theta of pixel pairs c & ~1, c | 1
+            const float2 cf = (c & 1) ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+            float2 gx = sub2(c + 1 < CW ? Z[rp][c + 1] : zr[rp], Z[rp][c]);
+            float2 gy;
+            gy.x = Z[rp][c].y - Z[rp][c].x;
+            gy.y = (rp + 1 < RP ? Z[rp + 1][c].x : zd[c]) - Z[rp][c].y;
+            if (EDGE) {   // D^+ is zero at the last column and the last row
+                if (jb + c >= N1 - 1) gx = make_float2(0.f, 0.f);
+                if (ib + 2 * rp >= N2 - 1) gy.x = 0.0f;
+                if (ib + 2 * rp + 1 >= N2 - 1) gy.y = 0.0f;
+            }
+            const float2 s2 = fma2(gx, gx, fma2(gy, gy, eps2));
+            const float2 ng = mul2(s2, make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y)));   // |psi|
+            const float2 den = fma2(cf, ng, one2);
+            const float2 inv = make_float2(rcp_ftz(den.x), rcp_ftz(den.y));
+            VX[rp][c] = mul2(fma2(t2, gx, VX[rp][c]), inv);
+            VY[rp][c] = mul2(fma2(t2, gy, VY[rp][c]), inv);
+        }
 }
 
 template <class S, int MAXT, int MINB, bool MULTI>
 __global__ void __launch_bounds__(MAXT, MINB)
 schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     using St = Stor<S>;
-    constexpr int RH = kSmallRH, CW = kSmallCW;
+    constexpr int RH = kSmallRH, CW = kSmallCW, RP = RH / 2;
+    static_assert(RH % 2 == 0 && CW == 4, "vertical pixel pairs, one float4 of q per row");
     extern __shared__ float4 sm4[];
     const int TX = blockDim.x, TY = blockDim.y;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NB = TY * RH * TX;                  // float4 slots per array
     float4* spx = sm4;                            // [RH][TY][TX]
     float4* spy = spx + NB;
-    float4* gs = spy + NB;
-    float* evx = reinterpret_cast<float*>(gs + NB);   // [RH][TY][TX]
+    float4* gs = spy + NB;                        // [RP * CW / 2][TY][TX], vertical pixel pairs
+    float4* cs = gs + NB;                         // t / theta, same layout
+    float* evx = reinterpret_cast<float*>(cs + NB);   // [RH][TY][TX]
     float* evy = evx + TY * RH * TX;                  // [CW][TY][TX]
     float* ezx = evy + TY * CW * TX;                  // [RH][TY][TX]
     float* ezy = ezx + TY * RH * TX;                  // [CW][TY][TX]
@@ -330,6 +395,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         const float thxl = sthx[tx * CW];         // column left of the block
         const float thyu = sthy[ty * RH];         // row above the block
         float wyu[CW];                            // w_y of the row above
+        float gk[RH][CW];                         // g_m of the thread's pixels
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
             const int i = ib - 1, j = jb + c;
@@ -380,12 +446,22 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                 gr[c] = gv;
                 wyu[c] = wyc;
             }
-            gs[(r * TY + ty) * TX + tx] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+#pragma unroll
+            for (int c = 0; c < CW; ++c) gk[r][c] = gr[c];
         }
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+            for (int c2 = 0; c2 < CW / 2; ++c2)
+                gs[((rp * (CW / 2) + c2) * TY + ty) * TX + tx] =
+                    make_float4(gk[2 * rp][2 * c2], gk[2 * rp + 1][2 * c2], gk[2 * rp][2 * c2 + 1],
+                                gk[2 * rp + 1][2 * c2 + 1]);
     }
 
     // ---- warm start q_m ---------------------------------------------------
-    float vx[RH][CW], vy[RH][CW];
+    // v is held as vertical pixel pairs, VX[rp][c] = (v_x(2 rp, c), v_x(2 rp + 1, c)),
+    // so that differences along x and the pointwise update run as f32x2.
+    float2 VX[RP][CW], VY[RP][CW];
     S* qx = static_cast<S*>(im.q) + (size_t)sub * 2 * im.hmax * im.qp;
     S* qy = qx + (size_t)im.hmax * im.qp;
 #pragma unroll
@@ -403,73 +479,78 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
             const bool in = thy[r] > 0.0f && thx[c] > 0.0f;
-            vx[r][c] = (in && jb + c <= N1 - 2) ? ax4[c] : 0.0f;
-            vy[r][c] = (in && ib + r <= N2 - 2) ? ay4[c] : 0.0f;
+            half_of(VX[r / 2][c], r & 1) = (in && jb + c <= N1 - 2) ? ax4[c] : 0.0f;
+            half_of(VY[r / 2][c], r & 1) = (in && ib + r <= N2 - 2) ? ay4[c] : 0.0f;
         }
     }
-    // t / theta as a product of per-row and per-column factors (0 outside Gamma_m)
-    float try_[RH], rthx[CW];
+    // t / theta per pixel; +inf outside Gamma_m, where the update then gives
+    // v = (v + t psi) * 0 = 0, so no mask is needed there
+    const int me = ty * TX + tx;
+    {
+        const float inf = __int_as_float(0x7f800000);
+        float rty[RH], rtx[CW];
 #pragma unroll
-    for (int r = 0; r < RH; ++r) try_[r] = thy[r] > 0.0f ? t / thy[r] : 0.0f;
+        for (int r = 0; r < RH; ++r) rty[r] = thy[r] > 0.0f ? t / thy[r] : inf;
 #pragma unroll
-    for (int c = 0; c < CW; ++c) rthx[c] = thx[c] > 0.0f ? 1.0f / thx[c] : 0.0f;
+        for (int c = 0; c < CW; ++c) rtx[c] = thx[c] > 0.0f ? 1.0f / thx[c] : inf;
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+            for (int c2 = 0; c2 < CW / 2; ++c2)
+                cs[(rp * (CW / 2) + c2) * TY * TX + me] =
+                    make_float4(rty[2 * rp] * rtx[2 * c2], rty[2 * rp + 1] * rtx[2 * c2],
+                                rty[2 * rp] * rtx[2 * c2 + 1], rty[2 * rp + 1] * rtx[2 * c2 + 1]);
+    }
+    // Blocks that reach the image's last column or row apply the D^+ boundary
+    // rule (psi_x = 0 in the last column, psi_y = 0 in the last row).
+    const bool edge = xa + CW * TX >= N1 || y0 + RH * TY >= N2;
+    float2* evx2 = reinterpret_cast<float2*>(evx);   // v_x of the last column, [RP][TY][TX]
+    float4* evy4 = reinterpret_cast<float4*>(evy);   // v_y of the last row, [TY][TX]
+    float2* ezx2 = reinterpret_cast<float2*>(ezx);   // z of the first column, [RP][TY][TX]
+    float4* ezy4 = reinterpret_cast<float4*>(ezy);   // z of the first row, [TY][TX]
 
     // ---- k inner updates on chip (Algorithm 3) --------------------------
     for (int it = 0; it < a.k; ++it) {
 #pragma unroll
-        for (int r = 0; r < RH; ++r) evx[(r * TY + ty) * TX + tx] = vx[r][CW - 1];
-#pragma unroll
-        for (int c = 0; c < CW; ++c) evy[(c * TY + ty) * TX + tx] = vy[RH - 1][c];
+        for (int rp = 0; rp < RP; ++rp) evx2[rp * TY * TX + me] = VX[rp][CW - 1];
+        evy4[me] = make_float4(VY[RP - 1][0].y, VY[RP - 1][1].y, VY[RP - 1][2].y, VY[RP - 1][3].y);
         __syncthreads();
-        float z[RH][CW];
+        float2 Z[RP][CW];
         {
-            float vxl[RH], vyu[CW];
+            float2 vxl[RP];
 #pragma unroll
-            for (int r = 0; r < RH; ++r) vxl[r] = tx > 0 ? evx[(r * TY + ty) * TX + tx - 1] : 0.0f;
+            for (int rp = 0; rp < RP; ++rp) vxl[rp] = tx > 0 ? evx2[rp * TY * TX + me - 1] : make_float2(0.f, 0.f);
+            const float4 u4 = ty > 0 ? evy4[me - TX] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float vyu[CW] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
-            for (int c = 0; c < CW; ++c) vyu[c] = ty > 0 ? evy[(c * TY + ty - 1) * TX + tx] : 0.0f;
+            for (int rp = 0; rp < RP; ++rp)
 #pragma unroll
-            for (int r = 0; r < RH; ++r) {
-                const float4 g4 = gs[(r * TY + ty) * TX + tx];
-                const float gr[CW] = {g4.x, g4.y, g4.z, g4.w};
+                for (int c2 = 0; c2 < CW / 2; ++c2) {
+                    const float4 g4 = gs[(rp * (CW / 2) + c2) * TY * TX + me];
+                    const float2 gp[2] = {make_float2(g4.x, g4.y), make_float2(g4.z, g4.w)};
 #pragma unroll
-                for (int c = 0; c < CW; ++c) {
-                    const float left = c > 0 ? vx[r][c - 1] : vxl[r];
-                    const float up = r > 0 ? vy[r - 1][c] : vyu[c];
-                    // outside the z region z is never read by an update of Gamma_m
-                    z[r][c] = ((vx[r][c] - left) + (vy[r][c] - up)) - gr[c];
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < RH; ++r) ezx[(r * TY + ty) * TX + tx] = z[r][0];
-#pragma unroll
-        for (int c = 0; c < CW; ++c) ezy[(c * TY + ty) * TX + tx] = z[0][c];
-        __syncthreads();
-        {
-            float zr[RH], zd[CW];
-#pragma unroll
-            for (int r = 0; r < RH; ++r) zr[r] = tx + 1 < TX ? ezx[(r * TY + ty) * TX + tx + 1] : 0.0f;
-#pragma unroll
-            for (int c = 0; c < CW; ++c) zd[c] = ty + 1 < TY ? ezy[(c * TY + ty + 1) * TX + tx] : 0.0f;
-#pragma unroll
-            for (int r = 0; r < RH; ++r)
-#pragma unroll
-                for (int c = 0; c < CW; ++c) {
-                    const float zc = z[r][c];
-                    const float right = c + 1 < CW ? z[r][c + 1] : zr[r];
-                    const float down = r + 1 < RH ? z[r + 1][c] : zd[c];
-                    const float gx = (jb + c < N1 - 1) ? right - zc : 0.0f;   // D^+ zero at the last column
-                    const float gy = (ib + r < N2 - 1) ? down - zc : 0.0f;    // and the last row
-                    const float s2 = gx * gx + gy * gy;
-                    const float ng = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;     // |psi|
-                    const float inv = __fdividef(1.0f, fmaf(try_[r] * rthx[c], ng, 1.0f));
-                    if (try_[r] > 0.0f && rthx[c] > 0.0f) {
-                        vx[r][c] = fmaf(t, gx, vx[r][c]) * inv;
-                        vy[r][c] = fmaf(t, gy, vy[r][c]) * inv;
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = 2 * c2 + h;
+                        const float2 dx = sub2(VX[rp][c], c > 0 ? VX[rp][c - 1] : vxl[rp]);
+                        float2 dy;
+                        dy.x = VY[rp][c].x - (rp > 0 ? VY[rp - 1][c].y : vyu[c]);
+                        dy.y = VY[rp][c].y - VY[rp][c].x;
+                        // outside the z region z is never read by an update of Gamma_m
+                        Z[rp][c] = sub2(add2(dx, dy), gp[h]);
                     }
                 }
         }
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp) ezx2[rp * TY * TX + me] = Z[rp][0];
+        ezy4[me] = make_float4(Z[0][0].x, Z[0][1].x, Z[0][2].x, Z[0][3].x);
+        __syncthreads();
+        float2 zr[RP];
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp) zr[rp] = tx + 1 < TX ? ezx2[rp * TY * TX + me + 1] : make_float2(0.f, 0.f);
+        const float4 d4 = ty + 1 < TY ? ezy4[me + TX] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float zd[CW] = {d4.x, d4.y, d4.z, d4.w};
+        if (edge) small_tile_update<true, RP, CW>(VX, VY, Z, zr, zd, cs + me, TY * TX, t, jb, ib, N1, N2);
+        else small_tile_update<false, RP, CW>(VX, VY, Z, zr, zd, cs + me, TY * TX, t, jb, ib, N1, N2);
     }
 
     // ---- new warm start q_m; p^{n+1} on the exclusive core -----------------
@@ -478,8 +559,15 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         if (ib + r < y1 && tx * CW < im.qp) {
             const size_t qo = (size_t)(ib + r - y0) * im.qp + tx * CW;
             const size_t qi = (size_t)sub * im.hmax * im.qp + qo;
-            St::st4(qx + qo, make_float4(vx[r][0], vx[r][1], vx[r][2], vx[r][3]), rkey(a.seed, qi, 0));
-            St::st4(qy + qo, make_float4(vy[r][0], vy[r][1], vy[r][2], vy[r][3]), rkey(a.seed, qi, 1));
+            const int rp = r / 2, h = r & 1;
+            St::st4(qx + qo,
+                    make_float4(half_of(VX[rp][0], h), half_of(VX[rp][1], h), half_of(VX[rp][2], h),
+                                half_of(VX[rp][3], h)),
+                    rkey(a.seed, qi, 0));
+            St::st4(qy + qo,
+                    make_float4(half_of(VY[rp][0], h), half_of(VY[rp][1], h), half_of(VY[rp][2], h),
+                                half_of(VY[rp][3], h)),
+                    rkey(a.seed, qi, 1));
         }
     const int ey0 = excl_lo(im.ay, my), ey1 = excl_hi(im.ay, my);
     const int ex0 = excl_lo(im.ax, mx), ex1 = excl_hi(im.ax, mx);
@@ -492,10 +580,11 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         const int i = ib + r;
         if (i < ey0 || i >= ey1) continue;
         const float4 u = spx[(r * TY + ty) * TX + tx], w = spy[(r * TY + ty) * TX + tx];
-        const float4 ox = make_float4(fmaf(ah, vx[r][0], bh * u.x), fmaf(ah, vx[r][1], bh * u.y),
-                                      fmaf(ah, vx[r][2], bh * u.z), fmaf(ah, vx[r][3], bh * u.w));
-        const float4 oy = make_float4(fmaf(ah, vy[r][0], bh * w.x), fmaf(ah, vy[r][1], bh * w.y),
-                                      fmaf(ah, vy[r][2], bh * w.z), fmaf(ah, vy[r][3], bh * w.w));
+        const int rp = r / 2, h = r & 1;
+        const float4 ox = make_float4(fmaf(ah, half_of(VX[rp][0], h), bh * u.x), fmaf(ah, half_of(VX[rp][1], h), bh * u.y),
+                                      fmaf(ah, half_of(VX[rp][2], h), bh * u.z), fmaf(ah, half_of(VX[rp][3], h), bh * u.w));
+        const float4 oy = make_float4(fmaf(ah, half_of(VY[rp][0], h), bh * w.x), fmaf(ah, half_of(VY[rp][1], h), bh * w.y),
+                                      fmaf(ah, half_of(VY[rp][2], h), bh * w.z), fmaf(ah, half_of(VY[rp][3], h), bh * w.w));
         const size_t o = (size_t)i * im.pitch + jb;
         if (jb >= ex0 && jb + CW <= ex1) {
             St::st4(nx + o, ox, rkey(pseed, o, 0));
