@@ -49,7 +49,8 @@ struct Schwarz2State {
     double alpha_hat;
     int hmax, wmax, wpad;   // largest subdomain extent, padded shared-memory row of the cluster kernel
     int qp;                 // row pitch of q; a subdomain's row starts at column start & ~3
-    int small, tx, ty;      // whole subdomain in one CTA of tx x ty threads (4 x 4 pixels each)
+    int small, tx, ty;      // 1: whole subdomain in one CTA of tx x ty threads (4 x 4 pixels each);
+                            // 2: a cluster of ncl such CTAs, band = 4 ty rows each; 0: band kernel
     int ncl, band;          // otherwise: CTAs per subdomain (cluster size) and rows per CTA
     size_t smem;            // dynamic shared memory per CTA
     int stor;               // tvs_storage of p and q

@@ -301,6 +301,12 @@ __host__ __device__ __forceinline__ size_t small_tile_smem_bytes(int tx, int ty)
 
 __device__ __forceinline__ float& half_of(float2& v, int h) { return h ? v.y : v.x; }
 
+template <bool CL>
+__device__ __forceinline__ void block_or_cluster_sync() {
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
 // One pointwise update of Algorithm 3 on the thread's pixels, given z on
 // them, on the column to their right (zr) and the row below (zd):
 // psi = grad z (D^+), v <- (v + t psi) / (1 + (t / theta) |psi|).
@@ -336,7 +342,11 @@ __device__ __forceinline__ void small_tile_update(float2 (&VX)[RP][CW], float2 (
         }
 }
 
-template <class S, int MAXT, int MINB, bool MULTI>
+// CL: a cluster of CTAs per subdomain (single image), each CTA a band of
+// RH * TY rows; the CTAs exchange the halo rows (v_y of the row above, z of
+// the row below) through distributed shared memory, with a cluster barrier
+// in place of the CTA barrier.
+template <class S, int MAXT, int MINB, bool MULTI, bool CL>
 __global__ void __launch_bounds__(MAXT, MINB)
 schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     using St = Stor<S>;
@@ -357,14 +367,22 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     float* sthx = ezy + TY * CW * TX;             // theta_x of columns xa - 1 .. xa + 4 TX - 1
     float* sthy = sthx + CW * TX + 1;             // theta_y of rows y0 - 1 .. y0 + 4 TY - 1
 
+    static_assert(!(CL && MULTI), "cluster mode runs one image");
     const TileImg& im = tile_image<MULTI>(a);
     const int N2 = im.ay.N, N1 = im.ax.N;
-    const int sub = blockIdx.x - im.first;
+    int sub = blockIdx.x - im.first, rank = 0, ncl = 1;
+    if (CL) {
+        const cg::cluster_group cl = cg::this_cluster();
+        rank = (int)cl.block_rank();
+        ncl = (int)cl.num_blocks();
+        sub = blockIdx.x / ncl;
+    }
     const int my = sub / im.ax.M, mx = sub - my * im.ax.M;
     const int y0 = im.ay.start(my), y1 = im.ay.end(my);
     const int x0 = im.ax.start(mx), x1 = im.ax.end(mx);
     const int xa = x0 & ~3;
-    const int ib = y0 + ty * RH, jb = xa + tx * CW;
+    const int yb = y0 + rank * RH * TY;           // first row of this CTA
+    const int ib = yb + ty * RH, jb = xa + tx * CW;
     const int zy1 = min(y1 + 1, N2), zx1 = min(x1 + 1, N1);   // z region: [y0, zy1) x [x0, zx1)
     const float t = a.t;
     {
@@ -374,7 +392,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
             sthx[c] = (j >= x0 && j < x1) ? im.ax.theta(mx, j) : 0.0f;
         }
         for (int r = tid; r <= RH * TY; r += nt) {
-            const int i = y0 - 1 + r;
+            const int i = yb - 1 + r;
             sthy[r] = (i >= y0 && i < y1) ? im.ay.theta(my, i) : 0.0f;
         }
     }
@@ -503,7 +521,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     }
     // Blocks that reach the image's last column or row apply the D^+ boundary
     // rule (psi_x = 0 in the last column, psi_y = 0 in the last row).
-    const bool edge = xa + CW * TX >= N1 || y0 + RH * TY >= N2;
+    const bool edge = xa + CW * TX >= N1 || yb + RH * TY >= N2;
     float2* evx2 = reinterpret_cast<float2*>(evx);   // v_x of the last column, [RP][TY][TX]
     float4* evy4 = reinterpret_cast<float4*>(evy);   // v_y of the last row, [TY][TX]
     float2* ezx2 = reinterpret_cast<float2*>(ezx);   // z of the first column, [RP][TY][TX]
@@ -514,13 +532,15 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
 #pragma unroll
         for (int rp = 0; rp < RP; ++rp) evx2[rp * TY * TX + me] = VX[rp][CW - 1];
         evy4[me] = make_float4(VY[RP - 1][0].y, VY[RP - 1][1].y, VY[RP - 1][2].y, VY[RP - 1][3].y);
-        __syncthreads();
+        block_or_cluster_sync<CL>();
         float2 Z[RP][CW];
         {
             float2 vxl[RP];
 #pragma unroll
             for (int rp = 0; rp < RP; ++rp) vxl[rp] = tx > 0 ? evx2[rp * TY * TX + me - 1] : make_float2(0.f, 0.f);
-            const float4 u4 = ty > 0 ? evy4[me - TX] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ty > 0) u4 = evy4[me - TX];
+            else if (CL && rank > 0) u4 = *cg::this_cluster().map_shared_rank(evy4 + (TY - 1) * TX + tx, rank - 1);
             const float vyu[CW] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
             for (int rp = 0; rp < RP; ++rp)
@@ -543,15 +563,19 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
 #pragma unroll
         for (int rp = 0; rp < RP; ++rp) ezx2[rp * TY * TX + me] = Z[rp][0];
         ezy4[me] = make_float4(Z[0][0].x, Z[0][1].x, Z[0][2].x, Z[0][3].x);
-        __syncthreads();
+        block_or_cluster_sync<CL>();
         float2 zr[RP];
 #pragma unroll
         for (int rp = 0; rp < RP; ++rp) zr[rp] = tx + 1 < TX ? ezx2[rp * TY * TX + me + 1] : make_float2(0.f, 0.f);
-        const float4 d4 = ty + 1 < TY ? ezy4[me + TX] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ty + 1 < TY) d4 = ezy4[me + TX];
+        else if (CL && rank + 1 < ncl) d4 = *cg::this_cluster().map_shared_rank(ezy4 + tx, rank + 1);
         const float zd[CW] = {d4.x, d4.y, d4.z, d4.w};
         if (edge) small_tile_update<true, RP, CW>(VX, VY, Z, zr, zd, cs + me, TY * TX, t, jb, ib, N1, N2);
         else small_tile_update<false, RP, CW>(VX, VY, Z, zr, zd, cs + me, TY * TX, t, jb, ib, N1, N2);
     }
+
+    if (CL) cg::this_cluster().sync();   // no CTA leaves while a neighbour could still read its shared memory
 
     // ---- new warm start q_m; p^{n+1} on the exclusive core -----------------
 #pragma unroll
@@ -639,52 +663,121 @@ struct QNeighbours {
 };
 
 // p^{n+1} on the overlap strips of every core (the frame between the core
-// and its exclusive part), after the small-tile kernel wrote the rest.
+// and its exclusive part), after the small-tile kernel wrote the rest.  The
+// frames of all cores are the overlap bands around the core boundaries; the
+// CTAs (sub, c) of subdomain (my, mx) take chunk c of the horizontal band on
+// its upper core boundary (rows [cy0 - ceil(s/2), cy0 + floor(s/2)), the
+// core's columns) and of the vertical band on its left boundary (columns
+// [cx0 - ceil(s/2), cx0 + floor(s/2)), the exclusive rows of the core).  A
+// band pixel lies in Gamma_l of the 2 (4 in a corner) subdomains l around
+// it; their extents come from shared memory, computed once per CTA.
+constexpr int kStripThreads = 128;
+
+// p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum_l q_l on up to NB pixels of
+// one column (rows i, i + di, ...): every load is issued before the first
+// store, so a thread keeps NB pixels' loads in flight.
+template <class S>
+struct StripCombine {
+    static constexpr int NB = 4;
+    const S* __restrict__ pin;
+    S* __restrict__ pout;
+    const S* __restrict__ q;
+    int pitch;
+    long plane;
+    size_t qplane;
+    int hmax, qp, M1, my, mx;
+    float ah;
+    uint32_t pseed;
+    __device__ __forceinline__ void run(const int (&nby)[3][2], const int (&nbx)[3][3], int i, int di, int n,
+                                        int j) const {
+        using St = Stor<S>;
+        float sx[NB], sy[NB], ux[NB], uy[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            sx[b] = sy[b] = ux[b] = uy[b] = 0.0f;
+            if (b >= n) continue;
+            const int ii = i + b * di;
+            const size_t o = (size_t)ii * pitch + j;
+            ux[b] = St::ld1(pin + o);
+            uy[b] = St::ld1(pin + plane + o);
+#pragma unroll
+            for (int da = 0; da < 3; ++da) {
+                if (ii < nby[da][0] || ii >= nby[da][1]) continue;
+#pragma unroll
+                for (int db = 0; db < 3; ++db) {
+                    if (j < nbx[db][0] || j >= nbx[db][2]) continue;
+                    const int l = (my - 1 + da) * M1 + (mx - 1 + db);
+                    const size_t off = ((size_t)l * 2 * hmax + (ii - nby[da][0])) * qp + (j - nbx[db][1]);
+                    sx[b] += St::ld1(q + off);
+                    sy[b] += St::ld1(q + off + qplane);
+                }
+            }
+        }
+        const float bh = 1.0f - ah;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (b >= n) continue;
+            const size_t o = (size_t)(i + b * di) * pitch + j;
+            St::st1(pout + o, fmaf(bh, ux[b], ah * sx[b]), rkey(pseed, o, 0));
+            St::st1(pout + plane + o, fmaf(bh, uy[b], ah * sy[b]), rkey(pseed, o, 1));
+        }
+    }
+};
 template <class S, bool MULTI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kStripThreads, 8)
 schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     using St = Stor<S>;
+    __shared__ int nbx[3][3], nby[3][2];   // columns: start, start & ~3, end; rows: start, end (mx-1..mx+1, my-1..my+1)
     const TileImg& im = tile_image<MULTI>(a);
     const S* __restrict__ pin = static_cast<const S*>(im.p);
     S* __restrict__ pout = static_cast<S*>(im.pnext);
     const S* __restrict__ q = static_cast<const S*>(im.q);
     const int pitch = im.pitch, hmax = im.hmax, qp = im.qp;
     const long plane = im.plane;
-    const Axis ay = im.ay, ax = im.ax;
-    const float ah = im.ahat;
-    const uint32_t seed = a.seed;
+    const Axis& ay = im.ay;
+    const Axis& ax = im.ax;
     const int sub = blockIdx.x - im.first;
     const int my = sub / ax.M, mx = sub - my * ax.M;
-    const int cy0 = ay.core(my), cy1 = my == ay.M - 1 ? ay.L : ay.core(my + 1);
-    const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
-    const int ey0 = excl_lo(ay, my), ey1 = excl_hi(ay, my);
-    const int ex0 = excl_lo(ax, mx), ex1 = excl_hi(ax, mx);
-    const int W = cx1 - cx0;
-    const int top = (ey0 - cy0) * W, bot = (cy1 - ey1) * W;
-    const int midh = ey1 - ey0, lw = ex0 - cx0, rw = cx1 - ex1;
-    const int total = top + bot + midh * (lw + rw);
-    QNeighbours nb;
-    nb.init(ay, ax, my, mx);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int i, j;
-        if (e < top) {
-            i = cy0 + e / W;
-            j = cx0 + e % W;
-        } else if (e < top + bot) {
-            const int f = e - top;
-            i = ey1 + f / W;
-            j = cx0 + f % W;
+    const int t = threadIdx.x;
+    if (t < 6) {   // one extent per thread
+        const int d = t % 3, b = (t < 3 ? mx : my) - 1 + d;
+        const Axis& A = t < 3 ? ax : ay;
+        const int M = A.M;
+        const int st = (b >= 0 && b < M) ? A.start(b) : 0, en = (b >= 0 && b < M) ? A.end(b) : 0;
+        if (t < 3) {
+            nbx[d][0] = st;
+            nbx[d][1] = st & ~3;
+            nbx[d][2] = en;
         } else {
-            const int f = e - top - bot, w = lw + rw;
-            i = ey0 + f / w;
-            const int c = f % w;
-            j = c < lw ? cx0 + c : ex1 + (c - lw);
+            nby[d][0] = st;
+            nby[d][1] = en;
         }
-        const float2 sq = nb.sum(q, hmax, qp, ax.M, my, mx, i, j);
-        const size_t o = (size_t)i * pitch + j;
-        const uint32_t pseed = seed ^ 0xa511e9b3U;
-        St::st1(pout + o, (1.0f - ah) * St::ld1(pin + o) + ah * sq.x, rkey(pseed, o, 0));
-        St::st1(pout + plane + o, (1.0f - ah) * St::ld1(pin + plane + o) + ah * sq.y, rkey(pseed, o, 1));
+    }
+    __syncthreads();
+    StripCombine<S> cb{pin, pout, q, pitch, plane, (size_t)hmax * qp, hmax, qp, ax.M, my, mx, im.ahat,
+                       a.seed ^ 0xa511e9b3U};
+    const int nch = gridDim.y, ch = blockIdx.y;
+    const int cy0 = ay.core(my);
+    const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
+    // horizontal band: s rows x this chunk's share of the core's columns;
+    // a thread takes one column and up to 4 rows at a time
+    if (my > 0 && ay.s > 0) {
+        const int W = cx1 - cx0;
+        const int j0 = cx0 + (int)((long long)W * ch / nch), j1 = cx0 + (int)((long long)W * (ch + 1) / nch);
+        const int i0 = cy0 - (ay.s + 1) / 2;
+        for (int j = j0 + t; j < j1; j += kStripThreads)
+            for (int r = 0; r < ay.s; r += StripCombine<S>::NB) cb.run(nby, nbx, i0 + r, 1, ay.s - r, j);
+    }
+    // vertical band: this chunk's share of the exclusive rows x s columns;
+    // a thread takes one column and up to 4 rows (rstep apart) at a time
+    if (mx > 0 && ax.s > 0 && t < (kStripThreads / ax.s) * ax.s) {
+        const int ey0 = excl_lo(ay, my), ey1 = excl_hi(ay, my);
+        const int H = max(ey1 - ey0, 0);
+        const int r0 = ey0 + (int)((long long)H * ch / nch), r1 = ey0 + (int)((long long)H * (ch + 1) / nch);
+        const int rstep = kStripThreads / ax.s;
+        const int j = cx0 - (ax.s + 1) / 2 + t % ax.s;
+        for (int i = r0 + t / ax.s; i < r1; i += StripCombine<S>::NB * rstep)
+            cb.run(nby, nbx, i, rstep, (r1 - i + rstep - 1) / rstep, j);
     }
 }
 
@@ -733,13 +826,34 @@ int small_tile_shape(int hmax, int wmax, int* tx, int* ty, int* qp, size_t* smem
     return *tx * *ty <= kSmallMaxThreads ? 1 : 0;
 }
 
+int small_cluster_shape(int hmax, int wmax, int* tx, int* ty, int* ncl, int* qp, size_t* smem) {
+    // a band of 4 ty rows of Gamma_m (plus the row below) per CTA, full width;
+    // two CTAs per SM if the cluster stays within 16 CTAs, else one
+    *tx = (wmax + 3 + 1 + kSmallCW - 1) / kSmallCW;
+    *qp = *tx * kSmallCW;
+    for (int cap : {kSmallPairThreads, kSmallMaxThreads}) {
+        if (*tx > cap) continue;
+        *ty = cap / *tx;
+        const int rows = hmax + 1;
+        *ncl = (rows + kSmallRH * *ty - 1) / (kSmallRH * *ty);
+        if (*ncl < 2) continue;
+        if (*ncl <= 16) {
+            // the same number of CTAs with the fewest rows each
+            *ty = (rows + kSmallRH * *ncl - 1) / (kSmallRH * *ncl);
+            *smem = small_tile_smem_bytes(*tx, *ty);
+            return 1;
+        }
+    }
+    return 0;
+}
+
 template <class S, bool MULTI>
 static void small_tile_attrs() {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI>,
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
-        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI>,
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
 }
@@ -749,10 +863,42 @@ static cudaError_t launch_small_tiles(const SmallTileArgs<S>& a, int nsub, int t
     small_tile_attrs<S, MULTI>();
     const size_t smem = small_tile_smem_bytes(tx, ty);
     if (tx * ty <= kSmallPairThreads)
-        schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI><<<nsub, dim3(tx, ty), smem, s>>>(a);
+        schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI, false><<<nsub, dim3(tx, ty), smem, s>>>(a);
     else
-        schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI><<<nsub, dim3(tx, ty), smem, s>>>(a);
+        schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI, false><<<nsub, dim3(tx, ty), smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Clusters of ncl CTAs of tx x ty threads per subdomain (one image).
+template <class S>
+static cudaError_t launch_small_clusters(const SmallTileArgs<S>& a, int nsub, int tx, int ty, int ncl,
+                                         cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, false, true>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, false, true>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    });
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsub * ncl, 1, 1);
+    cfg.blockDim = dim3(tx, ty, 1);
+    cfg.dynamicSmemBytes = small_tile_smem_bytes(tx, ty);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (tx * ty <= kSmallPairThreads)
+        return cudaLaunchKernelEx(&cfg, schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, false, true>, a);
+    return cudaLaunchKernelEx(&cfg, schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, false, true>, a);
 }
 
 template <class S>
@@ -773,7 +919,7 @@ static cudaError_t schwarz2_iterate_multi_t(const TileImg* imgs, int nimg, int n
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(kProfSchwarzCombine, s);
-            schwarz2_strip_kernel<S, true><<<nsub, 128, 0, s>>>(a);
+            schwarz2_strip_kernel<S, true><<<nsub, kStripThreads, 0, s>>>(a);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -821,11 +967,12 @@ void schwarz2_carve(Carver& cv, int n2, int n1, const tvs_decomp& dd, int pitch,
     for (int k = 0; k < dd.m1; ++k) st.wmax = std::max(st.wmax, ax.end(k) - ax.start(k));
     st.wpad = round_up(st.wmax + 1, 4);
     st.small = small_tile_shape(st.hmax, st.wmax, &st.tx, &st.ty, &st.qp, &st.smem);
+    st.ncl = 1;
+    if (!st.small && small_cluster_shape(st.hmax, st.wmax, &st.tx, &st.ty, &st.ncl, &st.qp, &st.smem)) st.small = 2;
     if (!st.small) st.qp = round_up(st.wmax + 3, 4);
     const size_t qbytes = (size_t)dd.m2 * dd.m1 * 2 * st.hmax * st.qp * storage_bytes(storage);
     if (st.small) {
-        st.ncl = 1;
-        st.band = st.hmax;
+        st.band = st.ty * kSmallRH;
         st.q = cv.take<char>(qbytes);
         return;
     }
@@ -887,6 +1034,9 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
     const int nsub = st.m2 * st.m1;
     const int hcore = (n2 + st.m2 - 1) / st.m2 + 1;
     const int chunks = std::max(1, std::min(64, hcore / 16));
+    // overlap-band pixels per subdomain, about s (core height + core width); ~512 per strip CTA
+    const int wcore = (n1 + st.m1 - 1) / st.m1 + 1;
+    const int strip_chunks = std::max(1, std::min(64, st.s * (hcore + wcore) / 512));
     const float ah = (float)st.alpha_hat;
     S* q = static_cast<S*>(st.q);
     for (int n = 0; n < n_outer; ++n) {
@@ -902,7 +1052,8 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
                 a.k = st.k;
                 a.t = t;
                 a.seed = seed;
-                e = launch_small_tiles<S, false>(a, nsub, st.tx, st.ty, s);
+                e = st.small == 2 ? launch_small_clusters<S>(a, nsub, st.tx, st.ty, st.ncl, s)
+                                  : launch_small_tiles<S, false>(a, nsub, st.tx, st.ty, s);
             }
             if (e != cudaSuccess) return e;
             if (st.s > 0 && nsub > 1) {
@@ -911,7 +1062,7 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
                 a.one = TileImg{*cur, *nxt, f2, q, pitch, plane, st.hmax, st.qp, ay, ax, ah, 0};
                 a.nimg = 1;
                 a.seed = seed;
-                schwarz2_strip_kernel<S, false><<<nsub, 128, 0, s>>>(a);
+                schwarz2_strip_kernel<S, false><<<dim3(nsub, strip_chunks), kStripThreads, 0, s>>>(a);
             }
         } else {
             {

@@ -251,17 +251,24 @@ def test_schwarz2_single_subdomain_equals_global(B):
     assert torch.abs(g.out - s.out).max().item() <= 1e-6
 
 
-def test_schwarz2_large_subdomains_use_clusters(B):
-    # 1024 x 1024 with 4 x 4 subdomains of ~264^2: each subdomain spans a
-    # cluster of CTAs; compare with the oracle after a few outer iterations.
-    n = 1024
-    d0 = image(n, n, 13, texture=True)
+@pytest.mark.parametrize("n2,n1,m2,m1,s,k,outer", [
+    # ~264^2 subdomains: clusters of 14 CTAs of 67 x 5 threads, two CTAs per SM
+    (1024, 1024, 4, 4, 8, 4, 3),
+    # 250 x 392 subdomains: clusters of 13 CTAs of 99 x 5 threads, one CTA per SM
+    (250, 780, 1, 2, 4, 5, 4),
+    # 1200 x 102 subdomains: taller than 16 such CTAs -> the shared-memory band kernel
+    (1200, 200, 1, 2, 4, 3, 3),
+])
+def test_schwarz2_large_subdomains_use_clusters(B, n2, n1, m2, m1, s, k, outer):
+    # subdomains too large for one CTA span a cluster of CTAs; compare with
+    # the oracle after a few outer iterations
+    d0 = image(n2, n1, 13, texture=True)
     tau = otvs.tfs(d0, 0.05, 0.125, 5)[0].astype(np.float32).astype(np.float64)
-    f2 = otvs.irv1_data(d0.astype(np.float32).astype(np.float64), otvs.normal_field(tau, n, n, 1e-3), 10.0)
-    dd = osch.Decomp(n, n, 4, 4, 8, False)
-    d_o, p_o, _ = osch.schwarz_irv1(f2, 10.0, dd, 0.125, 3, 4)
-    p = torch.zeros((2, n, n), dtype=torch.float32, device="cuda")
-    res = B.tvs_schwarz(2, cuda(d0), cuda(tau), 10.0, 1e-3, B.make_decomp(4, 4, 8, 4), B.make_iter(3), p=p)
+    f2 = otvs.irv1_data(d0.astype(np.float32).astype(np.float64), otvs.normal_field(tau, n2, n1, 1e-3), 10.0)
+    dd = osch.Decomp(n2, n1, m2, m1, s, False)
+    d_o, p_o, _ = osch.schwarz_irv1(f2, 10.0, dd, 0.125, outer, k)
+    p = torch.zeros((2, n2, n1), dtype=torch.float32, device="cuda")
+    res = B.tvs_schwarz(2, cuda(d0), cuda(tau), 10.0, 1e-3, B.make_decomp(m2, m1, s, k), B.make_iter(outer), p=p)
     assert np.abs(host(p) - p_o).max() <= TOL
     assert np.abs(host(res.out) - d_o).max() <= TOL
 
