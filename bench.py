@@ -61,6 +61,7 @@ def parse():
                     help="step-2 dual storage for --case: 0 f32, 1 bf16, 2 f16, 3 16-bit fixed point")
     ap.add_argument("--tile", type=int, default=256, help="Schwarz core size for --case schwarz2")
     ap.add_argument("--overlap", type=int, default=-1, help="Schwarz overlap for --case schwarz2 (default: 8, or 4)")
+    ap.add_argument("--k", type=int, default=-1, help="Schwarz inner updates for --case schwarz2 (default: 10)")
     return ap.parse_args()
 
 
@@ -345,6 +346,11 @@ def run_gpu(args):
         ms3, r3 = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(5000, T, 1e-4, 2), out=d))
         gap["step2_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms3 / mpx, "outer_iters": r3.report["iters"],
                                             "rel_gap": r3.report["rel_gap"]}
+        # step 1 under Schwarz (Algorithm 2 with the localized Algorithm 5)
+        tau_s = torch.empty_like(tau)
+        ms4, r4 = timed(lambda: B.tvs_schwarz(1, d0, None, DELTA, EPS, dd, B.make_iter(400, T, 1e-4, 2), out=tau_s))
+        gap["step1_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms4 / mpx, "outer_iters": r4.report["iters"],
+                                            "rel_gap": r4.report["rel_gap"]}
 
     large = None
     if rank == 0 and args.large_n > 0:
@@ -474,7 +480,7 @@ def run_large(args, B, dev, torch):
     del ws2
     torch.cuda.empty_cache()
     m = n // 64
-    for k in (1, 4, 16):
+    for k in (1, 4, 16, 32):
         dd = B.make_decomp(m, m, 4, k)
         wss = B.workspace(2, n, n, dd, device=dev)
         B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(2, T), out=d, ws=wss)
@@ -500,6 +506,16 @@ def run_large(args, B, dev, torch):
                                                          "rel_gap": r_s.report["rel_gap"]}
         del wss
         torch.cuda.empty_cache()
+    # reduced-precision dual under Schwarz: 16-bit fixed point, k = 16
+    dd = B.make_decomp(m, m, 4, 16)
+    wss = B.workspace(2, n, n, dd, device=dev, storage=3)
+    ms_s, r_s = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(100000, T, 1e-4, 2, storage=3),
+                                            out=d, ws=wss))
+    out["step2_to_gap"]["schwarz_64x64_s4_k16_s16"] = {"ms_per_mpixel": ms_s / mpx,
+                                                       "outer_iters": r_s.report["iters"],
+                                                       "rel_gap": r_s.report["rel_gap"]}
+    del wss
+    torch.cuda.empty_cache()
     return out
 
 
@@ -710,7 +726,7 @@ def run_case(args):
     tau = torch.zeros((2, n + 1, n + 1), dtype=torch.float32, device="cuda")
     m = max(1, n // args.tile)
     ov = args.overlap if args.overlap >= 0 else (OVERLAP if n // m >= 2 * OVERLAP else 4)
-    dd = B.make_decomp(m, m, ov, K_INNER)
+    dd = B.make_decomp(m, m, ov, args.k if args.k > 0 else K_INNER)
     it = B.make_iter(args.iters, T)
     it2 = B.make_iter(args.iters, T, storage=args.storage)
     t0 = time.perf_counter()

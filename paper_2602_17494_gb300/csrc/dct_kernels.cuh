@@ -450,6 +450,8 @@ __global__ void __launch_bounds__(kDctThreads)
 dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
                     RowSrcArgs sa, int G, const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
+    pdl_wait();
+    pdl_trigger();
     const int L = cols, M = pl.M, stride = padded_len(M);
     float2* buf = sm;
     float2* peel = sm + (size_t)G * stride;
@@ -495,6 +497,8 @@ __global__ void __launch_bounds__(kDctThreads)
 dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl, int G,
                     const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
+    pdl_wait();
+    pdl_trigger();
     const int L = cols, M = pl.M, stride = padded_len(M);
     float2* buf = sm;
     float2* peel = sm + (size_t)G * stride;
@@ -549,6 +553,8 @@ __global__ void __launch_bounds__(kDctThreads)
 dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
                       int G, const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
+    pdl_wait();
+    pdl_trigger();
     const int2 rr = batch_rows(ba, rows);       // rows outside rr are read as zero and not written
     S += (size_t)blockIdx.y * ba.bstride;
     const int L = rows, M = pl.M, stride = padded_len(M);
@@ -663,12 +669,12 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
     const dim3 grid((maxrows + 1) / 2, nbatch);
     const int nt = fft_threads(pl.M);
     if (src == RowSource::Plain)
-        dct_rows_fwd_kernel<RowSource::Plain, LM><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pl, sa, 1, ba);
-    else if (src == RowSource::DivField)
-        dct_rows_fwd_kernel<RowSource::DivField, LM><<<grid, nt, smem, s>>>(S, rows, cols, pitch, pl, sa, 1, ba);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return launch_pdl(dct_rows_fwd_kernel<RowSource::Plain, LM>, grid, dim3(nt), smem, s, S, rows, cols, pitch, pl,
+                          sa, 1, ba);
+    if (src == RowSource::DivField)
+        return launch_pdl(dct_rows_fwd_kernel<RowSource::DivField, LM>, grid, dim3(nt), smem, s, S, rows, cols, pitch,
+                          pl, sa, 1, ba);
+    return cudaErrorInvalidValue;
 }
 
 template <int LM>
@@ -678,8 +684,8 @@ cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPla
     const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
     std::call_once(once, [smem] { allow_dct_smem(dct_cols_solve_kernel<LM>, smem); });
     const dim3 grid((cols + 1) / 2, nbatch);
-    dct_cols_solve_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
-    return cudaGetLastError();
+    return launch_pdl(dct_cols_solve_kernel<LM>, grid, dim3(fft_threads(pl.M)), smem, s, S, rows, cols, pitch, pl, 1,
+                      ba);
 }
 
 template <int LM>
@@ -689,8 +695,8 @@ cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const Dc
     const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
     std::call_once(once, [smem] { allow_dct_smem(dct_rows_inv_kernel<LM>, smem); });
     const dim3 grid((maxrows + 1) / 2, nbatch);
-    dct_rows_inv_kernel<LM><<<grid, fft_threads(pl.M), smem, s>>>(S, rows, cols, pitch, pl, 1, ba);
-    return cudaGetLastError();
+    return launch_pdl(dct_rows_inv_kernel<LM>, grid, dim3(fft_threads(pl.M)), smem, s, S, rows, cols, pitch, pl, 1,
+                      ba);
 }
 
 #define TVS_DCT_INSTANTIATE(LM)                                                                                   \

@@ -132,6 +132,8 @@ constexpr size_t kDivSmem = (size_t)4 * kBoxFloats * 4 + (size_t)2 * (kTY + 1) *
 __global__ void __launch_bounds__(kTX * kBY)
 div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pitch, float* __restrict__ S,
                   unsigned* __restrict__ err) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
     constexpr int WH = kTY + 1, WW = kTX + 1;      // w region: rows i0-1.., cols j0-1..
@@ -185,8 +187,7 @@ cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plan
     if (!tile_maps(p, nullptr, nullptr, R, C, pitch, plane, &mp, &unused, &unused)) return cudaErrorInvalidValue;
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     ProfScope ps(kProfOther, s);
-    div_vecdiv_kernel<<<grd, blk, kDivSmem, s>>>(mp, R, C, pitch, S, err);
-    return cudaGetLastError();
+    return launch_pdl(div_vecdiv_kernel, grd, blk, kDivSmem, s, mp, R, C, pitch, S, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,6 +230,8 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
                   const __grid_constant__ CUtensorMap fmap, float* __restrict__ pout, int R, int C, int pitch,
                   long plane, float t, float delta, float* __restrict__ tau_out, int tau_pitch, long tau_plane,
                   double* __restrict__ partial, unsigned* __restrict__ err) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
     float* sphi = sp + 4 * kBoxFloats;             // [BH][BW]
@@ -341,6 +344,7 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     const bool wt = tau_out != nullptr;
     ProfScope ps((check || !write_p) ? kProfTfsCheck : kProfTfsUpdate, s);
+    cudaError_t e = cudaSuccess;
 #define TVS_TFS(CK, WP, WT)                                                                                   \
     do {                                                                                                      \
         static std::once_flag once;                                                                          \
@@ -348,8 +352,8 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
             cudaFuncSetAttribute(tfs_update_kernel<CK, WP, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                  (int)kUpdSmem);                                                             \
         });                                                                                                   \
-        tfs_update_kernel<CK, WP, WT><<<grd, blk, kUpdSmem, s>>>(mp, mphi, mf, pout, R, C, pitch, plane, t,    \
-                                                                 delta, tau_out, tau_pitch, tau_plane, partial, err); \
+        e = launch_pdl(tfs_update_kernel<CK, WP, WT>, grd, blk, kUpdSmem, s, mp, mphi, mf, pout, R, C, pitch,   \
+                       plane, t, delta, tau_out, tau_pitch, tau_plane, partial, err);                        \
     } while (0)
     if (!check && write_p && !wt) TVS_TFS(false, true, false);
     else if (check && write_p && !wt) TVS_TFS(true, true, false);
@@ -358,7 +362,7 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
     else if (!check && !write_p && wt) TVS_TFS(false, false, true);
     else TVS_TFS(true, true, true);
 #undef TVS_TFS
-    return cudaGetLastError();
+    return e;
 }
 
 // ---------------------------------------------------------------------------
