@@ -116,6 +116,8 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
                    const S* __restrict__ pin, S* __restrict__ pout, int R, int C, int pitch, long plane, float t,
                    float alpha_inv, float* __restrict__ d_out, int d_pitch, double* __restrict__ partial,
                    uint32_t seed, unsigned* __restrict__ err) {
+    pdl_wait();
+    pdl_trigger();
     using G = StreamGeom<S>;
     using St = Stor<S>;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -377,6 +379,7 @@ static cudaError_t launch_irv1_t(const S* pin, S* pout, const float* f2, int R, 
     const size_t smem = stream_smem_bytes<S>();
     const float ainv = 1.0f / alpha;
     const bool wd = d_out != nullptr;
+    cudaError_t e = cudaSuccess;
 #define TVS_IRV1(CK, WP, WD)                                                                                   \
     do {                                                                                                       \
         static std::once_flag once;                                                                           \
@@ -384,8 +387,8 @@ static cudaError_t launch_irv1_t(const S* pin, S* pout, const float* f2, int R, 
             cudaFuncSetAttribute(irv1_stream_kernel<S, CK, WP, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)stream_smem_bytes<S>());                                               \
         });                                                                                                    \
-        irv1_stream_kernel<S, CK, WP, WD><<<grd, blk, smem, s>>>(pmap, fmap, pin, pout, R, C, pitch, plane, t,   \
-                                                                 ainv, d_out, d_pitch, partial, seed, err);    \
+        e = launch_pdl(irv1_stream_kernel<S, CK, WP, WD>, grd, blk, smem, s, pmap, fmap, pin, pout, R, C, pitch, \
+                       plane, t, ainv, d_out, d_pitch, partial, seed, err);                                   \
     } while (0)
     if (!check && write_p && !wd) TVS_IRV1(false, true, false);
     else if (check && write_p && !wd) TVS_IRV1(true, true, false);
@@ -394,7 +397,7 @@ static cudaError_t launch_irv1_t(const S* pin, S* pout, const float* f2, int R, 
     else if (!check && !write_p && wd) TVS_IRV1(false, false, true);
     else TVS_IRV1(true, true, true);
 #undef TVS_IRV1
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int R, int C, int pitch,

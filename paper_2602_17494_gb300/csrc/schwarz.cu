@@ -250,6 +250,27 @@ struct SmallTileArgs {
     uint32_t seed;
 };
 
+// Index of the image of this CTA in a multi-image launch: the largest first <= blockIdx.x.
+template <class S>
+__device__ __forceinline__ int tile_index(const SmallTileArgs<S>& a) {
+    int lo = 0, hi = a.nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.imgs[mid].first <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Axis::theta for part k given its extent [start, end): the ramps start at
+// start (k > 0) and end at end (k < M - 1), s pixels wide (no division of
+// the core positions).
+__device__ __forceinline__ float ramp_theta(const Axis& A, int k, int start, int end, int x) {
+    if (A.s > 0 && k > 0 && x < start + A.s) return ((float)(x - start) + 0.5f) / (float)A.s;
+    if (A.s > 0 && k < A.M - 1 && x >= end - A.s) return ((float)(end - x) - 0.5f) / (float)A.s;
+    return 1.0f;
+}
+
 template <bool MULTI, class S>
 __device__ __forceinline__ const TileImg& tile_image(const SmallTileArgs<S>& a) {
     if (!MULTI) return a.one;   // parameter space: no indirection
@@ -368,18 +389,39 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     float* sthy = sthx + CW * TX + 1;             // theta_y of rows y0 - 1 .. y0 + 4 TY - 1
 
     static_assert(!(CL && MULTI), "cluster mode runs one image");
-    const TileImg& im = tile_image<MULTI>(a);
-    const int N2 = im.ay.N, N1 = im.ax.N;
-    int sub = blockIdx.x - im.first, rank = 0, ncl = 1;
+    pdl_wait();
+    pdl_trigger();
+    int rank = 0, ncl = 1;
     if (CL) {
         const cg::cluster_group cl = cg::this_cluster();
         rank = (int)cl.block_rank();
         ncl = (int)cl.num_blocks();
-        sub = blockIdx.x / ncl;
     }
-    const int my = sub / im.ax.M, mx = sub - my * im.ax.M;
-    const int y0 = im.ay.start(my), y1 = im.ay.end(my);
-    const int x0 = im.ax.start(mx), x1 = im.ax.end(mx);
+    // the subdomain and its extents, once per CTA: [0] image, [1] sub, [2] my,
+    // [3] mx, [4] y0, [5] y1, [6] x0, [7] x1
+    __shared__ int hdr[8];
+    {
+        const int tid = ty * TX + tx;
+        if (tid < 4) {
+            const int img = MULTI ? tile_index(a) : 0;
+            const TileImg& I = MULTI ? a.imgs[img] : a.one;
+            const int sub = CL ? (int)blockIdx.x / ncl : (int)blockIdx.x - I.first;
+            const int my = sub / I.ax.M, mx = sub - my * I.ax.M;
+            const int v = tid == 0 ? I.ay.start(my) : tid == 1 ? I.ay.end(my) : tid == 2 ? I.ax.start(mx) : I.ax.end(mx);
+            hdr[4 + tid] = v;
+            if (tid == 0) {
+                hdr[0] = img;
+                hdr[1] = sub;
+                hdr[2] = my;
+                hdr[3] = mx;
+            }
+        }
+    }
+    __syncthreads();
+    const TileImg& im = MULTI ? a.imgs[hdr[0]] : a.one;
+    const int N2 = im.ay.N, N1 = im.ax.N;
+    const int sub = hdr[1], my = hdr[2], mx = hdr[3];
+    const int y0 = hdr[4], y1 = hdr[5], x0 = hdr[6], x1 = hdr[7];
     const int xa = x0 & ~3;
     const int yb = y0 + rank * RH * TY;           // first row of this CTA
     const int ib = yb + ty * RH, jb = xa + tx * CW;
@@ -389,11 +431,11 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         const int tid = ty * TX + tx, nt = TX * TY;
         for (int c = tid; c <= CW * TX; c += nt) {
             const int j = xa - 1 + c;
-            sthx[c] = (j >= x0 && j < x1) ? im.ax.theta(mx, j) : 0.0f;
+            sthx[c] = (j >= x0 && j < x1) ? ramp_theta(im.ax, mx, x0, x1, j) : 0.0f;
         }
         for (int r = tid; r <= RH * TY; r += nt) {
             const int i = yb - 1 + r;
-            sthy[r] = (i >= y0 && i < y1) ? im.ay.theta(my, i) : 0.0f;
+            sthy[r] = (i >= y0 && i < y1) ? ramp_theta(im.ay, my, y0, y1, i) : 0.0f;
         }
     }
     __syncthreads();
@@ -508,9 +550,9 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         const float inf = __int_as_float(0x7f800000);
         float rty[RH], rtx[CW];
 #pragma unroll
-        for (int r = 0; r < RH; ++r) rty[r] = thy[r] > 0.0f ? t / thy[r] : inf;
+        for (int r = 0; r < RH; ++r) rty[r] = thy[r] > 0.0f ? t * rcp_ftz(thy[r]) : inf;
 #pragma unroll
-        for (int c = 0; c < CW; ++c) rtx[c] = thx[c] > 0.0f ? 1.0f / thx[c] : inf;
+        for (int c = 0; c < CW; ++c) rtx[c] = thx[c] > 0.0f ? rcp_ftz(thx[c]) : inf;
 #pragma unroll
         for (int rp = 0; rp < RP; ++rp)
 #pragma unroll
@@ -593,8 +635,9 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
                                 half_of(VY[rp][3], h)),
                     rkey(a.seed, qi, 1));
         }
-    const int ey0 = excl_lo(im.ay, my), ey1 = excl_hi(im.ay, my);
-    const int ex0 = excl_lo(im.ax, mx), ex1 = excl_hi(im.ax, mx);
+    // the exclusive part of the core: [start + s, end - s) inside the image
+    const int ey0 = my == 0 ? 0 : y0 + im.ay.s, ey1 = my == im.ay.M - 1 ? im.ay.L : y1 - im.ay.s;
+    const int ex0 = mx == 0 ? 0 : x0 + im.ax.s, ex1 = mx == im.ax.M - 1 ? im.ax.L : x1 - im.ax.s;
     const float ah = im.ahat, bh = 1.0f - im.ahat;
     const uint32_t pseed = a.seed ^ 0xa511e9b3U;   // p^{n+1}: the same keys as the strip kernel's
     S* __restrict__ nx = static_cast<S*>(im.pnext);
@@ -726,6 +769,8 @@ struct StripCombine {
 template <class S, bool MULTI>
 __global__ void __launch_bounds__(kStripThreads, 8)
 schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
+    pdl_wait();
+    pdl_trigger();
     using St = Stor<S>;
     __shared__ int nbx[3][3], nby[3][2];   // columns: start, start & ~3, end; rows: start, end (mx-1..mx+1, my-1..my+1)
     const TileImg& im = tile_image<MULTI>(a);
@@ -863,10 +908,10 @@ static cudaError_t launch_small_tiles(const SmallTileArgs<S>& a, int nsub, int t
     small_tile_attrs<S, MULTI>();
     const size_t smem = small_tile_smem_bytes(tx, ty);
     if (tx * ty <= kSmallPairThreads)
-        schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI, false><<<nsub, dim3(tx, ty), smem, s>>>(a);
-    else
-        schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI, false><<<nsub, dim3(tx, ty), smem, s>>>(a);
-    return cudaGetLastError();
+        return launch_pdl(schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, MULTI, false>, dim3(nsub), dim3(tx, ty),
+                          smem, s, a);
+    return launch_pdl(schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, MULTI, false>, dim3(nsub), dim3(tx, ty), smem,
+                      s, a);
 }
 
 // Clusters of ncl CTAs of tx x ty threads per subdomain (one image).
@@ -889,13 +934,15 @@ static cudaError_t launch_small_clusters(const SmallTileArgs<S>& a, int nsub, in
     cfg.blockDim = dim3(tx, ty, 1);
     cfg.dynamicSmemBytes = small_tile_smem_bytes(tx, ty);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = ncl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     if (tx * ty <= kSmallPairThreads)
         return cudaLaunchKernelEx(&cfg, schwarz2_small_tile_kernel<S, kSmallPairThreads, 2, false, true>, a);
     return cudaLaunchKernelEx(&cfg, schwarz2_small_tile_kernel<S, kSmallMaxThreads, 1, false, true>, a);
@@ -919,9 +966,8 @@ static cudaError_t schwarz2_iterate_multi_t(const TileImg* imgs, int nimg, int n
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(kProfSchwarzCombine, s);
-            schwarz2_strip_kernel<S, true><<<nsub, kStripThreads, 0, s>>>(a);
+            e = launch_pdl(schwarz2_strip_kernel<S, true>, dim3(nsub), dim3(kStripThreads), 0, s, a);
         }
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1062,7 +1108,8 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
                 a.one = TileImg{*cur, *nxt, f2, q, pitch, plane, st.hmax, st.qp, ay, ax, ah, 0};
                 a.nimg = 1;
                 a.seed = seed;
-                schwarz2_strip_kernel<S, false><<<dim3(nsub, strip_chunks), kStripThreads, 0, s>>>(a);
+                e = launch_pdl(schwarz2_strip_kernel<S, false>, dim3(nsub, strip_chunks), dim3(kStripThreads), 0, s, a);
+                if (e != cudaSuccess) return e;
             }
         } else {
             {
