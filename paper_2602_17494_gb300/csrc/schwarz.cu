@@ -322,6 +322,11 @@ __host__ __device__ __forceinline__ size_t small_tile_smem_bytes(int tx, int ty)
 
 __device__ __forceinline__ float& half_of(float2& v, int h) { return h ? v.y : v.x; }
 
+// Hint: bring the 128-byte line holding p into L2 (no register is written).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <bool CL>
 __device__ __forceinline__ void block_or_cluster_sync() {
     if (CL) cg::this_cluster().sync();
@@ -427,6 +432,27 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     const int ib = yb + ty * RH, jb = xa + tx * CW;
     const int zy1 = min(y1 + 1, N2), zx1 = min(x1 + 1, N1);   // z region: [y0, zy1) x [x0, zx1)
     const float t = a.t;
+    // start moving this thread's rows of p^n, f2 and q_m towards L2 while the
+    // ramps are computed (the loads below then wait on L2, not on DRAM)
+    if (jb < N1) {
+        const S* px = static_cast<const S*>(im.p);
+        const S* qx = static_cast<const S*>(im.q) + (size_t)sub * 2 * im.hmax * im.qp;
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int i = ib + r;
+            if (i < zy1) {
+                const size_t o = (size_t)i * im.pitch + jb;
+                prefetch_l2(px + o);
+                prefetch_l2(px + im.plane + o);
+                prefetch_l2(im.f2 + o);
+            }
+            if (i < y1 && tx * CW < im.qp) {
+                const size_t qo = (size_t)(i - y0) * im.qp + tx * CW;
+                prefetch_l2(qx + qo);
+                prefetch_l2(qx + (size_t)im.hmax * im.qp + qo);
+            }
+        }
+    }
     {
         const int tid = ty * TX + tx, nt = TX * TY;
         for (int c = tid; c <= CW * TX; c += nt) {
