@@ -26,7 +26,11 @@
  *      tangent field tau       : 2 planes on ~Omega, order tau1, tau2
  *  - Scratch memory comes from the caller: `ws` is a device buffer of at
  *    least tvs_workspace_bytes(...) bytes, 256-byte aligned.  The calls do
- *    not allocate device memory.
+ *    not allocate device memory for data.  Runs of unchecked iterations of
+ *    tvs_step1, tvs_step2 (FP32 dual), tvs_schwarz (step 2, FP32 dual) and
+ *    tvs_denoise are replayed from a cache of at most 32 instantiated CUDA
+ *    graphs (driver-owned objects, keyed by every pointer and size they
+ *    use); tvs_set_graphs(0) turns this off.
  *  - All device work is enqueued on `stream`.  Calls that fill a tvs_report
  *    synchronize `stream` before returning.
  *  - Argument errors return TVS_ERR_ARG before any work is enqueued.  CUDA
@@ -193,6 +197,11 @@ typedef struct {
 } tvs_kernel_time;
 int tvs_profile_enable(int on);
 int tvs_profile_read(tvs_kernel_time* out, int cap);
+
+/* Graph replay of the iteration runs (see the conventions above): on (1, the
+ * default) or off (0).  Returns the previous setting.  While profiling is
+ * enabled every launch is made directly. */
+int tvs_set_graphs(int on);
 
 /* Quality of a reconstruction d against a ground truth gt (Section 5.3),
  * both n2 x n1 dense float with intensities in [0, 1] (largest value R = 1):

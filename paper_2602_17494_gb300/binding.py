@@ -82,6 +82,8 @@ def _load() -> ctypes.CDLL:
     lib.tvs_project_noalloc.argtypes = [P, P, I, I, P]
     lib.tvs_profile_enable.restype = I
     lib.tvs_profile_enable.argtypes = [I]
+    lib.tvs_set_graphs.restype = I
+    lib.tvs_set_graphs.argtypes = [I]
     lib.tvs_profile_read.restype = I
     lib.tvs_profile_read.argtypes = [ctypes.POINTER(TvsKernelTime), I]
     E = ctypes.POINTER(TvsEngineConfig)
@@ -121,7 +123,8 @@ _lib = _load()
 EXPORTED = ["tvs_denoise", "tvs_engine_create", "tvs_engine_destroy", "tvs_engine_pending",
             "tvs_engine_pool_overhead", "tvs_engine_request_bytes", "tvs_engine_step", "tvs_engine_submit",
             "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
-            "tvs_project_noalloc", "tvs_quality", "tvs_schwarz", "tvs_status_string", "tvs_step1", "tvs_step2",
+            "tvs_project_noalloc", "tvs_quality", "tvs_schwarz", "tvs_set_graphs", "tvs_status_string", "tvs_step1",
+            "tvs_step2",
             "tvs_tune_schwarz2", "tvs_tune_workspace_bytes", "tvs_version",
             "tvs_workspace_bytes"]
 
@@ -256,6 +259,11 @@ def tvs_schwarz(step: int, d0: torch.Tensor, tau: torch.Tensor | None, weight: f
                           _stream(d0.device), ctypes.byref(rep))
     _check(st, "tvs_schwarz")
     return Result(out, rep.as_dict(), st)
+
+
+def tvs_set_graphs(on: bool) -> bool:
+    """Turn graph replay of the iteration runs on or off; returns the previous setting."""
+    return bool(_lib.tvs_set_graphs(1 if on else 0))
 
 
 def tvs_profile_enable(on: bool = True) -> None:

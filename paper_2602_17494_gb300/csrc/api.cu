@@ -2,7 +2,9 @@
 // layout and the host-side iteration drivers.  All arithmetic of the method
 // runs in the kernels of dct.cu, tfs.cu, irv.cu and schwarz.cu.
 #include "drivers.h"
+#include "graphs.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -155,6 +157,34 @@ tvs_status tfs_setup(const Step1Layout& L, const float* d0, int n2, int n1, doub
     return TVS_OK;
 }
 
+// Runs of plain (unchecked) iterations between two convergence checks are
+// replayed as cached CUDA graphs (graphs.h), at most kGraphRun iterations per
+// graph and always an even number, so that p^n is back in the same buffer.
+constexpr int kGraphRun = 64;
+
+static int plain_run(bool check_loop, int n, const tvs_iter& it) {
+    const int stop = check_loop ? std::min(it.max_iter, (n / it.check_every + 1) * it.check_every) : it.max_iter;
+    return std::min(stop - n, kGraphRun) & ~1;
+}
+
+static void key_plan(GraphKey& k, const DctPlan& pl) {
+    k.add((uint64_t)pl.L).add((uint64_t)pl.M).ptr(pl.chirp).ptr(pl.rot).ptr(pl.post).ptr(pl.tw).ptr(pl.bhat).ptr(pl.sig2);
+}
+
+// `count` plain TFS iterations from cur on stream st (cur and nxt alternate).
+static cudaError_t tfs_iters(const Step1Layout& L, float* cur, float* nxt, int count, float t, float fd,
+                             cudaStream_t st) {
+    for (int i = 0; i < count; ++i) {
+        cudaError_t e = tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, st);
+        if (e != cudaSuccess) return e;
+        e = launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, false, true, nullptr, 0, 0,
+                              L.red.partial, L.red.err, st);
+        if (e != cudaSuccess) return e;
+        std::swap(cur, nxt);
+    }
+    return cudaSuccess;
+}
+
 static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1, double delta, const tvs_iter& it,
                           float* tau, int tau_pitch, long tau_plane, float* p_user, cudaStream_t s,
                           tvs_report* rep) {
@@ -172,6 +202,17 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
     double r[kRedSlots];
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
+        const int run = ck ? 0 : plain_run(check_loop, n, it);
+        if (run >= 4) {
+            GraphKey key;
+            key.add(1).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.S).ptr(L.f1).add((uint64_t)L.R).add((uint64_t)L.C)
+                .add((uint64_t)L.P).add((uint64_t)L.plane).num(t).num(fd).ptr(L.red.partial).ptr(L.red.err);
+            key_plan(key, L.pp.row);
+            key_plan(key, L.pp.col);
+            TVS_CUDA(graph_run(key, s, [&](cudaStream_t st) { return tfs_iters(L, cur, nxt, run, t, fd, st); }));
+            n += run;
+            continue;
+        }
         TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
         TVS_CUDA(launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
                                    L.red.partial, L.red.err, s));
@@ -220,6 +261,27 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
     tvs_status st;
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
+        // FP32 dual only: 16-bit stores draw their rounding bits from the
+        // iteration number, which a replayed graph would repeat
+        const int run = (ck || L.st != TVS_F32) ? 0 : plain_run(check_loop, n, it);
+        if (run >= 4) {
+            GraphKey key;
+            key.add(2).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.f2).add((uint64_t)L.R).add((uint64_t)L.C)
+                .add((uint64_t)L.P).add((uint64_t)L.plane).num(t).num(fa).ptr(L.red.partial).ptr(L.red.err);
+            TVS_CUDA(graph_run(key, s, [&](cudaStream_t st) {
+                void* a = cur;
+                void* b = nxt;
+                for (int i = 0; i < run; ++i) {
+                    const cudaError_t e = launch_irv1_update(a, b, L.f2, L.R, L.C, L.P, L.plane, t, fa, false, true,
+                                                             nullptr, 0, L.red.partial, L.st, 0u, L.red.err, st);
+                    if (e != cudaSuccess) return e;
+                    std::swap(a, b);
+                }
+                return cudaSuccess;
+            }));
+            n += run;
+            continue;
+        }
         TVS_CUDA(launch_irv1_update(cur, nxt, L.f2, L.R, L.C, L.P, L.plane, t, fa, ck, true, nullptr, 0,
                                     L.red.partial, L.st, (uint32_t)n + 1u, L.red.err, s));
         std::swap(cur, nxt);
@@ -265,7 +327,26 @@ tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1,
     tvs_status st;
     while (n < it.max_iter) {
         const int step = chunk < it.max_iter - n ? chunk : it.max_iter - n;
-        TVS_CUDA(schwarz2_iterate(&cur, &nxt, L.f2, L.P, L.plane, n2, n1, S2, t, step, (uint32_t)n, s));
+        if (S2.stor == TVS_F32 && step >= 2) {
+            // even runs of outer iterations as cached graphs (FP32 dual: the
+            // rounding seed of 16-bit stores would repeat in a replay)
+            const int run = std::min(step, kGraphRun) & ~1;
+            GraphKey key;
+            key.add(3).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.f2).add((uint64_t)L.P).add((uint64_t)L.plane)
+                .add((uint64_t)n2).add((uint64_t)n1).num(t).ptr(S2.q).add((uint64_t)S2.m2).add((uint64_t)S2.m1)
+                .add((uint64_t)S2.s).add((uint64_t)S2.k).num(S2.alpha_hat).add((uint64_t)S2.small)
+                .add((uint64_t)S2.tx).add((uint64_t)S2.ty).add((uint64_t)S2.ncl).add((uint64_t)S2.band)
+                .add((uint64_t)S2.smem).add((uint64_t)S2.hmax).add((uint64_t)S2.wpad).add((uint64_t)S2.qp);
+            TVS_CUDA(graph_run(key, s, [&](cudaStream_t st) {
+                void* a = cur;
+                void* b = nxt;
+                return schwarz2_iterate(&a, &b, L.f2, L.P, L.plane, n2, n1, S2, t, run, 0u, st);
+            }));
+            if (step > run)
+                TVS_CUDA(schwarz2_iterate(&cur, &nxt, L.f2, L.P, L.plane, n2, n1, S2, t, step - run, (uint32_t)(n + run), s));
+        } else {
+            TVS_CUDA(schwarz2_iterate(&cur, &nxt, L.f2, L.P, L.plane, n2, n1, S2, t, step, (uint32_t)n, s));
+        }
         n += step;
         if (check_loop && n < it.max_iter) {
             TVS_CUDA(launch_irv1_update(cur, nullptr, L.f2, L.R, L.C, L.P, L.plane, t, fa, true, false, nullptr, 0,

@@ -53,6 +53,7 @@ void carve_plan(Carver& cv, DctPlan& pl, int L) {
     pl.post = cv.take<float2>(L);
     pl.tw = cv.take<float2>(pl.M);
     pl.bhat = cv.take<float2>(pl.M);
+    pl.sig2 = cv.take<float>(L);
 }
 
 __global__ void plan_tables_kernel(DctPlan pl) {
@@ -68,6 +69,7 @@ __global__ void plan_tables_kernel(DctPlan pl) {
             pl.rot[i] = make_float2((float)c, (float)s);
             sincospi((double)i / (2.0 * (double)L), &s, &c);
             pl.post[i] = make_float2((float)c, (float)-s);
+            pl.sig2[i] = (float)(4.0 * s * s);
         }
         if (i < M) {
             sincospi(2.0 * (double)i / (double)M, &s, &c);
@@ -118,7 +120,8 @@ static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const
     e = cudaErrorInvalidValue;
     {
         ProfScope ps(kProfCols, s);
-        TVS_LOGM_SWITCH(pp.col.logM, (e = launch_cols_lm<LM>(S, rows, cols, pitch, pp.col, ba, nbatch, s)));
+        TVS_LOGM_SWITCH(pp.col.logM,
+                        (e = launch_cols_lm<LM>(S, rows, cols, pitch, pp.col, pp.row.sig2, ba, nbatch, s)));
     }
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;

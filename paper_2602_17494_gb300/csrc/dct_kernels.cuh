@@ -541,17 +541,16 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
 
 // Lambda(ky, kx) = -1 / (sigma_{R,ky}^2 + sigma_{C,kx}^2), 0 at (0, 0):
 // the row frequency pairs with the row count (see the oracle's reading).
-__device__ __forceinline__ float lap_symbol(int ky, int kx, int R, int C) {
-    const float sy = 2.0f * sinpif((float)ky / (2.0f * (float)R));
-    const float sx = 2.0f * sinpif((float)kx / (2.0f * (float)C));
-    const float den = sy * sy + sx * sx;
-    return den > 0.f ? -1.0f / den : 0.f;
+// sy2, sx2: the tabulated sigma^2 of the two axes.
+__device__ __forceinline__ float lap_symbol(float sy2, float sx2) {
+    const float den = sy2 + sx2;
+    return den > 0.f ? -rcp_ftz(den) : 0.f;
 }
 
 template <int LOGM>
 __global__ void __launch_bounds__(kDctThreads)
 dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
-                      int G, const __grid_constant__ BatchArgs ba) {
+                      const float* __restrict__ sig2x, int G, const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
@@ -594,9 +593,10 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
             float2* bufg = buf + (size_t)g * stride;
             const float2 Xk = unpack_dct2(bufg, k, L, pl);
             const float2 Xm = unpack_dct2(bufg, km, L, pl);
-            const float2 Yk = make_float2(Xk.x * lap_symbol(k, c0, rows, cols), Xk.y * lap_symbol(k, c0 + 1, rows, cols));
-            const float2 Ym = make_float2(Xm.x * lap_symbol(km, c0, rows, cols),
-                                          Xm.y * lap_symbol(km, c0 + 1, rows, cols));
+            const float sx0 = __ldg(&sig2x[c0]), sx1 = c0 + 1 < cols ? __ldg(&sig2x[c0 + 1]) : 0.f;
+            const float syk = __ldg(&pl.sig2[k]), sym = __ldg(&pl.sig2[km]);
+            const float2 Yk = make_float2(Xk.x * lap_symbol(syk, sx0), Xk.y * lap_symbol(syk, sx1));
+            const float2 Ym = make_float2(Xm.x * lap_symbol(sym, sx0), Xm.y * lap_symbol(sym, sx1));
             if (k == 0) {
                 stage_sample(bufg, peel + g, 0, L, pack_dct3(Yk.x, 0.f, Yk.y, 0.f, 0, pl), pl);
             } else {
@@ -678,14 +678,14 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
 }
 
 template <int LM>
-cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
-                           int nbatch, cudaStream_t s) {
+cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const float* sig2x,
+                           const BatchArgs& ba, int nbatch, cudaStream_t s) {
     static std::once_flag once;
     const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
     std::call_once(once, [smem] { allow_dct_smem(dct_cols_solve_kernel<LM>, smem); });
     const dim3 grid((cols + 1) / 2, nbatch);
-    return launch_pdl(dct_cols_solve_kernel<LM>, grid, dim3(fft_threads(pl.M)), smem, s, S, rows, cols, pitch, pl, 1,
-                      ba);
+    return launch_pdl(dct_cols_solve_kernel<LM>, grid, dim3(fft_threads(pl.M)), smem, s, S, rows, cols, pitch, pl,
+                      sig2x, 1, ba);
 }
 
 template <int LM>
@@ -703,8 +703,8 @@ cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const Dc
     template cudaError_t launch_bhat_lm<LM>(const DctPlan&, cudaStream_t);                                        \
     template cudaError_t launch_rows_fwd_lm<LM>(RowSource, float*, int, int, int, const DctPlan&,                  \
                                                 const RowSrcArgs&, const BatchArgs&, int, int, cudaStream_t);      \
-    template cudaError_t launch_cols_lm<LM>(float*, int, int, int, const DctPlan&, const BatchArgs&, int,           \
-                                            cudaStream_t);                                                        \
+    template cudaError_t launch_cols_lm<LM>(float*, int, int, int, const DctPlan&, const float*, const BatchArgs&,  \
+                                            int, cudaStream_t);                                                   \
     template cudaError_t launch_rows_inv_lm<LM>(float*, int, int, int, const DctPlan&, const BatchArgs&, int, int, \
                                                 cudaStream_t);
 

@@ -30,8 +30,8 @@ template <int LM>
 cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int pitch, const DctPlan& pl,
                                const RowSrcArgs& sa, const BatchArgs& ba, int nbatch, int maxrows, cudaStream_t s);
 template <int LM>
-cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
-                           int nbatch, cudaStream_t s);
+cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const float* sig2x,
+                           const BatchArgs& ba, int nbatch, cudaStream_t s);
 template <int LM>
 cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                                int nbatch, int maxrows, cudaStream_t s);

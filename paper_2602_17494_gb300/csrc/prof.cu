@@ -39,6 +39,8 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 
+bool prof_enabled() { return g_on.load(std::memory_order_relaxed) != 0; }
+
 ProfScope::ProfScope(ProfClass cls, cudaStream_t s) : cls_(cls), s_(s), a_(nullptr) {
     if (!g_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);

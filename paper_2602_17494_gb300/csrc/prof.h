@@ -21,6 +21,9 @@ enum ProfClass : int {
     kProfClasses = 10
 };
 
+// True while per-kernel profiling is on.
+bool prof_enabled();
+
 // Records an event on `s` at construction and at destruction when profiling
 // is enabled; a no-op otherwise.
 class ProfScope {

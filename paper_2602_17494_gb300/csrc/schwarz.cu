@@ -215,22 +215,11 @@ schwarz2_tile_kernel(TileArgs<S> a) {
 }
 
 // Packed f32x2 arithmetic (one instruction for two lanes, each rounded to
-// nearest like its scalar counterpart) and single-instruction approximate
-// reciprocal and reciprocal square root with subnormals flushed to zero.
+// nearest like its scalar counterpart).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_ftz(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ---------------------------------------------------------------------------
 // Small subdomains: one CTA per subdomain, 4 x 4 pixels per thread

@@ -291,11 +291,14 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
 #pragma unroll
             for (int q = 0; q < 4; ++q) pv[q] = sp[q * kBoxFloats + ob];
             if (WRITE_P) {
+                // |psi_k| = s2 rsqrt(s2) (the 1e-30 keeps it finite at psi = 0, far
+                // below the resolution of |psi|), one reciprocal per channel
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    const float den = 1.0f + t * sqrtf(gx[k] * gx[k] + gy[k] * gy[k]);
-                    pout[(size_t)(2 * k) * plane + o] = (pv[2 * k] + t * gx[k]) / den;
-                    pout[(size_t)(2 * k + 1) * plane + o] = (pv[2 * k + 1] + t * gy[k]) / den;
+                    const float s2 = fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1e-30f));
+                    const float inv = rcp_ftz(fmaf(t, s2 * rsqrt_ftz(s2), 1.0f));
+                    pout[(size_t)(2 * k) * plane + o] = fmaf(t, gx[k], pv[2 * k]) * inv;
+                    pout[(size_t)(2 * k + 1) * plane + o] = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
                 }
             }
             if (WRITE_TAU) {

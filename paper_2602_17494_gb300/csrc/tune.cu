@@ -6,6 +6,7 @@
 // timed with CUDA events on the caller's stream, and the fastest candidate
 // that reached the gap wins.
 #include "drivers.h"
+#include "graphs.h"
 
 #include <algorithm>
 
@@ -92,7 +93,10 @@ tvs_status tvs_tune_schwarz2(const float* d0, const float* tau, int n2, int n1, 
                     goto out;
                 }
                 tvs_report rep;
-                st = run_schwarz2(L, S2, n2, n1, alpha, *it, d, nullptr, stream, &rep);
+                {
+                    GraphsOff direct;   // the timed run must not include graph capture
+                    st = run_schwarz2(L, S2, n2, n1, alpha, *it, d, nullptr, stream, &rep);
+                }
                 if (st != TVS_OK && st != TVS_ERR_NOT_CONVERGED) {
                     result = st;
                     goto out;

@@ -57,6 +57,19 @@ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Single-instruction hardware approximations (about 2 ulp; subnormals flushed
+// to zero) of 1/sqrt(x) and 1/x.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float2 c_mulconj(float2 a, float2 b) {  // a * conj(b)
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
@@ -97,6 +110,7 @@ struct DctPlan {
     float2* post;   // exp(-i pi k / (2L)), k < L (Makhoul's post-twiddle)
     float2* tw;     // exp(-2 pi i j / M), j < M/2
     float2* bhat;   // FFT_M of the chirp filter, bit-reversed order, times 1/M
+    float* sig2;    // sigma_{L,k}^2 = (2 sin(pi k / (2L)))^2, k < L: eigenvalues of the 1-D Neumann Laplacian
 };
 
 int fft_len_for(int L);
