@@ -227,9 +227,11 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                     wa[2] = c_mul(wa[1], wa[1]);
                     wa[3] = c_mul(wa[2], wa[1]);
                 }
+                // with MR a multiple of 16, pidx(j + r MR) = pidx(j) + r (MR + MR / 16)
+                const float2* xj = x + pidx(j);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    float2 a = x[pidx(j + r * MR)];
+                    float2 a = (MR % 16 == 0) ? xj[r * (MR + MR / 16)] : x[pidx(j + r * MR)];
                     if (r > 0 && NS > 1) {
                         float2 w = (r >> 2) == 0 ? wb[r & 3]
                                                  : ((r & 3) == 0 ? wa[r >> 2] : c_mul(wa[r >> 2], wb[r & 3]));
@@ -259,6 +261,7 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                 const int j = b * U + uu;
                 const int jm = j & (NS - 1);
                 const int dst = (j - jm) * R + jm;   // (j / NS) * NS * R + j % NS
+                float2* xd = x + pidx(dst);           // NS a multiple of 16: slot r at r (NS + NS / 16)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     float2 y = v[q][b * R + r];
@@ -268,7 +271,8 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                         const int k = dst + r * NS;
                         if (k < ep.L) y = c_add(c_mul(__ldg(&ep.chirp[k]), y), c_mul(ep.peel[g], __ldg(&ep.rot[k])));
                     }
-                    x[pidx(dst + r * NS)] = y;
+                    if (NS % 16 == 0) xd[r * (NS + NS / 16)] = y;
+                    else x[pidx(dst + r * NS)] = y;
                 }
             }
         }
