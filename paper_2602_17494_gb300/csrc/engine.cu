@@ -14,6 +14,7 @@
 // All state stays on the device between steps; the host keeps only indices
 // and the per-request reduction results.
 #include "drivers.h"
+#include "graphs.h"
 
 #include <algorithm>
 #include <cmath>
@@ -89,6 +90,13 @@ struct Request {
     int slot = 0;           // row of the pinned result array
     bool checked = false;   // a check was enqueued this engine step
     tvs_report rep[2] = {};
+    cudaGraphExec_t g1 = nullptr;   // captured full step-1 chunk (check_every even), replayed each engine step
+    Request() = default;
+    Request(const Request&) = delete;
+    Request& operator=(const Request&) = delete;
+    ~Request() {
+        if (g1) cudaGraphExecDestroy(g1);
+    }
 };
 
 // Step-2 decomposition of an image under the engine's tile policy.
@@ -299,22 +307,47 @@ static tvs_status admit(EngineImpl* e) {
 
 // Step-1 chunk of one request on its side stream; the last update of the
 // chunk also evaluates the gap at its input iterate.
-static tvs_status step1_chunk(EngineImpl* e, Request* r) {
+// n TFS updates (the last with the check sums), the reduction and its copy
+// to the request's row of the pinned result array, on stream s; cur1/nxt1
+// alternate from *cur, *nxt.
+static cudaError_t step1_launches(EngineImpl* e, Request* r, int n, float** cur, float** nxt, cudaStream_t s) {
     const Step1Layout& L = r->L1;
-    cudaStream_t s = e->side[r->side];
     const float t = (float)e->cfg.it1.t, fd = (float)e->cfg.delta;
-    const int n = std::min(e->cfg.it1.check_every, e->cfg.it1.max_iter - r->it1);
     for (int j = 0; j < n; ++j) {
         const bool ck = j == n - 1;
-        TVS_CUDA(tfs_phi(r->cur1, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
-        TVS_CUDA(launch_tfs_update(r->cur1, r->nxt1, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
-                                   L.red.partial, L.red.err, s));
-        std::swap(r->cur1, r->nxt1);
+        cudaError_t err = tfs_phi(*cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s);
+        if (err != cudaSuccess) return err;
+        err = launch_tfs_update(*cur, *nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
+                                L.red.partial, L.red.err, s);
+        if (err != cudaSuccess) return err;
+        std::swap(*cur, *nxt);
     }
+    const cudaError_t err = finalize_red(L.red, tfs_blocks(L.R, L.C), s);
+    if (err != cudaSuccess) return err;
+    return cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
+                           cudaMemcpyDeviceToHost, s);
+}
+
+static tvs_status step1_chunk(EngineImpl* e, Request* r) {
+    cudaStream_t s = e->side[r->side];
+    const int n = std::min(e->cfg.it1.check_every, e->cfg.it1.max_iter - r->it1);
+    // a full chunk of an even number of updates leaves p in the buffer it
+    // started from, so one captured graph per request serves every such chunk
+    if (n == e->cfg.it1.check_every && n % 2 == 0 && graphs_enabled()) {
+        if (!r->g1) {
+            float* c0 = r->cur1;
+            float* c1 = r->nxt1;
+            graph_capture([&](cudaStream_t cs) { return step1_launches(e, r, n, &c0, &c1, cs); }, &r->g1);
+        }
+        if (r->g1) {
+            TVS_CUDA(cudaGraphLaunch(r->g1, s));
+            r->it1 += n;
+            r->checked = true;
+            return TVS_OK;
+        }
+    }
+    TVS_CUDA(step1_launches(e, r, n, &r->cur1, &r->nxt1, s));
     r->it1 += n;
-    TVS_CUDA(finalize_red(L.red, tfs_blocks(L.R, L.C), s));
-    TVS_CUDA(cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
-                             cudaMemcpyDeviceToHost, s));
     r->checked = true;
     return TVS_OK;
 }
@@ -324,6 +357,10 @@ static tvs_status step1_chunk(EngineImpl* e, Request* r) {
 static tvs_status step1_to_step2(EngineImpl* e, Request* r) {
     const Step1Layout& L = r->L1;
     cudaStream_t s = e->stream;
+    if (r->g1) {   // step 1 is over; its graph is not replayed again
+        cudaGraphExecDestroy(r->g1);
+        r->g1 = nullptr;
+    }
     unsigned err = 0;   // step 1 finished on a side stream that the last synchronization covered
     TVS_CUDA(cudaMemcpy(&err, L.red.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (err) {

@@ -44,6 +44,36 @@ bool graphs_enabled() { return g_off == 0 && g_global_on.load(std::memory_order_
 GraphsOff::GraphsOff() { ++g_off; }
 GraphsOff::~GraphsOff() { --g_off; }
 
+bool graph_capture(const std::function<cudaError_t(cudaStream_t)>& enqueue, cudaGraphExec_t* out) {
+    *out = nullptr;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaStream_t cs = capture_stream(device);
+    if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t launched = enqueue(cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ended = cudaStreamEndCapture(cs, &graph);
+    if (launched != cudaSuccess || ended != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t inst = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (inst != cudaSuccess) {
+        *out = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 cudaError_t graph_run(const GraphKey& key, cudaStream_t s, const std::function<cudaError_t(cudaStream_t)>& enqueue) {
     if (!graphs_enabled() || !key.valid()) return enqueue(s);
     int device = 0;
@@ -60,25 +90,7 @@ cudaError_t graph_run(const GraphKey& key, cudaStream_t s, const std::function<c
     }
     if (exec) return cudaGraphLaunch(exec, s);
 
-    cudaStream_t cs = capture_stream(device);
-    if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        return enqueue(s);
-    }
-    const cudaError_t launched = enqueue(cs);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ended = cudaStreamEndCapture(cs, &graph);
-    if (launched != cudaSuccess || ended != cudaSuccess || !graph) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return enqueue(s);
-    }
-    const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (inst != cudaSuccess) {
-        cudaGetLastError();
-        return enqueue(s);
-    }
+    if (!graph_capture(enqueue, &exec)) return enqueue(s);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (g_cache.size() >= kMaxGraphs) {

@@ -49,6 +49,11 @@ struct GraphsOff {
     GraphsOff& operator=(const GraphsOff&) = delete;
 };
 
+// Captures enqueue(stream) on a private stream into an instantiated graph
+// (*out, owned by the caller, cudaGraphExecDestroy).  Returns false (and
+// leaves no error pending) if capture or instantiation fails.
+bool graph_capture(const std::function<cudaError_t(cudaStream_t)>& enqueue, cudaGraphExec_t* out);
+
 // Runs enqueue(stream) on s: through the cached graph of `key` (capturing it
 // on first use) when graphs are enabled, else directly.  Capture or
 // instantiation failures fall back to the direct launches.
