@@ -26,7 +26,7 @@ namespace tvs {
 
 namespace {
 
-constexpr int kSideStreams = 8;
+constexpr int kSideStreams = 16;
 
 // First-fit allocator over [0, size) of the caller's pool (256-byte units).
 class PoolAlloc {
