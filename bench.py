@@ -496,8 +496,20 @@ def run_large(args, B, dev, torch):
         sides = [min(n, (i + 1) * 64 + 2) - max(0, i * 64 - 2) for i in range(m)]
         upd = k * sum(sides) ** 2
         tile_us = kern.get("schwarz_tile", {}).get("us_per_launch", float("nan"))
+        strip_us = kern.get("schwarz_combine", {}).get("us_per_launch", 0.0)
+        # the HBM roofline at k-fold reuse: one outer iteration moves about 44
+        # algorithmic bytes per image pixel (FP32; p^n with halo 9, f2 4.5, q
+        # read 9 and write 9, p^{n+1} on the exclusive cores 7, strip frames 5)
+        # and performs k updates of it
+        bpp = 44.0 / k
+        roof = hbm / bpp
+        ach = k * n * n / ((tile_us + strip_us) * 1e-6) / 1e9
         out[f"schwarz_64x64_s4_k{k}_kernels"] = {"kernels": kern, "redundancy": upd / (k * n * n),
-                                                 "tile_gpix_updates_per_s": upd / tile_us / 1e3}
+                                                 "tile_gpix_updates_per_s": upd / tile_us / 1e3,
+                                                 "k_reuse_roofline": {"bytes_per_pixel_update": bpp,
+                                                                      "roofline_gpix_updates_per_s": roof,
+                                                                      "achieved_gpix_updates_per_s": ach,
+                                                                      "frac": ach / roof}}
         ms_s, r_s = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(100000, T, 1e-4,
                                                                                       max(1, 40 // k)),
                                                 out=d, ws=wss))
