@@ -295,13 +295,14 @@ __device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, cons
     }
 }
 
-// Unit size and units per thread: 8-point units (radix-8 passes) up to 4096
-// points, so short transforms get twice the threads; 16-point units beyond;
+// Unit size and units per thread: 8-point units (radix-8 passes) up to 1024
+// points, so short transforms get twice the threads; 16-point units beyond
+// (fewer passes, and so fewer barriers, on the critical path of a line pair);
 // transforms of 16384 points have 1024 units for 512 threads.
 template <int LOGM>
 struct FftShape {
     static constexpr int M = 1 << LOGM;
-    static constexpr int LOGUV = LOGM <= 12 ? 3 : 4;
+    static constexpr int LOGUV = LOGM <= 10 ? 3 : 4;
     static constexpr int UV = 1 << LOGUV;
     static constexpr int UNITS = M < UV ? 1 : M / UV;
     static constexpr int UPT = UNITS > kDctThreads ? 2 : 1;

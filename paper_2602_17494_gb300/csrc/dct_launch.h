@@ -36,10 +36,10 @@ template <int LM>
 cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                                int nbatch, int maxrows, cudaStream_t s);
 
-// Threads for a transform of length M: one per FFT unit (8 points up to 4096,
+// Threads for a transform of length M: one per FFT unit (8 points up to 1024,
 // 16 beyond), two units per thread for the 16384-point transforms.
 inline int fft_threads(int M) {
-    const int uv = M <= 4096 ? 8 : 16;
+    const int uv = M <= 1024 ? 8 : 16;
     int units = M < uv ? 1 : M / uv;
     if (units > kDctThreads) units = (units + 1) / 2;
     int t = (units + 31) / 32 * 32;
