@@ -194,9 +194,12 @@ struct FftEpi {
 
 // One Stockham pass with everything about the shape known at compile time.
 // A thread "unit" holds UV = min(16, M) points: UV / R butterflies of radix R.
-template <int R, bool INV, int UPT, int M, int NS, int UVMAX, int EPI>
+// HALFIN (first pass only): the line is zero from M/2 on, so the upper half
+// of every butterfly's inputs is the constant 0 and is not read.
+template <int R, bool INV, int UPT, int M, int NS, int UVMAX, int EPI, bool HALFIN>
 __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
                                               const FftEpi& ep) {
+    static_assert(!HALFIN || NS == 1, "only the first pass reads the input line");
     constexpr int UV = M < UVMAX ? M : UVMAX;    // points per unit
     constexpr int B = UV / R;                    // butterflies per unit
     constexpr int U = M / UV;                    // units per transform
@@ -231,7 +234,8 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                 const float2* xj = x + pidx(j);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    float2 a = (MR % 16 == 0) ? xj[r * (MR + MR / 16)] : x[pidx(j + r * MR)];
+                    float2 a = make_float2(0.f, 0.f);
+                    if (!(HALFIN && r >= R / 2)) a = (MR % 16 == 0) ? xj[r * (MR + MR / 16)] : x[pidx(j + r * MR)];
                     if (r > 0 && NS > 1) {
                         float2 w = (r >> 2) == 0 ? wb[r & 3]
                                                  : ((r & 3) == 0 ? wa[r >> 2] : c_mul(wa[r >> 2], wb[r & 3]));
@@ -268,8 +272,10 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                     if (EPI == kEpiMul) {
                         y = c_mul(y, __ldg(&ep.mul[dst + r * NS]));
                     } else if (EPI == kEpiOut) {
+                        // outputs k >= L are read by no one: not stored
                         const int k = dst + r * NS;
-                        if (k < ep.L) y = c_add(c_mul(__ldg(&ep.chirp[k]), y), c_mul(ep.peel[g], __ldg(&ep.rot[k])));
+                        if (k >= ep.L) continue;
+                        y = c_add(c_mul(__ldg(&ep.chirp[k]), y), c_mul(ep.peel[g], __ldg(&ep.rot[k])));
                     }
                     if (NS % 16 == 0) xd[r * (NS + NS / 16)] = y;
                     else x[pidx(dst + r * NS)] = y;
@@ -282,16 +288,16 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
 
 // The pass sequence for M = 2^LOGM: radix 16 while at least 16 points remain
 // per sub-transform, then the remaining 8, 4 or 2.
-template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, int EPI>
+template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, int EPI, bool HALFIN>
 __device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
                                          const FftEpi& ep) {
     if constexpr (LOGNS < LOGM) {
         constexpr int REM = LOGM - LOGNS;
         constexpr int LR = REM >= LOGUV ? LOGUV : REM;
         constexpr bool LAST = LOGNS + LR == LOGM;
-        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS), (1 << LOGUV), LAST ? EPI : kEpiNone>(
-            buf, stride, nfft, tw, ep);
-        fft_from<LOGM, LOGNS + LR, INV, UPT, LOGUV, EPI>(buf, stride, nfft, tw, ep);
+        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS), (1 << LOGUV), LAST ? EPI : kEpiNone,
+                      HALFIN && LOGNS == 0>(buf, stride, nfft, tw, ep);
+        fft_from<LOGM, LOGNS + LR, INV, UPT, LOGUV, EPI, false>(buf, stride, nfft, tw, ep);
     }
 }
 
@@ -308,10 +314,11 @@ struct FftShape {
     static constexpr int UPT = UNITS > kDctThreads ? 2 : 1;
 };
 
-template <int LOGM, bool INV, int EPI = kEpiNone>
+// HALFIN: every line is zero from M/2 on.
+template <int LOGM, bool INV, int EPI = kEpiNone, bool HALFIN = false>
 __device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
                                              const FftEpi& ep = FftEpi{}) {
-    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT, FftShape<LOGM>::LOGUV, EPI>(buf, stride, nfft, tw, ep);
+    fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT, FftShape<LOGM>::LOGUV, EPI, HALFIN>(buf, stride, nfft, tw, ep);
 }
 
 // Chirp filter spectrum: b[m] = conj(c_m) for lags m in [-(L-2), L-1] stored
@@ -357,7 +364,9 @@ __device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const 
     const FftEpi ep{pl.bhat, pl.chirp, pl.rot, peel, pl.L};
     // FFT, times the filter spectrum (fused into the last pass), inverse FFT,
     // then the chirp and the peeled sample (fused into its last pass)
-    fft_stockham<LOGM, false, kEpiMul>(buf, stride, G, pl.tw, ep);
+    // the chirped input occupies [0, L - 1) with L - 1 <= M / 2, so the first
+    // pass reads only the lower half
+    fft_stockham<LOGM, false, kEpiMul, true>(buf, stride, G, pl.tw, ep);
     fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, pl.tw, ep);
 }
 
@@ -371,8 +380,10 @@ __device__ __forceinline__ void stage_sample(float2* bufg, float2* peelg, int n,
     else bufg[pidx(n)] = c_mul(z, __ldg(&pl.chirp[n]));
 }
 
+// Zeros at [L - 1, M / 2): the part of the lower half that the staged
+// samples leave free (the first pass never reads the upper half).
 __device__ __forceinline__ void zero_tail(float2* buf, int stride, int G, int L, int M) {
-    const int t = M - (L - 1);
+    const int t = M / 2 - (L - 1);
     for (int b = threadIdx.x; b < G * t; b += blockDim.x) {
         const int g = b / t;
         buf[(size_t)g * stride + pidx((L - 1) + (b - g * t))] = make_float2(0.f, 0.f);
@@ -610,9 +621,9 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
             }
             if (k == 0 ? L == 1 : km == L - 1) bufg[pidx(L - 1)] = make_float2(0.f, 0.f);
         }
-        // the rest of the zero tail, [L, M), is read by no thread above
+        // the rest of the lower half's zero tail, [L, M / 2), is read by no thread above
         {
-            const int tl = M - L;
+            const int tl = M / 2 - L;
             for (int b = threadIdx.x; b < gc * tl; b += blockDim.x) {
                 const int g = b / tl;
                 buf[(size_t)g * stride + pidx(L + (b - g * tl))] = make_float2(0.f, 0.f);
