@@ -272,7 +272,10 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
                     if (EPI == kEpiMul) {
                         y = c_mul(y, __ldg(&ep.mul[dst + r * NS]));
                     } else if (EPI == kEpiOut) {
-                        // outputs k >= L are read by no one: not stored
+                        // outputs k >= L are read by no one: not stored.  In this
+                        // last pass (NS R = M) every r > R/2 gives k > M/2 >= L - 1,
+                        // known at compile time, so those outputs are not computed
+                        if (r > R / 2) continue;
                         const int k = dst + r * NS;
                         if (k >= ep.L) continue;
                         y = c_add(c_mul(__ldg(&ep.chirp[k]), y), c_mul(ep.peel[g], __ldg(&ep.rot[k])));
@@ -681,6 +684,7 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
     std::call_once(once, [smem] {
         allow_dct_smem(dct_rows_fwd_kernel<RowSource::Plain, LM>, smem);
         allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivField, LM>, smem);
+        allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivVecdiv, LM>, smem);
     });
     const dim3 grid((maxrows + 1) / 2, nbatch);
     const int nt = fft_threads(pl.M);
@@ -689,6 +693,9 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
                           sa, 1, ba);
     if (src == RowSource::DivField)
         return launch_pdl(dct_rows_fwd_kernel<RowSource::DivField, LM>, grid, dim3(nt), smem, s, S, rows, cols, pitch,
+                          pl, sa, 1, ba);
+    if (src == RowSource::DivVecdiv)
+        return launch_pdl(dct_rows_fwd_kernel<RowSource::DivVecdiv, LM>, grid, dim3(nt), smem, s, S, rows, cols, pitch,
                           pl, sa, 1, ba);
     return cudaErrorInvalidValue;
 }
