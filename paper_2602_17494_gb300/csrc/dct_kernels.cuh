@@ -590,10 +590,17 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
             const int g = b - r * gc;
             const int c0 = 2 * (base + g);
             const bool in = r >= rr.x && r < rr.y;
-            const float* a = in ? S + row_off(ba, rr, r, pitch) + c0 : S;
-            const float x0 = in ? a[0] : 0.f;
-            const float x1 = (in && c0 + 1 < cols) ? a[1] : 0.f;
-            stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(r, L), L, make_float2(x0, x1), pl);
+            // with an even pitch the pair (c0, c0 + 1) is one 8-byte load (c0 is
+            // even; c0 + 1 <= pitch - 1 is inside the row's storage even when it
+            // is the padding column)
+            float2 x = make_float2(0.f, 0.f);
+            if (in) {
+                const float* a = S + row_off(ba, rr, r, pitch) + c0;
+                if ((pitch & 1) == 0) x = *reinterpret_cast<const float2*>(a);
+                else x = make_float2(a[0], c0 + 1 < cols ? a[1] : 0.f);
+            }
+            if (c0 + 1 >= cols) x.y = 0.f;
+            stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(r, L), L, x, pl);
         }
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
@@ -641,8 +648,12 @@ dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
             if (r < rr.x || r >= rr.y) continue;
             const float2 Y = buf[(size_t)g * stride + pidx(mk_perm(r, L))];
             float* a = S + row_off(ba, rr, r, pitch) + c0;
-            a[0] = Y.x * invL;
-            if (c0 + 1 < cols) a[1] = -Y.y * invL;
+            if (c0 + 1 < cols && (pitch & 1) == 0) {
+                *reinterpret_cast<float2*>(a) = make_float2(Y.x * invL, -Y.y * invL);
+            } else {
+                a[0] = Y.x * invL;
+                if (c0 + 1 < cols) a[1] = -Y.y * invL;
+            }
         }
         __syncthreads();
     }
@@ -684,7 +695,6 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
     std::call_once(once, [smem] {
         allow_dct_smem(dct_rows_fwd_kernel<RowSource::Plain, LM>, smem);
         allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivField, LM>, smem);
-        allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivVecdiv, LM>, smem);
     });
     const dim3 grid((maxrows + 1) / 2, nbatch);
     const int nt = fft_threads(pl.M);
@@ -693,9 +703,6 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
                           sa, 1, ba);
     if (src == RowSource::DivField)
         return launch_pdl(dct_rows_fwd_kernel<RowSource::DivField, LM>, grid, dim3(nt), smem, s, S, rows, cols, pitch,
-                          pl, sa, 1, ba);
-    if (src == RowSource::DivVecdiv)
-        return launch_pdl(dct_rows_fwd_kernel<RowSource::DivVecdiv, LM>, grid, dim3(nt), smem, s, S, rows, cols, pitch,
                           pl, sa, 1, ba);
     return cudaErrorInvalidValue;
 }
