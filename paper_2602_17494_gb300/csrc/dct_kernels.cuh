@@ -529,19 +529,25 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
         const int base = blockIdx.x * G;
         if (base >= npairs) return;
         const int gc = min(G, npairs - base);
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int g = b / L;
-            const int k = b - g * L;
+        // one thread per pair (k, L - k): the same four loads stage both samples
+        const int half = L / 2 + 1;
+        for (int b = threadIdx.x; b < gc * half; b += blockDim.x) {
+            const int g = b / half;
+            const int k = b - g * half;
+            const int km = k == 0 ? 0 : L - k;
+            if (k > km) continue;                            // each pair once
             const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
             const float* a0 = S + row_off(ba, rr, r0, pitch);
-            const float x1k = a0[k], x1m = k ? a0[L - k] : 0.f;
+            const float x1k = a0[k], x1m = k ? a0[km] : 0.f;
             float x2k = 0.f, x2m = 0.f;
             if (r1 < rr.y) {
                 const float* a1 = S + row_off(ba, rr, r1, pitch);
                 x2k = a1[k];
-                x2m = k ? a1[L - k] : 0.f;
+                x2m = k ? a1[km] : 0.f;
             }
-            stage_sample(buf + (size_t)g * stride, peel + g, k, L, pack_dct3(x1k, x1m, x2k, x2m, k, pl), pl);
+            float2* bufg = buf + (size_t)g * stride;
+            stage_sample(bufg, peel + g, k, L, pack_dct3(x1k, x1m, x2k, x2m, k, pl), pl);
+            if (k != 0 && km != k) stage_sample(bufg, peel + g, km, L, pack_dct3(x1m, x1k, x2m, x2k, km, pl), pl);
         }
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
