@@ -373,6 +373,11 @@ __device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const 
     fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, pl.tw, ep);
 }
 
+// Rows start on 16-byte boundaries: base and pitch (in floats) allow float4 access.
+__device__ __forceinline__ bool vec4_ok(const float* base, int pitch) {
+    return ((reinterpret_cast<uintptr_t>(base) & 15) == 0) && ((pitch & 3) == 0);
+}
+
 // Makhoul's reordering: position of input sample j in the reordered line.
 __device__ __forceinline__ int mk_perm(int j, int L) { return (j & 1) ? (L - 1 - (j >> 1)) : (j >> 1); }
 
@@ -482,30 +487,94 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
         const int base = blockIdx.x * G;
         if (base >= npairs) return;
         const int gc = min(G, npairs - base);
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int g = b / L;
-            const int j = b - g * L;
-            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
-            float x0, x1;
-            if (SRC == RowSource::Plain) {
-                x0 = __ldg(&sa.a[row_off(ba, rr, r0, sa.pitch) + j]);
-                x1 = (r1 < rr.y) ? __ldg(&sa.a[row_off(ba, rr, r1, sa.pitch) + j]) : 0.f;
-            } else {
-                x0 = row_source<SRC>(sa, r0, j, rows, cols);
-                x1 = (r1 < rr.y) ? row_source<SRC>(sa, r1, j, rows, cols) : 0.f;
+        if (SRC == RowSource::Plain && vec4_ok(sa.a, sa.pitch) && vec4_ok(out, pitch)) {
+            // groups of four samples, one 16-byte load per row
+            const int ng = (L + 3) >> 2;
+            for (int b = threadIdx.x; b < gc * ng; b += blockDim.x) {
+                const int g = b / ng;
+                const int j0 = (b - g * ng) << 2;
+                const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+                const float* a0 = sa.a + row_off(ba, rr, r0, sa.pitch) + j0;
+                const float* a1 = sa.a + row_off(ba, rr, r1, sa.pitch) + j0;
+                float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
+                if (j0 + 3 < L) {
+                    const float4 u = __ldg(reinterpret_cast<const float4*>(a0));
+                    v0[0] = u.x; v0[1] = u.y; v0[2] = u.z; v0[3] = u.w;
+                    if (r1 < rr.y) {
+                        const float4 w = __ldg(reinterpret_cast<const float4*>(a1));
+                        v1[0] = w.x; v1[1] = w.y; v1[2] = w.z; v1[3] = w.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (j0 + e < L) {
+                            v0[e] = __ldg(a0 + e);
+                            if (r1 < rr.y) v1[e] = __ldg(a1 + e);
+                        }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j0 + e < L)
+                        stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(j0 + e, L), L,
+                                     make_float2(v0[e], v1[e]), pl);
             }
-            stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(j, L), L, make_float2(x0, x1), pl);
+        } else {
+            for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+                const int g = b / L;
+                const int j = b - g * L;
+                const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+                float x0, x1;
+                if (SRC == RowSource::Plain) {
+                    x0 = __ldg(&sa.a[row_off(ba, rr, r0, sa.pitch) + j]);
+                    x1 = (r1 < rr.y) ? __ldg(&sa.a[row_off(ba, rr, r1, sa.pitch) + j]) : 0.f;
+                } else {
+                    x0 = row_source<SRC>(sa, r0, j, rows, cols);
+                    x1 = (r1 < rr.y) ? row_source<SRC>(sa, r1, j, rows, cols) : 0.f;
+                }
+                stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(j, L), L, make_float2(x0, x1), pl);
+            }
         }
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
         bluestein<LOGM>(buf, stride, gc, pl, peel);
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int g = b / L;
-            const int k = b - g * L;
-            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
-            const float2 X = unpack_dct2(buf + (size_t)g * stride, k, L, pl);
-            out[row_off(ba, rr, r0, pitch) + k] = X.x;
-            if (r1 < rr.y) out[row_off(ba, rr, r1, pitch) + k] = X.y;
+        if (vec4_ok(out, pitch)) {
+            // groups of four outputs, one 16-byte store per row
+            const int ng = (L + 3) >> 2;
+            for (int b = threadIdx.x; b < gc * ng; b += blockDim.x) {
+                const int g = b / ng;
+                const int k0 = (b - g * ng) << 2;
+                const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+                float v0[4], v1[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 X = k0 + e < L ? unpack_dct2(buf + (size_t)g * stride, k0 + e, L, pl)
+                                                : make_float2(0.f, 0.f);
+                    v0[e] = X.x;
+                    v1[e] = X.y;
+                }
+                float* o0 = out + row_off(ba, rr, r0, pitch) + k0;
+                float* o1 = out + row_off(ba, rr, r1, pitch) + k0;
+                if (k0 + 3 < L) {
+                    *reinterpret_cast<float4*>(o0) = make_float4(v0[0], v0[1], v0[2], v0[3]);
+                    if (r1 < rr.y) *reinterpret_cast<float4*>(o1) = make_float4(v1[0], v1[1], v1[2], v1[3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (k0 + e < L) {
+                            o0[e] = v0[e];
+                            if (r1 < rr.y) o1[e] = v1[e];
+                        }
+                }
+            }
+        } else {
+            for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+                const int g = b / L;
+                const int k = b - g * L;
+                const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+                const float2 X = unpack_dct2(buf + (size_t)g * stride, k, L, pl);
+                out[row_off(ba, rr, r0, pitch) + k] = X.x;
+                if (r1 < rr.y) out[row_off(ba, rr, r1, pitch) + k] = X.y;
+            }
         }
         __syncthreads();
     }
@@ -552,13 +621,44 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
         bluestein<LOGM>(buf, stride, gc, pl, peel);
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int g = b / L;
-            const int j = b - g * L;
-            const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
-            const float2 Y = buf[(size_t)g * stride + pidx(mk_perm(j, L))];
-            S[row_off(ba, rr, r0, pitch) + j] = Y.x * invL;
-            if (r1 < rr.y) S[row_off(ba, rr, r1, pitch) + j] = -Y.y * invL;
+        if (vec4_ok(S, pitch)) {
+            // groups of four outputs, one 16-byte store per row
+            const int ng = (L + 3) >> 2;
+            for (int b = threadIdx.x; b < gc * ng; b += blockDim.x) {
+                const int g = b / ng;
+                const int j0 = (b - g * ng) << 2;
+                const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+                float v0[4], v1[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 Y = j0 + e < L ? buf[(size_t)g * stride + pidx(mk_perm(j0 + e, L))]
+                                                : make_float2(0.f, 0.f);
+                    v0[e] = Y.x * invL;
+                    v1[e] = -Y.y * invL;
+                }
+                float* o0 = S + row_off(ba, rr, r0, pitch) + j0;
+                float* o1 = S + row_off(ba, rr, r1, pitch) + j0;
+                if (j0 + 3 < L) {
+                    *reinterpret_cast<float4*>(o0) = make_float4(v0[0], v0[1], v0[2], v0[3]);
+                    if (r1 < rr.y) *reinterpret_cast<float4*>(o1) = make_float4(v1[0], v1[1], v1[2], v1[3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (j0 + e < L) {
+                            o0[e] = v0[e];
+                            if (r1 < rr.y) o1[e] = v1[e];
+                        }
+                }
+            }
+        } else {
+            for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
+                const int g = b / L;
+                const int j = b - g * L;
+                const int r0 = rr.x + 2 * (base + g), r1 = r0 + 1;
+                const float2 Y = buf[(size_t)g * stride + pidx(mk_perm(j, L))];
+                S[row_off(ba, rr, r0, pitch) + j] = Y.x * invL;
+                if (r1 < rr.y) S[row_off(ba, rr, r1, pitch) + j] = -Y.y * invL;
+            }
         }
         __syncthreads();
     }
