@@ -86,7 +86,7 @@ struct Request {
     float* tau = nullptr;
     float *cur1 = nullptr, *nxt1 = nullptr;
     void *cur2 = nullptr, *nxt2 = nullptr;
-    int side = 0;           // side stream of step 1
+    int side = 0;           // side stream of the step-1 chunks and the step-2 checks
     int slot = 0;           // row of the pinned result array
     bool checked = false;   // a check was enqueued this engine step
     tvs_report rep[2] = {};
@@ -139,7 +139,7 @@ struct EngineImpl {
     PoolAlloc alloc;
     cudaStream_t stream;
     cudaStream_t side[kSideStreams];
-    cudaEvent_t ev_main, ev_side[kSideStreams];
+    cudaEvent_t ev_main, ev_s2, ev_side[kSideStreams];   // ev_s2: the shared step-2 launches are enqueued
     std::deque<Request*> queue;
     std::vector<Request*> live;
     std::vector<Request*> done;
@@ -214,7 +214,8 @@ tvs_status tvs_engine_create(const tvs_engine_config* cfg, void* pool, size_t po
                             cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(reinterpret_cast<void**>(&e->host_imgs), 2 * (size_t)cfg->max_live * sizeof(TileImg),
                             cudaHostAllocDefault) == cudaSuccess &&
-              cudaEventCreateWithFlags(&e->ev_main, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&e->ev_main, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->ev_s2, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < kSideStreams; ++i)
         ok = cudaStreamCreateWithFlags(&e->side[i], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&e->ev_side[i], cudaEventDisableTiming) == cudaSuccess;
@@ -263,6 +264,7 @@ void tvs_engine_destroy(tvs_engine* h) {
             if (e->ev_side[i]) cudaEventDestroy(e->ev_side[i]);
         }
         if (e->ev_main) cudaEventDestroy(e->ev_main);
+        if (e->ev_s2) cudaEventDestroy(e->ev_s2);
         if (e->host_red) cudaFreeHost(e->host_red);
         if (e->host_imgs) cudaFreeHost(e->host_imgs);
         for (Request* r : e->queue) delete r;
@@ -414,15 +416,24 @@ static tvs_status step2_chunk(EngineImpl* e, std::vector<Request*>& rs) {
     // the host array is rewritten next step, after this step's synchronization
     TVS_CUDA(schwarz2_iterate_multi(c.it2.storage, e->dev_imgs, nimg, nsub, tx, ty, c.k_inner, (float)c.it2.t, n,
                                     seed, e->stream));
+    // the per-request checks are independent small launches: they run on the
+    // requests' side streams, after the shared launches, so that they overlap
+    TVS_CUDA(cudaEventRecord(e->ev_s2, e->stream));
+    bool waited[kSideStreams] = {};
     for (Request* r : rs) {
         if (n & 1) std::swap(r->cur2, r->nxt2);
         r->it2 += n;
         const Step2Layout& L = r->L2;
+        cudaStream_t ss = e->side[r->side];
+        if (!waited[r->side]) {
+            TVS_CUDA(cudaStreamWaitEvent(ss, e->ev_s2, 0));
+            waited[r->side] = true;
+        }
         TVS_CUDA(launch_irv1_update(r->cur2, nullptr, L.f2, L.R, L.C, L.P, L.plane, (float)c.it2.t, (float)c.alpha,
-                                    true, false, nullptr, 0, L.red.partial, L.st, 0u, L.red.err, e->stream));
-        TVS_CUDA(finalize_red(L.red, irv1_blocks(L.R, L.C), e->stream));
+                                    true, false, nullptr, 0, L.red.partial, L.st, 0u, L.red.err, ss));
+        TVS_CUDA(finalize_red(L.red, irv1_blocks(L.R, L.C), ss));
         TVS_CUDA(cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
-                                 cudaMemcpyDeviceToHost, e->stream));
+                                 cudaMemcpyDeviceToHost, ss));
         r->checked = true;
     }
     return TVS_OK;
