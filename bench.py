@@ -198,8 +198,9 @@ def algorithmic(name: str, launches: int) -> tuple[str, float, str]:
     if name in ("dct_rows_fwd", "dct_rows_inv"):
         # one packed Bluestein transform (2 FFTs of length M) per pair of rows
         return "alu", ((R + 1) // 2) * 2 * fft_flops(C), "flops"
-    if name == "dct_cols_solve":
-        return "alu", ((C + 1) // 2) * 4 * fft_flops(R), "flops"
+    if name == "tri_cols_solve":
+        # one Neumann tridiagonal solve per column, in place: read and write 4 B per point
+        return "hbm", 8.0 * R * C, "bytes"
     if name == "schwarz_tile":
         # per inner update and pixel: div (4 add), residual (1), grad (2), norm (3 + sqrt),
         # update (2 mul + 2 fma + 2 div ~ 8) -- ~20 flops
@@ -317,7 +318,7 @@ def run_gpu(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
     # capture of the current kernel at this workload; the 1025^2 grid stays in L2
-    traffic = {"dct_cols_solve": 4449792.0}.get(name) if N == 1024 else None
+    traffic = {"dct_rows_fwd": 4418560.0, "dct_rows_inv": 4415488.0, "tri_cols_solve": 4355584.0}.get(name) if N == 1024 else None
     roof.update({"frac": achieved / peak, "traffic": traffic, "kernel": name,
                  "avg_launch_us": avg_s * 1e6, "launches_per_step": nl // args.steps})
 

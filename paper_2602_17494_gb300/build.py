@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtvs.so")
-SOURCES = ["api.cu", "dct.cu", "tfs.cu", "irv.cu", "schwarz.cu", "schwarz1.cu", "prof.cu", "noalloc.cu", "tma.cu", "engine.cu", "tune.cu", "quality.cu", "graphs.cu",
+SOURCES = ["api.cu", "dct.cu", "tfs.cu", "irv.cu", "schwarz.cu", "schwarz1.cu", "prof.cu", "noalloc.cu", "tma.cu", "engine.cu", "tune.cu", "quality.cu", "graphs.cu", "tri_solve.cu",
            "dct_lm_a.cu", "dct_lm_b.cu", "dct_lm_c.cu", "dct_lm_d.cu", "dct_lm_e.cu", "dct_lm_f.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -23,8 +23,8 @@
 //
 // Kernels:
 //   dct_rows_fwd  : per pair of rows, optional fused stencil source -> X'
-//   dct_cols_solve: per strip of column pairs, forward DCT along y, multiply
-//                   by Lambda(k_y, k_x), inverse DCT along y (in place)
+//   tri_cols_solve: per column pair, D'^{-1} Lambda(., k_x) D' along y, which
+//                   is a Neumann tridiagonal solve (tri_solve.cu; in place)
 //   dct_rows_inv  : per pair of rows, inverse DCT along x (in place)
 #include "dct_launch.h"
 #include "prof.h"
@@ -88,26 +88,23 @@ cudaError_t build_plan(const DctPlan& pl, cudaStream_t s) {
     return e;
 }
 
-void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols) {
+void carve_poisson(Carver& cv, PoissonPlans& pp, int cols) {
     carve_plan(cv, pp.row, cols);
-    carve_plan(cv, pp.col, rows);
 }
 
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s) {
-    cudaError_t e = build_plan(pp.row, s);
-    if (e != cudaSuccess) return e;
-    return build_plan(pp.col, s);
+    return build_plan(pp.row, s);
 }
 
 // --------------------------------------------------------------------------
-// Poisson solve: row transforms, fused column solve, inverse row transforms.
+// Poisson solve: row transforms, tridiagonal column solve, inverse row transforms.
 // One pair of lines per CTA (the kernels are latency-bound, so resident warps
 // matter more than batching).
 // --------------------------------------------------------------------------
 static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const PoissonPlans& pp, RowSource src,
                                   const RowSrcArgs& sa, int nbatch, const int2* ranges, long bstride, int maxrows,
                                   int packed, cudaStream_t s) {
-    if (pp.row.logM < kMinLogM || pp.row.logM > kMaxLogM || pp.col.logM < kMinLogM || pp.col.logM > kMaxLogM)
+    if (pp.row.logM < kMinLogM || pp.row.logM > kMaxLogM)
         return cudaErrorInvalidValue;
     const BatchArgs ba{ranges, bstride, packed};
     cudaError_t e = cudaErrorInvalidValue;
@@ -120,8 +117,7 @@ static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const
     e = cudaErrorInvalidValue;
     {
         ProfScope ps(kProfCols, s);
-        TVS_LOGM_SWITCH(pp.col.logM,
-                        (e = launch_cols_lm<LM>(S, rows, cols, pitch, pp.col, pp.row.sig2, ba, nbatch, s)));
+        e = launch_tri_cols(S, rows, cols, pitch, pp.row.sig2, ba, nbatch, s);
     }
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;

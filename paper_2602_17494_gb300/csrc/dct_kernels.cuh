@@ -23,8 +23,8 @@
 //
 // Kernels:
 //   dct_rows_fwd  : per pair of rows, optional fused stencil source -> X'
-//   dct_cols_solve: per strip of column pairs, forward DCT along y, multiply
-//                   by Lambda(k_y, k_x), inverse DCT along y (in place)
+//   (between them the column pass applies D'^{-1} Lambda D' along y as one
+//    tridiagonal solve per column: tri_solve.cu)
 //   dct_rows_inv  : per pair of rows, inverse DCT along x (in place)
 //
 // This header holds the templated device code; dct_lm_*.cu instantiate it for
@@ -350,13 +350,6 @@ __global__ void __launch_bounds__(kDctThreads) plan_bhat_kernel(const __grid_con
         pl.bhat[m] = make_float2(sm[pidx(m)].x * inv, sm[pidx(m)].y * inv);
 }
 
-__device__ __forceinline__ int2 batch_rows(const BatchArgs& ba, int rows) {
-    return ba.ranges ? ba.ranges[blockIdx.y] : make_int2(0, rows);
-}
-__device__ __forceinline__ size_t row_off(const BatchArgs& ba, int2 rr, int r, int pitch) {
-    return (size_t)(ba.packed ? r - rr.x : r) * pitch;
-}
-
 // --------------------------------------------------------------------------
 // Bluestein core: buf[g][0 .. L-2] holds the chirped input a_n = z_n c_n,
 // buf[g][L-1 .. M) is zero and peel[g] = z_{L-1}.  On return buf[g][k] =
@@ -664,108 +657,6 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
     }
 }
 
-// Lambda(ky, kx) = -1 / (sigma_{R,ky}^2 + sigma_{C,kx}^2), 0 at (0, 0):
-// the row frequency pairs with the row count (see the oracle's reading).
-// sy2, sx2: the tabulated sigma^2 of the two axes.
-__device__ __forceinline__ float lap_symbol(float sy2, float sx2) {
-    const float den = sy2 + sx2;
-    return den > 0.f ? -rcp_ftz(den) : 0.f;
-}
-
-template <int LOGM>
-__global__ void __launch_bounds__(kDctThreads)
-dct_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
-                      const float* __restrict__ sig2x, int G, const __grid_constant__ BatchArgs ba) {
-    extern __shared__ float2 sm[];
-    pdl_wait();
-    pdl_trigger();
-    const int2 rr = batch_rows(ba, rows);       // rows outside rr are read as zero and not written
-    S += (size_t)blockIdx.y * ba.bstride;
-    const int L = rows, M = pl.M, stride = padded_len(M);
-    float2* buf = sm;
-    float2* peel = sm + (size_t)G * stride;
-    const int npairs = (cols + 1) >> 1;
-    const float invL = 1.0f / (float)L;
-    {
-        const int base = blockIdx.x * G;
-        if (base >= npairs) return;
-        const int gc = min(G, npairs - base);
-        // load with the pair index fastest so that a warp reads contiguous row segments
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int r = b / gc;
-            const int g = b - r * gc;
-            const int c0 = 2 * (base + g);
-            const bool in = r >= rr.x && r < rr.y;
-            // with an even pitch the pair (c0, c0 + 1) is one 8-byte load (c0 is
-            // even; c0 + 1 <= pitch - 1 is inside the row's storage even when it
-            // is the padding column)
-            float2 x = make_float2(0.f, 0.f);
-            if (in) {
-                const float* a = S + row_off(ba, rr, r, pitch) + c0;
-                if ((pitch & 1) == 0) x = *reinterpret_cast<const float2*>(a);
-                else x = make_float2(a[0], c0 + 1 < cols ? a[1] : 0.f);
-            }
-            if (c0 + 1 >= cols) x.y = 0.f;
-            stage_sample(buf + (size_t)g * stride, peel + g, mk_perm(r, L), L, x, pl);
-        }
-        zero_tail(buf, stride, gc, L, M);
-        __syncthreads();
-        bluestein<LOGM>(buf, stride, gc, pl, peel);
-        // Spectrum step in place: one thread per pair (k, L - k) reads both lines'
-        // DCT-II values at k and L - k, multiplies by (tilde Delta)^dagger and
-        // writes the inverse transform's staged inputs back to the same two
-        // positions (position L - 1 goes to the peel slot and is cleared).
-        const int half = L / 2 + 1;
-        for (int b = threadIdx.x; b < gc * half; b += blockDim.x) {
-            const int g = b / half;
-            const int k = b - g * half;
-            const int km = k == 0 ? 0 : L - k;
-            if (k > km) continue;                            // each pair once
-            const int c0 = 2 * (base + g);
-            float2* bufg = buf + (size_t)g * stride;
-            const float2 Xk = unpack_dct2(bufg, k, L, pl);
-            const float2 Xm = unpack_dct2(bufg, km, L, pl);
-            const float sx0 = __ldg(&sig2x[c0]), sx1 = c0 + 1 < cols ? __ldg(&sig2x[c0 + 1]) : 0.f;
-            const float syk = __ldg(&pl.sig2[k]), sym = __ldg(&pl.sig2[km]);
-            const float2 Yk = make_float2(Xk.x * lap_symbol(syk, sx0), Xk.y * lap_symbol(syk, sx1));
-            const float2 Ym = make_float2(Xm.x * lap_symbol(sym, sx0), Xm.y * lap_symbol(sym, sx1));
-            if (k == 0) {
-                stage_sample(bufg, peel + g, 0, L, pack_dct3(Yk.x, 0.f, Yk.y, 0.f, 0, pl), pl);
-            } else {
-                stage_sample(bufg, peel + g, k, L, pack_dct3(Yk.x, Ym.x, Yk.y, Ym.y, k, pl), pl);
-                if (km != k) stage_sample(bufg, peel + g, km, L, pack_dct3(Ym.x, Yk.x, Ym.y, Yk.y, km, pl), pl);
-            }
-            if (k == 0 ? L == 1 : km == L - 1) bufg[pidx(L - 1)] = make_float2(0.f, 0.f);
-        }
-        // the rest of the lower half's zero tail, [L, M / 2), is read by no thread above
-        {
-            const int tl = M / 2 - L;
-            for (int b = threadIdx.x; b < gc * tl; b += blockDim.x) {
-                const int g = b / tl;
-                buf[(size_t)g * stride + pidx(L + (b - g * tl))] = make_float2(0.f, 0.f);
-            }
-        }
-        __syncthreads();
-        bluestein<LOGM>(buf, stride, gc, pl, peel);
-        for (int b = threadIdx.x; b < gc * L; b += blockDim.x) {
-            const int r = b / gc;
-            const int g = b - r * gc;
-            const int c0 = 2 * (base + g);
-            if (r < rr.x || r >= rr.y) continue;
-            const float2 Y = buf[(size_t)g * stride + pidx(mk_perm(r, L))];
-            float* a = S + row_off(ba, rr, r, pitch) + c0;
-            if (c0 + 1 < cols && (pitch & 1) == 0) {
-                *reinterpret_cast<float2*>(a) = make_float2(Y.x * invL, -Y.y * invL);
-            } else {
-                a[0] = Y.x * invL;
-                if (c0 + 1 < cols) a[1] = -Y.y * invL;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-
 // ---------------------------------------------------------------------------
 // Launchers for one FFT length
 // ---------------------------------------------------------------------------
@@ -814,17 +705,6 @@ cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int 
 }
 
 template <int LM>
-cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const float* sig2x,
-                           const BatchArgs& ba, int nbatch, cudaStream_t s) {
-    static std::once_flag once;
-    const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
-    std::call_once(once, [smem] { allow_dct_smem(dct_cols_solve_kernel<LM>, smem); });
-    const dim3 grid((cols + 1) / 2, nbatch);
-    return launch_pdl(dct_cols_solve_kernel<LM>, grid, dim3(fft_threads(pl.M)), smem, s, S, rows, cols, pitch, pl,
-                      sig2x, 1, ba);
-}
-
-template <int LM>
 cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                                int nbatch, int maxrows, cudaStream_t s) {
     static std::once_flag once;
@@ -839,8 +719,6 @@ cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const Dc
     template cudaError_t launch_bhat_lm<LM>(const DctPlan&, cudaStream_t);                                        \
     template cudaError_t launch_rows_fwd_lm<LM>(RowSource, float*, int, int, int, const DctPlan&,                  \
                                                 const RowSrcArgs&, const BatchArgs&, int, int, cudaStream_t);      \
-    template cudaError_t launch_cols_lm<LM>(float*, int, int, int, const DctPlan&, const float*, const BatchArgs&,  \
-                                            int, cudaStream_t);                                                   \
     template cudaError_t launch_rows_inv_lm<LM>(float*, int, int, int, const DctPlan&, const BatchArgs&, int, int, \
                                                 cudaStream_t);
 

@@ -23,6 +23,14 @@ struct BatchArgs {
     int packed;
 };
 
+// Row range [x, y) of this CTA's array (blockIdx.y) and the storage offset of row r.
+__device__ __forceinline__ int2 batch_rows(const BatchArgs& ba, int rows) {
+    return ba.ranges ? ba.ranges[blockIdx.y] : make_int2(0, rows);
+}
+__device__ __forceinline__ size_t row_off(const BatchArgs& ba, int2 rr, int r, int pitch) {
+    return (size_t)(ba.packed ? r - rr.x : r) * pitch;
+}
+
 
 template <int LM>
 cudaError_t launch_bhat_lm(const DctPlan& pl, cudaStream_t s);
@@ -30,11 +38,14 @@ template <int LM>
 cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int pitch, const DctPlan& pl,
                                const RowSrcArgs& sa, const BatchArgs& ba, int nbatch, int maxrows, cudaStream_t s);
 template <int LM>
-cudaError_t launch_cols_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const float* sig2x,
-                           const BatchArgs& ba, int nbatch, cudaStream_t s);
-template <int LM>
 cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                                int nbatch, int maxrows, cudaStream_t s);
+
+// Column pass of the Poisson pseudo-inverse as Neumann tridiagonal solves along
+// y (tri_solve.cu): S holds the row-transformed planes, sig2x the x-axis
+// sigma^2 table (length cols).
+cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float* sig2x, const BatchArgs& ba,
+                            int nbatch, cudaStream_t s);
 
 // Threads for a transform of length M: one per FFT unit (8 points up to 1024,
 // 16 beyond), two units per thread for the 16384-point transforms.

@@ -11,7 +11,7 @@
 
 namespace tvs {
 
-static const char* kNames[kProfClasses] = {"dct_rows_fwd",     "dct_cols_solve", "dct_rows_inv", "tfs_update",
+static const char* kNames[kProfClasses] = {"dct_rows_fwd",     "tri_cols_solve", "dct_rows_inv", "tfs_update",
                                            "irv1_update",      "schwarz_tile",   "schwarz_combine", "stencil_other",
                                            "tfs_check",        "irv1_check"};
 

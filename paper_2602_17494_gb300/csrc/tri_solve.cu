@@ -1,0 +1,264 @@
+// Column pass of the Neumann Poisson pseudo-inverse as tridiagonal solves
+// (eqs. form:DiscInvLapl, form:DiscInvLaplTild, Section 4.1).
+//
+// After the forward DCT along x (dct_rows_fwd), the pseudo-inverse acts on
+// column k_x of the spectrum as D'^{-1} Lambda(:, k_x) D' along y, with D' the
+// unnormalised DCT-II pair of length L = rows.  D' diagonalises the Neumann
+// second difference
+//   T = tridiag(-1, 2, -1) with 1 in both corners,  eigenvalues sigma_{R,k}^2,
+// so that operator is exactly
+//   -(T + lambda I)^{-1},  lambda = sigma_{C,k_x}^2 > 0        (k_x >= 1),
+//   -T^dagger (zero-mean input part dropped, zero-mean output) (k_x = 0).
+// Two more DCTs per column cost O(L log L) with Bluestein lengths 2L; the
+// system itself is solved here in O(L).  With r + 1/r = 2 + lambda, 0 < r < 1
+// and S the shift (S x)_i = x_{i-1},
+//   T + lambda I = r^{-1} (1 - r S)(1 - r S^{-1})
+// on the integers.  The Neumann rows are the interior rows applied to the
+// half-sample symmetric extension of b (period 2L), whose bounded solution
+// keeps that symmetry, so the two first-order recursions get closed-form
+// start values:
+//   c_i = b_i + r c_{i-1},  c_{-1} = sum_j b_j (r^j + r^{2L-1-j}) / (1 - r^{2L}),
+//   w_i = c_i + r w_{i+1},  w_{L-1} = c_{L-1} / (1 - r)   (from w_L = w_{L-1}),
+//   y = -r w.
+// For k_x = 0 (r = 1) the input loses its mean, c_{-1} = 0, w_L = 0 and the
+// output loses its mean.  1 - r is carried as q = (sqrt(lambda (4 + lambda))
+// - lambda) / 2, which has no cancellation, and every recursion step is
+// x + s - q s, so the solved system is the one for lambda up to rounding of q
+// even where r is within 1e-3 of 1.
+//
+// Parallel form: one CTA per column pair (the pair is one 8-byte access per
+// row), each thread N consecutive rows of both columns in registers.  The
+// recursions run over the N rows in registers; the chunk carries combine with
+// the constant multiplier r^N as Kogge-Stone scans within a warp and a short
+// serial pass over the warps' totals.  The start value c_{-1} and c_{L-1} come
+// from two block sums, so the whole solve needs two barriers (two more in the
+// CTA holding k_x = 0).
+#include "dct_launch.h"
+
+namespace tvs {
+namespace {
+
+constexpr int kTriThreads = 256;   // threads per CTA at most (rows per thread chosen to fit)
+constexpr int kTriWarps = kTriThreads / 32;
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// x + s - q s, one step of a recursion with r = 1 - q (nq = -q)
+__device__ __forceinline__ float2 rstep(float2 s, float2 x, float2 nq) { return fma2(nq, s, add2(s, x)); }
+// r^k of both columns from l2 = log2 r
+__device__ __forceinline__ float2 rpow(float2 l2, int k) {
+    const float kf = (float)k;
+    return f2(exp2f(kf * l2.x), exp2f(kf * l2.y));
+}
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d) {
+    return f2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int d) {
+    return f2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 warp_sum2(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = add2(v, f2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Removes the mean over rows [0, L) of the first column (the k_x = 0 column of
+// the CTA with blockIdx.x == 0).  Rows >= L stay zero.
+template <int N>
+__device__ __forceinline__ void remove_mean_x(float2 (&v)[N], int row0, int L, float* sh, int lane, int wid, int nw) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) s += v[i].x;
+    s = warp_sum(s);
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < nw; ++w) tot += sh[w];
+    const float mean = tot / (float)L;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (row0 + i < L) v[i].x -= mean;
+}
+
+// S: the row-transformed planes (in place); rows = L; sig2x[k] = sigma_{C,k}^2.
+// Batch mode as in the DCT kernels: blockIdx.y selects the array, rows outside
+// batch_rows() are zero on input and not written.
+template <int N>
+__global__ void __launch_bounds__(kTriThreads)
+tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const float* __restrict__ sig2x,
+                      const __grid_constant__ BatchArgs ba) {
+    __shared__ float2 sh_fwd[kTriWarps], sh_s1[kTriWarps], sh_r2[kTriWarps], sh_bwd[kTriWarps];
+    __shared__ float sh_m0[kTriWarps], sh_m1[kTriWarps];
+    pdl_wait();
+    pdl_trigger();
+    const int2 rr = batch_rows(ba, rows);
+    S += (size_t)blockIdx.y * ba.bstride;
+    const int L = rows;
+    const int c0 = 2 * blockIdx.x;
+    const bool has1 = c0 + 1 < cols;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int row0 = threadIdx.x * N;
+    const bool zero_mode = blockIdx.x == 0;  // column 0 is k_x = 0
+
+    const float lx = __ldg(&sig2x[c0]);
+    const float ly = has1 ? __ldg(&sig2x[c0 + 1]) : 1.f;
+    const float2 q = f2(0.5f * (sqrtf(lx * (4.f + lx)) - lx), 0.5f * (sqrtf(ly * (4.f + ly)) - ly));
+    const float2 nq = f2(-q.x, -q.y);
+    const float2 lr = f2(log1pf(-q.x), log1pf(-q.y));  // ln r
+    const float2 l2 = f2(lr.x * kLog2e, lr.y * kLog2e);
+
+    float2 v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int r = row0 + i;
+        float2 x = f2(0.f, 0.f);
+        if (r >= rr.x && r < rr.y) {
+            // with an even pitch the pair (c0, c0 + 1) is one 8-byte load; c0 + 1
+            // is inside the row's storage even when it is the padding column
+            const float* a = S + row_off(ba, rr, r, pitch) + c0;
+            if ((pitch & 1) == 0) x = *reinterpret_cast<const float2*>(a);
+            else x = f2(a[0], has1 ? a[1] : 0.f);
+        }
+        if (!has1) x.y = 0.f;
+        v[i] = x;
+    }
+    if (zero_mode) remove_mean_x<N>(v, row0, L, sh_m0, lane, wid, nw);
+
+    // sum_j b_j r^j over the chunk (Horner), then the causal recursion from zero
+    float2 h = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) h = rstep(h, v[i], nq);
+    const float2 s1 = mul2(rpow(l2, row0), h);
+    const int e = min(L - 1, row0 + N - 1);  // last row of the chunk (below row0 when the chunk is empty)
+    float2 p = f2(0.f, 0.f), a = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        p = rstep(p, v[i], nq);
+        if (row0 + i == e) a = p;
+        v[i] = row0 + i < L ? p : f2(0.f, 0.f);
+    }
+    // c0_{L-1} = sum over chunks of r^{L-1-e} a
+    const float2 r2 = mul2(rpow(l2, L - 1 - e), a);
+
+    // forward scan of the chunk carries within the warp (multiplier r^N)
+    const float2 m = rpow(l2, N);
+    float2 f = a, md = m;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float2 y = shfl_up2(f, d);
+        if (lane >= d) f = fma2(md, y, f);
+        md = mul2(md, md);
+    }
+    const float2 s1w = warp_sum2(s1), r2w = warp_sum2(r2);
+    if (lane == 31) sh_fwd[wid] = f;
+    if (lane == 0) {
+        sh_s1[wid] = s1w;
+        sh_r2[wid] = r2w;
+    }
+    __syncthreads();
+    const float2 m32 = rpow(l2, 32 * N);
+    float2 cw = f2(0.f, 0.f), S1 = f2(0.f, 0.f), R2 = f2(0.f, 0.f);
+    for (int w = 0; w < nw; ++w) {
+        if (w < wid) cw = fma2(m32, cw, sh_fwd[w]);
+        S1 = add2(S1, sh_s1[w]);
+        R2 = add2(R2, sh_r2[w]);
+    }
+    // start values: u0 = c_{-1}, cL = c_{L-1}, wL = w_L
+    const float2 rL = rpow(l2, L);
+    float2 u0 = f2(0.f, 0.f), wL = f2(0.f, 0.f);
+    if (q.x > 0.f) u0.x = -(S1.x + rL.x * R2.x) / expm1f((float)(2 * L) * lr.x);
+    if (q.y > 0.f) u0.y = -(S1.y + rL.y * R2.y) / expm1f((float)(2 * L) * lr.y);
+    const float2 cL = fma2(rL, u0, R2);
+    if (q.x > 0.f) wL.x = cL.x / q.x;
+    if (q.y > 0.f) wL.y = cL.y / q.y;
+
+    // true causal values: carry into the chunk = in-warp prefix + warp carry + u0
+    float2 fex = shfl_up2(f, 1);
+    if (lane == 0) fex = f2(0.f, 0.f);
+    p = fma2(rpow(l2, row0), u0, fma2(rpow(l2, lane * N), cw, fex));
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        p = fma2(nq, p, p);
+        if (row0 + i < L) v[i] = add2(v[i], p);
+    }
+
+    // anti-causal recursion from zero, then its scan (reversed, multiplier r^N)
+    p = f2(0.f, 0.f);
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        p = rstep(p, v[i], nq);
+        v[i] = p;
+    }
+    float2 g = v[0];
+    md = m;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float2 y = shfl_down2(g, d);
+        if (lane + d < 32) g = fma2(md, y, g);
+        md = mul2(md, md);
+    }
+    if (lane == 0) sh_bwd[wid] = g;
+    __syncthreads();
+    float2 cb = f2(0.f, 0.f);
+    for (int w = nw - 1; w > wid; --w) cb = fma2(m32, cb, sh_bwd[w]);
+    float2 gex = shfl_down2(g, 1);
+    if (lane == 31) gex = f2(0.f, 0.f);
+    // carry into the chunk from the right: w at row min(L, row0 + N)
+    p = fma2(rpow(l2, L - min(L, row0 + N)), wL, fma2(rpow(l2, (31 - lane) * N), cb, gex));
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        if (row0 + i < L) {
+            p = fma2(nq, p, p);
+            v[i] = add2(v[i], p);
+        }
+    }
+    if (zero_mode) remove_mean_x<N>(v, row0, L, sh_m1, lane, wid, nw);
+
+    // y = -r w = q w - w
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int r = row0 + i;
+        if (r < rr.x || r >= rr.y) continue;
+        const float2 y = fma2(q, v[i], f2(-v[i].x, -v[i].y));
+        float* o = S + row_off(ba, rr, r, pitch) + c0;
+        if (has1 && (pitch & 1) == 0) {
+            *reinterpret_cast<float2*>(o) = y;
+        } else {
+            o[0] = y.x;
+            if (has1) o[1] = y.y;
+        }
+    }
+}
+
+template <int N>
+cudaError_t launch_n(float* S, int rows, int cols, int pitch, const float* sig2x, const BatchArgs& ba, int nbatch,
+                     cudaStream_t s) {
+    const int threads = round_up((rows + N - 1) / N, 32);
+    return launch_pdl(tri_cols_solve_kernel<N>, dim3((cols + 1) / 2, nbatch), dim3(threads), 0, s, S, rows, cols,
+                      pitch, sig2x, ba);
+}
+
+}  // namespace
+
+cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float* sig2x, const BatchArgs& ba,
+                            int nbatch, cudaStream_t s) {
+    // fewest rows per thread that keep the CTA within kTriThreads
+    if (rows < 1 || cols < 1) return cudaErrorInvalidValue;
+    if (rows <= 3 * kTriThreads) return launch_n<3>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
+    if (rows <= 5 * kTriThreads) return launch_n<5>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
+    if (rows <= 9 * kTriThreads) return launch_n<9>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
+    if (rows <= 17 * kTriThreads) return launch_n<17>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
+    if (rows <= 33 * kTriThreads) return launch_n<33>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tvs

@@ -120,10 +120,9 @@ cudaError_t build_plan(const DctPlan& pl, cudaStream_t s);
 // Poisson / projection machinery on a rows x cols grid (pitch in floats).
 //   s_to_phi: in place, S <- Delta^dagger S (Neumann, min-norm).
 struct PoissonPlans {
-    DctPlan row;   // length cols (x transforms)
-    DctPlan col;   // length rows (y transforms)
+    DctPlan row;   // length cols (x transforms; the y pass is a tridiagonal solve and needs no plan)
 };
-void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols);
+void carve_poisson(Carver& cv, PoissonPlans& pp, int cols);
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s);
 
 // Source functors for the fused forward row transform.
