@@ -28,7 +28,7 @@ size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
     L.C = n1 + 1;
     L.P = round_up(L.C, kPitchAlign);
     L.plane = (long)L.R * L.P;
-    carve_poisson(cv, L.pp, L.C);
+    carve_poisson(cv, L.pp, L.R, L.C);
     L.pa = cv.take<float>(4 * (size_t)L.plane);
     L.pb = cv.take<float>(4 * (size_t)L.plane);
     L.f1 = cv.take<float>(2 * (size_t)L.plane);
@@ -55,7 +55,7 @@ size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int storage) {
 size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
     L.P = round_up(cols, kPitchAlign);
     L.plane = (long)rows * L.P;
-    carve_poisson(cv, L.pp, cols);
+    carve_poisson(cv, L.pp, rows, cols);
     L.u = cv.take<float>(2 * (size_t)L.plane);
     L.S = cv.take<float>((size_t)L.plane);
     return cv.used();
@@ -208,6 +208,7 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             key.add(1).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.S).ptr(L.f1).add((uint64_t)L.R).add((uint64_t)L.C)
                 .add((uint64_t)L.P).add((uint64_t)L.plane).num(t).num(fd).ptr(L.red.partial).ptr(L.red.err);
             key_plan(key, L.pp.row);
+            key.add((uint64_t)L.pp.rows).ptr(L.pp.tri);
             TVS_CUDA(graph_run(key, s, [&](cudaStream_t st) { return tfs_iters(L, cur, nxt, run, t, fd, st); }));
             n += run;
             continue;

@@ -88,12 +88,16 @@ cudaError_t build_plan(const DctPlan& pl, cudaStream_t s) {
     return e;
 }
 
-void carve_poisson(Carver& cv, PoissonPlans& pp, int cols) {
+void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols) {
     carve_plan(cv, pp.row, cols);
+    pp.rows = rows;
+    pp.tri = cv.take<float4>(2 * (size_t)cols);
 }
 
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s) {
-    return build_plan(pp.row, s);
+    const cudaError_t e = build_plan(pp.row, s);
+    if (e != cudaSuccess) return e;
+    return build_tri_table(pp.tri, pp.rows, pp.row.L, s);
 }
 
 // --------------------------------------------------------------------------
@@ -104,7 +108,7 @@ cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s) {
 static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const PoissonPlans& pp, RowSource src,
                                   const RowSrcArgs& sa, int nbatch, const int2* ranges, long bstride, int maxrows,
                                   int packed, cudaStream_t s) {
-    if (pp.row.logM < kMinLogM || pp.row.logM > kMaxLogM)
+    if (pp.row.logM < kMinLogM || pp.row.logM > kMaxLogM || rows != pp.rows || cols != pp.row.L)
         return cudaErrorInvalidValue;
     const BatchArgs ba{ranges, bstride, packed};
     cudaError_t e = cudaErrorInvalidValue;
@@ -117,7 +121,7 @@ static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const
     e = cudaErrorInvalidValue;
     {
         ProfScope ps(kProfCols, s);
-        e = launch_tri_cols(S, rows, cols, pitch, pp.row.sig2, ba, nbatch, s);
+        e = launch_tri_cols(S, rows, cols, pitch, pp.tri, ba, nbatch, s);
     }
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;

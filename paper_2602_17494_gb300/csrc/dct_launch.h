@@ -42,10 +42,11 @@ cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const Dc
                                int nbatch, int maxrows, cudaStream_t s);
 
 // Column pass of the Poisson pseudo-inverse as Neumann tridiagonal solves along
-// y (tri_solve.cu): S holds the row-transformed planes, sig2x the x-axis
-// sigma^2 table (length cols).
-cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float* sig2x, const BatchArgs& ba,
+// y (tri_solve.cu): S holds the row-transformed planes; tab the per-column
+// coefficients written by build_tri_table for the same rows and cols.
+cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float4* tab, const BatchArgs& ba,
                             int nbatch, cudaStream_t s);
+cudaError_t build_tri_table(float4* tab, int rows, int cols, cudaStream_t s);
 
 // Threads for a transform of length M: one per FFT unit (8 points up to 1024,
 // 16 beyond), two units per thread for the 16384-point transforms.

@@ -27,7 +27,7 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 size_t noalloc_need(int rows, int cols) {
     Carver cv(nullptr);
     PoissonPlans pp;
-    carve_poisson(cv, pp, cols);
+    carve_poisson(cv, pp, rows, cols);
     cv.take<float>((size_t)rows * cols);
     return cv.used();
 }
@@ -69,7 +69,7 @@ extern "C" tvs_status tvs_project_noalloc(const float* in, float* out, int rows,
     }
     Carver cv(base);
     PoissonPlans pp;
-    carve_poisson(cv, pp, cols);
+    carve_poisson(cv, pp, rows, cols);
     float* S = cv.take<float>((size_t)rows * cols);
     // Every scratch word read below is written first in this call (tables,
     // then all rows of S), so nothing from an earlier call needs clearing.

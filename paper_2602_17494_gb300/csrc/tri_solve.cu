@@ -24,7 +24,8 @@
 // output loses its mean.  1 - r is carried as q = (sqrt(lambda (4 + lambda))
 // - lambda) / 2, which has no cancellation, and every recursion step is
 // x + s - q s, so the solved system is the one for lambda up to rounding of q
-// even where r is within 1e-3 of 1.
+// even where r is within 1e-3 of 1.  q and the powers of r that do not depend
+// on the thread come from a per-column table built in FP64 with the plan.
 //
 // Parallel form: one CTA per column pair (the pair is one 8-byte access per
 // row), each thread N consecutive rows of both columns in registers.  The
@@ -40,7 +41,6 @@ namespace {
 
 constexpr int kTriThreads = 256;   // threads per CTA at most (rows per thread chosen to fit)
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -89,12 +89,12 @@ __device__ __forceinline__ void remove_mean_x(float2 (&v)[N], int row0, int L, f
         if (row0 + i < L) v[i].x -= mean;
 }
 
-// S: the row-transformed planes (in place); rows = L; sig2x[k] = sigma_{C,k}^2.
+// S: the row-transformed planes (in place); rows = L; tab: build_tri_table(rows, cols).
 // Batch mode as in the DCT kernels: blockIdx.y selects the array, rows outside
 // batch_rows() are zero on input and not written.
 template <int N>
 __global__ void __launch_bounds__(kTriThreads)
-tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const float* __restrict__ sig2x,
+tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, const float4* __restrict__ tab,
                       const __grid_constant__ BatchArgs ba) {
     __shared__ float2 sh_fwd[kTriWarps], sh_s1[kTriWarps], sh_r2[kTriWarps], sh_bwd[kTriWarps];
     __shared__ float sh_m0[kTriWarps], sh_m1[kTriWarps];
@@ -109,12 +109,16 @@ tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
     const int row0 = threadIdx.x * N;
     const bool zero_mode = blockIdx.x == 0;  // column 0 is k_x = 0
 
-    const float lx = __ldg(&sig2x[c0]);
-    const float ly = has1 ? __ldg(&sig2x[c0 + 1]) : 1.f;
-    const float2 q = f2(0.5f * (sqrtf(lx * (4.f + lx)) - lx), 0.5f * (sqrtf(ly * (4.f + ly)) - ly));
-    const float2 nq = f2(-q.x, -q.y);
-    const float2 lr = f2(log1pf(-q.x), log1pf(-q.y));  // ln r
-    const float2 l2 = f2(lr.x * kLog2e, lr.y * kLog2e);
+    // per-column coefficients (a missing second column reuses the first's)
+    const float4 a0 = __ldg(&tab[2 * c0]), b0 = __ldg(&tab[2 * c0 + 1]);
+    const float4 a1 = has1 ? __ldg(&tab[2 * c0 + 2]) : a0, b1 = has1 ? __ldg(&tab[2 * c0 + 3]) : b0;
+    const float2 q = f2(a0.x, a1.x), nq = f2(-a0.x, -a1.x);
+    const float2 l2 = f2(a0.y, a1.y);   // log2 r
+    const float2 m = f2(a0.z, a1.z);    // r^N
+    const float2 m32 = f2(a0.w, a1.w);  // r^(32 N)
+    const float2 rL = f2(b0.x, b1.x);   // r^L
+    const float2 dnm = f2(b0.y, b1.y);  // 1 / (1 - r^(2L)), 0 for k_x = 0
+    const float2 iq = f2(b0.z, b1.z);   // 1 / q, 0 for k_x = 0
 
     float2 v[N];
 #pragma unroll
@@ -139,6 +143,8 @@ tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
     for (int i = N - 1; i >= 0; --i) h = rstep(h, v[i], nq);
     const float2 s1 = mul2(rpow(l2, row0), h);
     const int e = min(L - 1, row0 + N - 1);  // last row of the chunk (below row0 when the chunk is empty)
+    // r^(L-1-e) = r^(L - min(L, row0 + N)): from the chunk's end to row L - 1, and from row L to the chunk's end
+    const float2 rt = rpow(l2, L - min(L, row0 + N));
     float2 p = f2(0.f, 0.f), a = f2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -147,10 +153,9 @@ tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
         v[i] = row0 + i < L ? p : f2(0.f, 0.f);
     }
     // c0_{L-1} = sum over chunks of r^{L-1-e} a
-    const float2 r2 = mul2(rpow(l2, L - 1 - e), a);
+    const float2 r2 = mul2(rt, a);
 
     // forward scan of the chunk carries within the warp (multiplier r^N)
-    const float2 m = rpow(l2, N);
     float2 f = a, md = m;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -165,21 +170,16 @@ tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
         sh_r2[wid] = r2w;
     }
     __syncthreads();
-    const float2 m32 = rpow(l2, 32 * N);
     float2 cw = f2(0.f, 0.f), S1 = f2(0.f, 0.f), R2 = f2(0.f, 0.f);
     for (int w = 0; w < nw; ++w) {
         if (w < wid) cw = fma2(m32, cw, sh_fwd[w]);
         S1 = add2(S1, sh_s1[w]);
         R2 = add2(R2, sh_r2[w]);
     }
-    // start values: u0 = c_{-1}, cL = c_{L-1}, wL = w_L
-    const float2 rL = rpow(l2, L);
-    float2 u0 = f2(0.f, 0.f), wL = f2(0.f, 0.f);
-    if (q.x > 0.f) u0.x = -(S1.x + rL.x * R2.x) / expm1f((float)(2 * L) * lr.x);
-    if (q.y > 0.f) u0.y = -(S1.y + rL.y * R2.y) / expm1f((float)(2 * L) * lr.y);
+    // start values: u0 = c_{-1}, cL = c_{L-1}, wL = w_L (all zero for k_x = 0)
+    const float2 u0 = mul2(fma2(rL, R2, S1), dnm);
     const float2 cL = fma2(rL, u0, R2);
-    if (q.x > 0.f) wL.x = cL.x / q.x;
-    if (q.y > 0.f) wL.y = cL.y / q.y;
+    const float2 wL = mul2(cL, iq);
 
     // true causal values: carry into the chunk = in-warp prefix + warp carry + u0
     float2 fex = shfl_up2(f, 1);
@@ -213,7 +213,7 @@ tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
     float2 gex = shfl_down2(g, 1);
     if (lane == 31) gex = f2(0.f, 0.f);
     // carry into the chunk from the right: w at row min(L, row0 + N)
-    p = fma2(rpow(l2, L - min(L, row0 + N)), wL, fma2(rpow(l2, (31 - lane) * N), cb, gex));
+    p = fma2(rt, wL, fma2(rpow(l2, (31 - lane) * N), cb, gex));
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
         if (row0 + i < L) {
@@ -239,26 +239,65 @@ tri_cols_solve_kernel(float* __restrict__ S, int rows, int cols, int pitch, cons
     }
 }
 
+// Per-column coefficients in FP64 for a column pass of `rows` rows over
+// `cols` x frequencies (lambda = sigma_{C,k}^2 = 4 sin^2(pi k / (2 cols))):
+//   tab[2k]     = (q, log2 r, r^N, r^(32 N)),
+//   tab[2k + 1] = (r^rows, 1 / (1 - r^(2 rows)), 1 / q, 0),
+// with k = 0 stored as r = 1 and both start-value factors zero.
+__global__ void tri_table_kernel(float4* __restrict__ tab, int rows, int cols, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cols) return;
+    if (k == 0) {
+        tab[0] = make_float4(0.f, 0.f, 1.f, 1.f);
+        tab[1] = make_float4(1.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    double sn, cs;
+    sincospi((double)k / (2.0 * (double)cols), &sn, &cs);
+    const double lam = 4.0 * sn * sn;
+    const double q = 0.5 * (sqrt(lam * (4.0 + lam)) - lam);
+    const double lr = log1p(-q);  // ln r
+    tab[2 * k] = make_float4((float)q, (float)(lr / 0.69314718055994531), (float)exp((double)N * lr),
+                             (float)exp(32.0 * (double)N * lr));
+    tab[2 * k + 1] = make_float4((float)exp((double)rows * lr), (float)(-1.0 / expm1(2.0 * (double)rows * lr)),
+                                 (float)(1.0 / q), 0.f);
+}
+
+// Rows per thread: the fewest that keep the CTA within kTriThreads (0: too long).
+int rows_per_thread(int rows) {
+    for (int n : {3, 5, 9, 17, 33})
+        if (rows <= n * kTriThreads) return n;
+    return 0;
+}
+
 template <int N>
-cudaError_t launch_n(float* S, int rows, int cols, int pitch, const float* sig2x, const BatchArgs& ba, int nbatch,
+cudaError_t launch_n(float* S, int rows, int cols, int pitch, const float4* tab, const BatchArgs& ba, int nbatch,
                      cudaStream_t s) {
     const int threads = round_up((rows + N - 1) / N, 32);
     return launch_pdl(tri_cols_solve_kernel<N>, dim3((cols + 1) / 2, nbatch), dim3(threads), 0, s, S, rows, cols,
-                      pitch, sig2x, ba);
+                      pitch, tab, ba);
 }
 
 }  // namespace
 
-cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float* sig2x, const BatchArgs& ba,
+cudaError_t build_tri_table(float4* tab, int rows, int cols, cudaStream_t s) {
+    const int n = rows_per_thread(rows);
+    if (n == 0 || cols < 1) return cudaErrorInvalidValue;
+    tri_table_kernel<<<(cols + 127) / 128, 128, 0, s>>>(tab, rows, cols, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float4* tab, const BatchArgs& ba,
                             int nbatch, cudaStream_t s) {
-    // fewest rows per thread that keep the CTA within kTriThreads
-    if (rows < 1 || cols < 1) return cudaErrorInvalidValue;
-    if (rows <= 3 * kTriThreads) return launch_n<3>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
-    if (rows <= 5 * kTriThreads) return launch_n<5>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
-    if (rows <= 9 * kTriThreads) return launch_n<9>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
-    if (rows <= 17 * kTriThreads) return launch_n<17>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
-    if (rows <= 33 * kTriThreads) return launch_n<33>(S, rows, cols, pitch, sig2x, ba, nbatch, s);
-    return cudaErrorInvalidValue;
+    if (cols < 1) return cudaErrorInvalidValue;
+    switch (rows_per_thread(rows)) {
+        case 3: return launch_n<3>(S, rows, cols, pitch, tab, ba, nbatch, s);
+        case 5: return launch_n<5>(S, rows, cols, pitch, tab, ba, nbatch, s);
+        case 9: return launch_n<9>(S, rows, cols, pitch, tab, ba, nbatch, s);
+        case 17: return launch_n<17>(S, rows, cols, pitch, tab, ba, nbatch, s);
+        case 33: return launch_n<33>(S, rows, cols, pitch, tab, ba, nbatch, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace tvs

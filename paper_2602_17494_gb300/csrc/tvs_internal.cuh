@@ -120,9 +120,11 @@ cudaError_t build_plan(const DctPlan& pl, cudaStream_t s);
 // Poisson / projection machinery on a rows x cols grid (pitch in floats).
 //   s_to_phi: in place, S <- Delta^dagger S (Neumann, min-norm).
 struct PoissonPlans {
-    DctPlan row;   // length cols (x transforms; the y pass is a tridiagonal solve and needs no plan)
+    DctPlan row;         // length cols (x transforms)
+    int rows = 0;        // y length; the y pass is a tridiagonal solve per column
+    float4* tri = nullptr;  // its per-column coefficients, two float4 per column (tri_solve.cu)
 };
-void carve_poisson(Carver& cv, PoissonPlans& pp, int cols);
+void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols);
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s);
 
 // Source functors for the fused forward row transform.

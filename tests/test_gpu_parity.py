@@ -48,7 +48,10 @@ def rel(a, b):
 # ---------------------------------------------------------------------------
 # the divergence-free projection
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("shape", [(3, 3), (3, 17), (9, 14), (65, 65), (66, 131), (257, 130), (1025, 1025)])
+# (2049, 70), (4097, 33), (8193, 24): long columns, 9, 17 and 33 rows per thread in the
+# tridiagonal column pass; (24, 8193): 16384-point Bluestein row transforms
+@pytest.mark.parametrize("shape", [(3, 3), (3, 17), (9, 14), (65, 65), (66, 131), (257, 130), (1025, 1025),
+                                   (2049, 70), (4097, 33), (8193, 24), (24, 8193)])
 def test_projection_matches_oracle(B, shape):
     rng = np.random.default_rng(sum(shape))
     tau = rng.standard_normal((2,) + shape)
