@@ -318,7 +318,7 @@ def run_gpu(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
     # capture of the current kernel at this workload; the 1025^2 grid stays in L2
-    traffic = {"dct_rows_fwd": 4418560.0, "dct_rows_inv": 4415488.0, "tri_cols_solve": 4355584.0}.get(name) if N == 1024 else None
+    traffic = {"dct_rows_fwd": 4418560.0, "dct_rows_inv": 4415488.0, "tri_cols_solve": 4380928.0}.get(name) if N == 1024 else None
     roof.update({"frac": achieved / peak, "traffic": traffic, "kernel": name,
                  "avg_launch_us": avg_s * 1e6, "launches_per_step": nl // args.steps})
 

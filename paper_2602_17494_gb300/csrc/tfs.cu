@@ -88,6 +88,35 @@ __device__ __forceinline__ bool tile_load(uint64_t* bar, uint32_t bytes, float* 
     return false;
 }
 
+// tile_load for the TFS update under programmatic dependent launch: the boxes
+// of p and f1 (written two or more launches earlier, so complete once this
+// grid may start) are issued before griddepcontrol.wait and overlap the tail
+// of the previous kernel; the box of phi, which the previous launch writes,
+// is issued after it.
+__device__ __forceinline__ bool tile_load_early(uint64_t* bar, uint32_t bytes, float* sp, const CUtensorMap* mp,
+                                                float* sphi, const CUtensorMap* mphi, float* sf,
+                                                const CUtensorMap* mf, int x, int y, unsigned* err) {
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    if (lead) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        mbar_expect_tx(bar, bytes);
+        tma_load_3d(sp, mp, x, y, 0, bar);
+        tma_load_3d(sf, mf, x, y, 0, bar);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (lead) tma_load_2d(sphi, mphi, x, y, bar);
+    __syncthreads();
+    const bool ok = mbar_wait(bar, 0);
+    if (__syncthreads_and(ok)) return true;
+    if (lead) {
+        atomicOr(err, 1u);
+        (void)mbar_wait(bar, 0);
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // tau0 (Neumann backward differences onto the extended grid)
 // ---------------------------------------------------------------------------
@@ -230,8 +259,9 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
                   const __grid_constant__ CUtensorMap fmap, float* __restrict__ pout, int R, int C, int pitch,
                   long plane, float t, float delta, float* __restrict__ tau_out, int tau_pitch, long tau_plane,
                   double* __restrict__ partial, unsigned* __restrict__ err) {
-    pdl_wait();
-    pdl_trigger();
+    // every caller launches this right after the Poisson solve that writes phi
+    // (four launches that read p and write only phi's plane and the error word),
+    // so p and f1 may be read before griddepcontrol.wait (tile_load_early)
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
     float* sphi = sp + 4 * kBoxFloats;             // [BH][BW]
@@ -242,7 +272,7 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
     const int tid = ty * kTX + tx;
     constexpr int NT = kTX * kBY;
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
-    if (!tile_load(bar, 7 * kBoxFloats * 4, sp, &pmap, sphi, &phimap, sf, &fmap, j0 - kBoxC, i0 - kBoxR, err))
+    if (!tile_load_early(bar, 7 * kBoxFloats * 4, sp, &pmap, sphi, &phimap, sf, &fmap, j0 - kBoxC, i0 - kBoxR, err))
         return;
     // box offsets of grid point (i, j)
     auto B = [&](int i, int j) -> int { return (i - i0 + kBoxR) * kBW + (j - j0 + kBoxC); };
