@@ -731,6 +731,18 @@ struct QNeighbours {
 // it; their extents come from shared memory, computed once per CTA.
 constexpr int kStripThreads = 128;
 
+// SMs of the current device (queried once per device and thread).
+static int sm_count() {
+    thread_local int dev = -1, n = 0;
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return 152;
+    if (d != dev) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 152;
+        dev = d;
+    }
+    return n;
+}
+
 // p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum_l q_l on up to NB pixels of
 // one column (rows i, i + di, ...): every load is issued before the first
 // store, so a thread keeps NB pixels' loads in flight.
@@ -820,13 +832,17 @@ schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     const int cy0 = ay.core(my);
     const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
     // horizontal band: s rows x this chunk's share of the core's columns;
-    // a thread takes one column and up to 4 rows at a time
+    // one item is one column and up to NB rows, spread over all threads
     if (my > 0 && ay.s > 0) {
+        constexpr int NB = StripCombine<S>::NB;
         const int W = cx1 - cx0;
         const int j0 = cx0 + (int)((long long)W * ch / nch), j1 = cx0 + (int)((long long)W * (ch + 1) / nch);
         const int i0 = cy0 - (ay.s + 1) / 2;
-        for (int j = j0 + t; j < j1; j += kStripThreads)
-            for (int r = 0; r < ay.s; r += StripCombine<S>::NB) cb.run(nby, nbx, i0 + r, 1, ay.s - r, j);
+        const int wc = j1 - j0, items = wc * ((ay.s + NB - 1) / NB);
+        for (int it = t; it < items; it += kStripThreads) {
+            const int g = it / wc, r = g * NB, j = j0 + (it - g * wc);
+            cb.run(nby, nbx, i0 + r, 1, ay.s - r, j);
+        }
     }
     // vertical band: this chunk's share of the exclusive rows x s columns;
     // a thread takes one column and up to 4 rows (rstep apart) at a time
@@ -1095,9 +1111,11 @@ static cudaError_t schwarz2_iterate_t(S** cur, S** nxt, const float* f2, int pit
     const int nsub = st.m2 * st.m1;
     const int hcore = (n2 + st.m2 - 1) / st.m2 + 1;
     const int chunks = std::max(1, std::min(64, hcore / 16));
-    // overlap-band pixels per subdomain, about s (core height + core width); ~512 per strip CTA
+    // overlap-band pixels per subdomain, about s (core height + core width); ~512 per strip CTA,
+    // and at least two strip CTAs per SM when there are few subdomains
     const int wcore = (n1 + st.m1 - 1) / st.m1 + 1;
-    const int strip_chunks = std::max(1, std::min(64, st.s * (hcore + wcore) / 512));
+    const int strip_chunks =
+        std::max(1, std::min(64, std::max(st.s * (hcore + wcore) / 512, (2 * sm_count() + nsub - 1) / nsub)));
     const float ah = (float)st.alpha_hat;
     S* q = static_cast<S*>(st.q);
     for (int n = 0; n < n_outer; ++n) {
