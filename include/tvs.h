@@ -7,7 +7,9 @@
  *   step 1 (tangent field smoothing, TFS): the dual problem eq. tfsdualdis on
  *          the extended grid, solved by Chambolle's semi-implicit iteration
  *          (Algorithm 1) with the divergence-free projection P_K
- *          (eq. formula:PKh, evaluated through the DCT, eq. form:DiscInvLapl);
+ *          (eq. formula:PKh; Delta^dagger of eq. form:DiscInvLapl evaluated as a
+ *          DCT along x and one Neumann tridiagonal solve per x frequency along y,
+ *          the same operator up to rounding);
  *   step 2 (image reconstruction IRV1): the dual problem eq. ir1dualdis on the
  *          image grid with the normal field xi of eq. defXi2:discrete.
  * Both may also run under the overlapping Schwarz decomposition of
@@ -120,8 +122,9 @@ const char* tvs_last_error(void);
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage);
 
 /* Divergence-free projection P_K = I - grad Delta^dagger div on a grid of
- * `rows` x `cols` points (eq. formula:PKh, Appendix B), with Delta^dagger by
- * the 2-D DCT (eqs. form:DiscInvLapl, form:DiscInvLaplTild).
+ * `rows` x `cols` points (eq. formula:PKh, Appendix B), with Delta^dagger of
+ * eqs. form:DiscInvLapl, form:DiscInvLaplTild (DCT along x, tridiagonal solves
+ * along y).
  *   in   : 2 planes rows x cols (x-part, y-part); out: same layout; in == out allowed.
  *   rows, cols >= 3.  ws: tvs_workspace_bytes(3, rows-1, cols-1, NULL, 0). */
 tvs_status tvs_project(const float* in, float* out, int rows, int cols,
