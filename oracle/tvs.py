@@ -24,8 +24,15 @@ Readings of the paper taken here (each stated where it is used):
 
 Parity: pinned by invariants (adjointness, projection, feasibility,
 monotone dual energy, gap identity, gap -> 0), by special cases (constant
-image is a fixed point; xi = 0 reduces IRV1 to Chambolle's ROF iteration) and
-by brute-force dense solves on 8x8 images (tests/test_oracle_tvs.py).
+image is a fixed point; xi = 0 reduces IRV1 to Chambolle's ROF iteration;
+IRV2 with the noisy image's own tangent field returns the image), by
+hand-derived values of xi, div xi and f_2 on a 2x3 image, by the identity
+that the normal field of tau_0 is the eps-normalised backward gradient of
+d_0, by brute-force dense solves on 8x8 images (FISTA, a different
+algorithm, on the explicit matrices; for W^{1,1} on the shifted ball
+|p - xi| <= 1 straight from eq. IRW11:dual) and, for the IRV2 potential, by
+exact recovery of a known potential and numpy's least-squares solve
+(tests/test_oracle_tvs.py, tests/test_oracle_irv2.py).
 """
 from __future__ import annotations
 
@@ -227,6 +234,84 @@ def irv1(f2: np.ndarray, alpha: float, t: float = 0.125, iters: int = 300,
     rep = irv1_report(f2, p, alpha, n)
     rep.history = hist
     return irv1_image(f2, p, alpha), p, rep
+
+
+# --------------------------------------------------------------------------
+# W^{1,1} variant of step 2 (Remark IRPW11, eq. IRW11:dual)
+# --------------------------------------------------------------------------
+
+
+def w11(d0: np.ndarray, xi: np.ndarray, alpha: float, t: float = 0.125, iters: int = 300,
+        p0: np.ndarray | None = None, rel_gap_tol: float = 0.0, check_every: int = 0):
+    """Dual eq. IRW11:dual, min ||div p - alpha d0||^2 over |p - xi| <= 1.
+
+    Reading: with q = p - xi the problem is eq. IRPXi_dual / ir1dualdis
+    (``||div q - (alpha d0 - div xi)||^2`` over |q| <= 1), so Chambolle's
+    iteration runs on q exactly as for IRV1 and p = q + xi.  Both give
+    ``d = d0 - div p / alpha`` (the first optimality condition of the
+    proposition after eq. IRW11:dual).  ``p0`` is a warm start of p.
+    Returns (d, p, report); the report is the IRV1 report of q.
+    """
+    f2 = irv1_data(d0, xi, alpha)
+    q0 = None if p0 is None else p0 - xi
+    d, q, rep = irv1(f2, alpha, t, iters, q0, rel_gap_tol, check_every)
+    return d, q + xi, rep
+
+
+# --------------------------------------------------------------------------
+# IRV2, the alternative step 2 (Section 3.3: eqs. modifiedStep2,
+# modifiedStep2_2, modifiedStep2_2_dual; discrete eq. ir2dualdis)
+# --------------------------------------------------------------------------
+
+
+def potential(tau: np.ndarray, n2: int, n1: int) -> np.ndarray:
+    """Image g with grad g = tau_perp, tau_perp = R_Omega(tau_2, -tau_1).
+
+    The paper asks for (D^-_x g, D^-_y g) = tau_perp on the image grid.  The
+    backward differences between neighbouring image pixels are the equations
+        g[i, j] - g[i, j-1] = tau_2[i, j]     (1 <= j <= N1-1),
+        g[i, j] - g[i-1, j] = -tau_1[i, j]    (1 <= i <= N2-1),
+    which are consistent exactly when div tau = D^-_x tau_1 + D^-_y tau_2
+    vanishes at the extended-grid points 1 <= i <= N2-1, 1 <= j <= N1-1
+    (the paper's condition div tau = 0).  The rows of D^- at
+    the first and last index (zero extension) are not consistent in general,
+    so, reading: g is the least-squares solution of the pixel-difference
+    equations above, fixed to mean zero.  These equations are
+    grad g = v with the forward-edge field v_x[i, j] = tau_2[i, j+1],
+    v_y[i, j] = -tau_1[i+1, j] (zero in the last column / row, where grad has
+    no equation), so the least-squares g solves the normal equations
+    div grad g = div v, i.e. g = Delta^dagger div v on the N2 x N1 grid
+    (eq. form:DiscInvLapl on that grid; the paper constructs g "with the help
+    of the Fourier transform").  Where an exact potential exists this is it,
+    up to the constant, which cancels in d (see ``irv2``).
+    """
+    a = tau[1][:n2, :n1]
+    b = -tau[0][:n2, :n1]
+    v = np.zeros((2, n2, n1))
+    v[0][:, :-1] = a[:, 1:]
+    v[1][:-1, :] = b[1:, :]
+    return ops.inv_lap(ops.div(v))
+
+
+def irv2_data(d0: np.ndarray, g: np.ndarray, alpha: float) -> np.ndarray:
+    """f = alpha (d_0 - g), the data of eq. ir2dualdis."""
+    return alpha * (d0 - g)
+
+
+def irv2(d0: np.ndarray, tau: np.ndarray, alpha: float, t: float = 0.125, iters: int = 300,
+         p0: np.ndarray | None = None, rel_gap_tol: float = 0.0, check_every: int = 0):
+    """IRV2: g from tau, the ROF problem eq. modifiedStep2_2 in u = d - g by
+    Chambolle's iteration on its dual eq. ir2dualdis, then d = u + g.
+
+    A constant added to g shifts d_0 - g and u by opposite amounts and leaves
+    d (and p) unchanged.  Returns (d, p, report, g); the report is that of
+    the ROF problem in u (beta = alpha, data d_0 - g).
+    """
+    n2, n1 = d0.shape
+    g = potential(tau, n2, n1)
+    f = irv2_data(d0, g, alpha)
+    u, p, rep = irv1(f, alpha, t, iters, p0, rel_gap_tol, check_every)
+    return u + g, p, rep, g
 
 
 # --------------------------------------------------------------------------
