@@ -115,10 +115,11 @@ const char* tvs_last_error(void);
 
 /* Bytes of scratch needed by a call.
  *   step = 1: tvs_step1 / tvs_schwarz(step=1); step = 2: tvs_step2 /
- *   tvs_schwarz(step=2); step = 0: tvs_denoise (covers both); step = 3:
- *   tvs_project; step = 4: tvs_quality.  dd = NULL means the global iteration.  storage: the
- *   tvs_iter.storage of the (step-2) call.  Returns 0 for invalid sizes or
- *   a storage the step does not support. */
+ *   tvs_schwarz(step=2) / tvs_step2_w11; step = 0: tvs_denoise (covers
+ *   both); step = 3: tvs_project; step = 4: tvs_quality; step = 5: tvs_irv2.
+ *   dd = NULL means the global iteration.  storage: the tvs_iter.storage of
+ *   the (step-2) call.  Returns 0 for invalid sizes or a storage the step
+ *   does not support. */
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage);
 
 /* Divergence-free projection P_K = I - grad Delta^dagger div on a grid of
@@ -141,10 +142,12 @@ tvs_status tvs_project(const float* in, float* out, int rows, int cols,
  *             on every GPU that loads the library until the process exits.
  *             Larger grids return TVS_ERR_UNSUPPORTED with a message in
  *             tvs_last_error().
- *   The first call on a device looks up that array's device address; make
- *   that first call before any stream capture.  All calls share the one
- *   array, so calls whose GPU work overlaps (other streams, other host
- *   threads) race; serialize them on one stream.  Allocates nothing. */
+ *   Every call looks up that array's device address on the current device
+ *   (a host-side query; the first one on a device loads the library's device
+ *   code there, so make that first call before any stream capture).  All
+ *   calls share the one array, so calls whose GPU work overlaps (other
+ *   streams, other host threads) race; serialize them on one stream.
+ *   Allocates nothing. */
 tvs_status tvs_project_noalloc(const float* in, float* out, int rows, int cols, cudaStream_t stream);
 
 /* Step 1, TFS (Section 4.2, eq. tfsdualdis, Algorithm 1 with the projected
@@ -165,6 +168,41 @@ tvs_status tvs_step1(const float* d0, int n2, int n1, double delta, const tvs_it
 tvs_status tvs_step2(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
                      const tvs_iter* it, float* d, float* p, void* ws, size_t ws_bytes,
                      cudaStream_t stream, tvs_report* rep);
+
+/* W^{1,1} variant of step 2 (Remark IRPW11, eq. IRW11:dual): the dual
+ *   min ||div p - alpha d0||^2 over |p - xi| <= 1,  d = d0 - div p / alpha,
+ * with xi of eq. defXi2:discrete as in tvs_step2.  With q = p - xi this is the
+ * IRV1 dual (eq. IRPXi_dual over |q| <= 1), so the same iteration runs on q
+ * and the call returns p = q + xi; d equals tvs_step2's d.
+ *   p  : out, 2 planes on Omega, the W^{1,1} dual.
+ *   p0 : warm start of p (2 planes, may equal p) or NULL to start from p = xi.
+ *   Other arguments and ws as for tvs_step2 (tvs_workspace_bytes(2, ...)). */
+tvs_status tvs_step2_w11(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
+                         const tvs_iter* it, float* d, float* p, const float* p0, void* ws, size_t ws_bytes,
+                         cudaStream_t stream, tvs_report* rep);
+
+/* Image reconstruction variant 2 (IRV2, Section 3.3: eqs. modifiedStep2,
+ * modifiedStep2_2, modifiedStep2_2_dual; discrete eq. ir2dualdis).
+ *   g   : potential of tau_perp = R_Omega(tau_2, -tau_1) on the image grid.
+ *         The paper asks for (D^-_x g, D^-_y g) = tau_perp; those equations
+ *         between neighbouring pixels are consistent exactly when div tau = 0
+ *         inside the extended grid, while the zero-extension rows of D^- are
+ *         not in general.  g is therefore the least-squares solution of the
+ *         neighbour differences (g = Delta^dagger div v on the n2 x n1 grid,
+ *         v the forward-edge field of tau_perp; DCT along x, tridiagonal
+ *         solves along y), with mean zero.  Where an exact potential exists
+ *         this is it; a constant in g does not change d.
+ *   Then Chambolle's iteration for ||div p - alpha (d0 - g)||^2 over |p| <= 1
+ *   (globally, or under the Schwarz decomposition dd when dd != NULL, as
+ *   tvs_schwarz step 2), u = d0 - g - div p / alpha and d = u + g.
+ *   tau  : 2 planes on ~Omega (from tvs_step1).   n2, n1 >= 3.   alpha > 0.
+ *   d    : out, n2 x n1.   p: in/out (2 planes on Omega) or NULL.
+ *   g_out: out, n2 x n1, or NULL.
+ *   rep  : the ROF problem in u (beta = alpha, data d0 - g).
+ *   ws   : tvs_workspace_bytes(5, n2, n1, dd, it->storage). */
+tvs_status tvs_irv2(const float* d0, const float* tau, int n2, int n1, double alpha, const tvs_iter* it,
+                    const tvs_decomp* dd, float* d, float* p, float* g_out, void* ws, size_t ws_bytes,
+                    cudaStream_t stream, tvs_report* rep);
 
 /* Both steps: d0 -> tau -> xi, f2 -> d.  Step 2 runs under the Schwarz
  * decomposition dd2 when dd2 != NULL, else globally.  tau may be NULL (kept
@@ -200,6 +238,16 @@ typedef struct {
 } tvs_kernel_time;
 int tvs_profile_enable(int on);
 int tvs_profile_read(tvs_kernel_time* out, int cap);
+
+/* Limit of the bounded device-side waits (the TMA tile and row loads of the
+ * step-1 stencils and the step-2 update), in SM cycles; cycles <= 0 restores
+ * the default of about two seconds.  A diagnostic, not an operation of the
+ * paper: with a limit of a few cycles the first wait of a launch gives up
+ * before its copy lands, the kernel records that in the call's error word,
+ * waits (with the default limit) for its copies still in flight and
+ * returns, and the call reports TVS_ERR_TIMEOUT.  Applies to launches
+ * enqueued after it returns; call it while no work of the library runs. */
+tvs_status tvs_set_wait_limit(long long cycles);
 
 /* Graph replay of the iteration runs (see the conventions above): on (1, the
  * default) or off (0).  Returns the previous setting.  While profiling is

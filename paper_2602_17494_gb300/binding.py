@@ -78,10 +78,18 @@ def _load() -> ctypes.CDLL:
     lib.tvs_schwarz.restype = I
     lib.tvs_schwarz.argtypes = [I, P, P, I, I, D, D, ctypes.POINTER(TvsDecomp), ctypes.POINTER(TvsIter),
                                 P, P, P, S, P, ctypes.POINTER(TvsReport)]
+    lib.tvs_step2_w11.restype = I
+    lib.tvs_step2_w11.argtypes = [P, P, I, I, D, D, ctypes.POINTER(TvsIter), P, P, P, P, S, P,
+                                  ctypes.POINTER(TvsReport)]
+    lib.tvs_irv2.restype = I
+    lib.tvs_irv2.argtypes = [P, P, I, I, D, ctypes.POINTER(TvsIter), ctypes.POINTER(TvsDecomp), P, P, P, P, S, P,
+                             ctypes.POINTER(TvsReport)]
     lib.tvs_project_noalloc.restype = I
     lib.tvs_project_noalloc.argtypes = [P, P, I, I, P]
     lib.tvs_profile_enable.restype = I
     lib.tvs_profile_enable.argtypes = [I]
+    lib.tvs_set_wait_limit.restype = I
+    lib.tvs_set_wait_limit.argtypes = [ctypes.c_longlong]
     lib.tvs_set_graphs.restype = I
     lib.tvs_set_graphs.argtypes = [I]
     lib.tvs_profile_read.restype = I
@@ -123,8 +131,8 @@ _lib = _load()
 EXPORTED = ["tvs_denoise", "tvs_engine_create", "tvs_engine_destroy", "tvs_engine_pending",
             "tvs_engine_pool_overhead", "tvs_engine_request_bytes", "tvs_engine_step", "tvs_engine_submit",
             "tvs_last_error", "tvs_profile_enable", "tvs_profile_read", "tvs_project",
-            "tvs_project_noalloc", "tvs_quality", "tvs_schwarz", "tvs_set_graphs", "tvs_status_string", "tvs_step1",
-            "tvs_step2",
+            "tvs_project_noalloc", "tvs_quality", "tvs_schwarz", "tvs_set_graphs", "tvs_set_wait_limit", "tvs_status_string", "tvs_step1",
+            "tvs_step2", "tvs_step2_w11", "tvs_irv2",
             "tvs_tune_schwarz2", "tvs_tune_workspace_bytes", "tvs_version",
             "tvs_workspace_bytes"]
 
@@ -231,6 +239,38 @@ def tvs_step2(d0: torch.Tensor, tau: torch.Tensor, alpha: float, eps: float, it:
     return Result(d, rep.as_dict(), st)
 
 
+def tvs_step2_w11(d0: torch.Tensor, tau: torch.Tensor, alpha: float, eps: float, it: TvsIter,
+                  d: torch.Tensor | None = None, p: torch.Tensor | None = None, p0: torch.Tensor | None = None,
+                  ws: torch.Tensor | None = None):
+    """W^{1,1} step 2: returns (d, p, report, status) with p the dual of eq. IRW11:dual."""
+    n2, n1 = d0.shape
+    d = torch.empty_like(d0) if d is None else d
+    p = torch.empty((2, n2, n1), dtype=torch.float32, device=d0.device) if p is None else p
+    ws = workspace(2, n2, n1, device=d0.device, storage=it.storage) if ws is None else ws
+    rep = TvsReport()
+    st = _lib.tvs_step2_w11(_ptr(d0), _ptr(tau), n2, n1, float(alpha), float(eps), ctypes.byref(it), _ptr(d),
+                            _ptr(p), _ptr(p0), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device),
+                            ctypes.byref(rep))
+    _check(st, "tvs_step2_w11")
+    return d, p, rep.as_dict(), st
+
+
+def tvs_irv2(d0: torch.Tensor, tau: torch.Tensor, alpha: float, it: TvsIter, dd: TvsDecomp | None = None,
+             d: torch.Tensor | None = None, p: torch.Tensor | None = None, g: torch.Tensor | None = None,
+             ws: torch.Tensor | None = None):
+    """IRV2 step 2: returns (d, g, report, status); g is the potential of tau_perp."""
+    n2, n1 = d0.shape
+    d = torch.empty_like(d0) if d is None else d
+    g = torch.empty_like(d0) if g is None else g
+    ws = workspace(5, n2, n1, dd, device=d0.device, storage=it.storage) if ws is None else ws
+    rep = TvsReport()
+    st = _lib.tvs_irv2(_ptr(d0), _ptr(tau), n2, n1, float(alpha), ctypes.byref(it),
+                       ctypes.byref(dd) if dd is not None else None, _ptr(d), _ptr(p), _ptr(g),
+                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device), ctypes.byref(rep))
+    _check(st, "tvs_irv2")
+    return d, g, rep.as_dict(), st
+
+
 def tvs_denoise(d0: torch.Tensor, delta: float, alpha: float, eps: float, it1: TvsIter, it2: TvsIter,
                 dd2: TvsDecomp | None = None, tau: torch.Tensor | None = None, d: torch.Tensor | None = None,
                 ws: torch.Tensor | None = None):
@@ -259,6 +299,11 @@ def tvs_schwarz(step: int, d0: torch.Tensor, tau: torch.Tensor | None, weight: f
                           _stream(d0.device), ctypes.byref(rep))
     _check(st, "tvs_schwarz")
     return Result(out, rep.as_dict(), st)
+
+
+def tvs_set_wait_limit(cycles: int) -> None:
+    """Limit of the bounded device-side waits in SM cycles (<= 0: the default)."""
+    _check(_lib.tvs_set_wait_limit(int(cycles)), "tvs_set_wait_limit", False)
 
 
 def tvs_set_graphs(on: bool) -> bool:

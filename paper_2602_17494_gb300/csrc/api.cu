@@ -3,6 +3,7 @@
 // runs in the kernels of dct.cu, tfs.cu, irv.cu and schwarz.cu.
 #include "drivers.h"
 #include "graphs.h"
+#include "tma.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -51,6 +52,14 @@ size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int storage) {
     return cv.used();
 }
 
+
+// IRV2: Poisson plans on the n2 x n1 image grid and the potential g, then the
+// step-2 state (and, with a decomposition, the Schwarz warm starts).
+static size_t layout_irv2(Carver& cv, int n2, int n1, int storage, Step2Layout& L, PoissonPlans& pp, float** g) {
+    carve_poisson(cv, pp, n2, n1);
+    *g = cv.take<float>((size_t)n2 * round_up(n1, kPitchAlign));
+    return layout_step2(cv, n2, n1, L, storage);
+}
 
 size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L) {
     L.P = round_up(cols, kPitchAlign);
@@ -242,11 +251,10 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
     return TVS_OK;
 }
 
-static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* tau, int n2, int n1, double alpha,
-                           double eps, const tvs_iter& it, float* d, float* p_user, cudaStream_t s,
-                           tvs_report* rep) {
-    const int R = n2 + 1, C = n1 + 1;
-    TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P, s));
+// Chambolle's iteration for ||div p - f2||^2 over |p| <= 1 with f2 already in
+// L.f2 (IRV1: alpha d0 - div xi; IRV2: alpha (d0 - g)); d = (f2 - div p) / alpha.
+static tvs_status run_irv1_loop(const Step2Layout& L, int n1, double alpha, const tvs_iter& it, float* d,
+                                float* p_user, cudaStream_t s, tvs_report* rep) {
     if (p_user) TVS_CUDA(p2_in(L, p_user, s));
     else TVS_CUDA(p2_zero(L, s));
     TVS_CUDA(cudaMemsetAsync(L.red.err, 0, sizeof(unsigned), s));
@@ -307,6 +315,14 @@ static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* t
     if (p_user) TVS_CUDA(p2_out(L, p_user, cur, s));
     if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
     return TVS_OK;
+}
+
+static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* tau, int n2, int n1, double alpha,
+                           double eps, const tvs_iter& it, float* d, float* p_user, cudaStream_t s,
+                           tvs_report* rep) {
+    const int R = n2 + 1, C = n1 + 1;
+    TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P, s));
+    return run_irv1_loop(L, n1, alpha, it, d, p_user, s, rep);
 }
 
 tvs_status run_schwarz2(const Step2Layout& L, Schwarz2State& S2, int n2, int n1, double alpha,
@@ -444,6 +460,13 @@ const char* tvs_status_string(tvs_status st) {
 
 const char* tvs_last_error(void) { return g_last_error.c_str(); }
 
+tvs_status tvs_set_wait_limit(long long cycles) {
+    const long long v = cycles > 0 && cycles < kWaitCycles ? cycles : kWaitCycles;
+    TVS_CUDA(tfs_set_wait_limit(v));
+    TVS_CUDA(irv_set_wait_limit(v));
+    return TVS_OK;
+}
+
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage) {
     if (storage_bytes(storage) == 0) return 0;
     if (storage != TVS_F32 && (step == 1 || step == 3)) return 0;   // step 1 keeps an FP32 dual
@@ -472,6 +495,15 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
     if (step == 4) {
         RedBuf rb;
         return quality_layout(cv, rb);
+    }
+    if (step == 5) {
+        if (n2 < 3 || n1 < 3) return 0;
+        Step2Layout L;
+        PoissonPlans pp;
+        float* g;
+        size_t b = layout_irv2(cv, n2, n1, storage, L, pp, &g);
+        if (dd) b = schwarz2_extend(cv, n2, n1, *dd, L.P, storage);
+        return b;
     }
     if (step == 0) {
         Step1Layout L1;
@@ -569,6 +601,72 @@ tvs_status tvs_schwarz(int step, const float* d0, const float* tau, int n2, int 
     const int R = n2 + 1, C = n1 + 1;
     TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)weight, (float)eps, L.f2, L.P, stream));
     return run_schwarz2(L, S2, n2, n1, weight, *outer, out, p, stream, rep);
+}
+
+tvs_status tvs_step2_w11(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
+                         const tvs_iter* it, float* d, float* p, const float* p0, void* ws, size_t ws_bytes,
+                         cudaStream_t stream, tvs_report* rep) {
+    if (!d0 || !tau || !d || !p || !side_ok(n2) || !side_ok(n1) || !(alpha > 0.0) || !(eps > 0.0))
+        return TVS_ERR_ARG;
+    tvs_status st = check_iter(it, true);
+    if (st != TVS_OK) return st;
+    Carver cv0(nullptr);
+    Step2Layout L;
+    st = check_ws(ws, ws_bytes, layout_step2(cv0, n2, n1, L, it->storage));
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    layout_step2(cv, n2, n1, L, it->storage);
+    const long tplane = (long)(n2 + 1) * (n1 + 1);
+    const size_t pbytes = 2 * (size_t)n2 * n1 * sizeof(float);
+    // q = p - xi is the IRV1 dual (eq. IRPXi_dual); start from q0 = p0 - xi, or 0
+    if (p0) {
+        if (p0 != p) TVS_CUDA(cudaMemcpyAsync(p, p0, pbytes, cudaMemcpyDeviceToDevice, stream));
+        TVS_CUDA(launch_shift_xi(p, n2, n1, tau, tplane, n1 + 1, (float)eps, -1.0f, stream));
+    } else {
+        TVS_CUDA(cudaMemsetAsync(p, 0, pbytes, stream));
+    }
+    st = run_irv1(L, d0, tau, n2, n1, alpha, eps, *it, d, p, stream, rep);
+    if (st != TVS_OK && st != TVS_ERR_NOT_CONVERGED) return st;
+    TVS_CUDA(launch_shift_xi(p, n2, n1, tau, tplane, n1 + 1, (float)eps, 1.0f, stream));
+    return st;
+}
+
+tvs_status tvs_irv2(const float* d0, const float* tau, int n2, int n1, double alpha, const tvs_iter* it,
+                    const tvs_decomp* dd, float* d, float* p, float* g_out, void* ws, size_t ws_bytes,
+                    cudaStream_t stream, tvs_report* rep) {
+    if (!d0 || !tau || !d || n2 < 3 || n1 < 3 || !side_ok(n2) || !side_ok(n1) || !(alpha > 0.0)) return TVS_ERR_ARG;
+    tvs_status st = check_iter(it, true);
+    if (st != TVS_OK) return st;
+    if (dd) {
+        st = schwarz2_check(n2, n1, *dd);
+        if (st != TVS_OK) return st;
+    }
+    st = check_ws(ws, ws_bytes, tvs_workspace_bytes(5, n2, n1, dd, it->storage));
+    if (st != TVS_OK) return st;
+    Carver cv(ws);
+    Step2Layout L;
+    PoissonPlans pp;
+    float* g = nullptr;
+    layout_irv2(cv, n2, n1, it->storage, L, pp, &g);
+    // g = Delta^dagger div v on the image grid, then f = alpha (d0 - g)
+    TVS_CUDA(build_poisson(pp, stream));
+    TVS_CUDA(launch_potential_src(tau, (long)(n2 + 1) * (n1 + 1), n1 + 1, n2, n1, g, L.P, stream));
+    RowSrcArgs sa{g, 0, L.P};
+    TVS_CUDA(poisson_solve(g, n2, n1, L.P, pp, RowSource::Plain, sa, stream));
+    TVS_CUDA(launch_irv2_f(d0, n1, g, L.P, n2, n1, (float)alpha, L.f2, L.P, stream));
+    TVS_CUDA(cudaMemsetAsync(L.red.err, 0, sizeof(unsigned), stream));
+    if (dd) {
+        Schwarz2State S2;
+        schwarz2_carve(cv, n2, n1, *dd, L.P, it->storage, S2);
+        st = run_schwarz2(L, S2, n2, n1, alpha, *it, d, p, stream, rep);
+    } else {
+        st = run_irv1_loop(L, n1, alpha, *it, d, p, stream, rep);
+    }
+    if (st != TVS_OK && st != TVS_ERR_NOT_CONVERGED) return st;
+    // d = u + g (eq. modifiedStep2_2 solved for u = d - g)
+    TVS_CUDA(launch_add_plane(d, n1, g, L.P, n2, n1, stream));
+    if (g_out) TVS_CUDA(from_pitched(g_out, g, L.P, n2, n1, 1, stream));
+    return st;
 }
 
 tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alpha, double eps, const tvs_iter* it1,

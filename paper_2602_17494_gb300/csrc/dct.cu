@@ -24,7 +24,9 @@
 // Kernels:
 //   dct_rows_fwd  : per pair of rows, optional fused stencil source -> X'
 //   tri_cols_solve: per column pair, D'^{-1} Lambda(., k_x) D' along y, which
-//                   is a Neumann tridiagonal solve (tri_solve.cu; in place)
+//                   is a Neumann tridiagonal solve (tri_solve.cu; in place);
+//                   long columns go through the chunked form of the same
+//                   solve (tri_chunk_* kernels, coalesced rows)
 //   dct_rows_inv  : per pair of rows, inverse DCT along x (in place)
 #include "dct_launch.h"
 #include "prof.h"
@@ -92,6 +94,13 @@ void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols) {
     carve_plan(cv, pp.row, cols);
     pp.rows = rows;
     pp.tri = cv.take<float4>(2 * (size_t)cols);
+    if (rows >= kTriChunkRows) {
+        pp.tnch = tri_chunks(rows);
+        pp.tsum = cv.take<float>(tri_chunk_floats(rows, cols));
+    } else {
+        pp.tnch = 0;
+        pp.tsum = nullptr;
+    }
 }
 
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s) {
@@ -121,7 +130,8 @@ static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const
     e = cudaErrorInvalidValue;
     {
         ProfScope ps(kProfCols, s);
-        e = launch_tri_cols(S, rows, cols, pitch, pp.tri, ba, nbatch, s);
+        if (pp.tsum && nbatch == 1 && !ranges) e = launch_tri_cols_chunked(S, rows, cols, pitch, pp, s);
+        else e = launch_tri_cols(S, rows, cols, pitch, pp.tri, ba, nbatch, s);
     }
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;

@@ -47,6 +47,10 @@ cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const Dc
 cudaError_t launch_tri_cols(float* S, int rows, int cols, int pitch, const float4* tab, const BatchArgs& ba,
                             int nbatch, cudaStream_t s);
 cudaError_t build_tri_table(float4* tab, int rows, int cols, cudaStream_t s);
+// The same solve for one unbatched problem with long columns (pp.tsum set):
+// chunks of kTriChunk rows, three kernels with coalesced row accesses.
+cudaError_t launch_tri_cols_chunked(float* S, int rows, int cols, int pitch, const PoissonPlans& pp,
+                                    cudaStream_t s);
 
 // Threads for a transform of length M: one per FFT unit (8 points up to 1024,
 // 16 beyond), two units per thread for the 16384-point transforms.

@@ -322,24 +322,24 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
         if (failed >= 0) {
             // a row never arrived: record it and drain this warp's copies still in flight
             if (lane == 0) atomicOr(err, 1u);
-            for (int k = failed; k < issued; ++k) (void)mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+            for (int k = failed; k < issued; ++k) (void)mbar_drain(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
         } else {
             // loads issued past the last visited item (none when the chunk ends on an item boundary)
-            for (int k = nitems; k < issued; ++k) (void)mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+            for (int k = nitems; k < issued; ++k) (void)mbar_drain(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
         }
     }
     if (CHECK) {
-        double acc[kRedSlots];
+        // deterministic warp reduction of FP32 pairs (two-sum), one FP64 partial per warp
+        FF acc[kRedSlots];
 #pragma unroll
-        for (int k = 0; k < kRedSlots; ++k) acc[k] = k < 4 ? ks[k].value() : (k == 4 ? (double)pmax : 0.0);
-        // deterministic warp reduction, one partial per warp
+        for (int k = 0; k < kRedSlots; ++k) acc[k] = k < 4 ? ks[k].pair() : FF{k == 4 ? pmax : 0.0f, 0.0f};
 #pragma unroll
         for (int k = 0; k < kRedSlots; ++k) {
-            double x = acc[k];
+            FF x = acc[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double y = __shfl_xor_sync(0xffffffffu, x, o);
-                x = red_is_max(k) ? fmax(x, y) : x + y;
+                const FF y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+                x = red_is_max(k) ? FF{fmaxf(x.hi, y.hi), 0.0f} : ff_add(x, y);
             }
             acc[k] = x;
         }
@@ -348,7 +348,7 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
             double v = 0.0;
 #pragma unroll
             for (int k = 0; k < kRedSlots; ++k)
-                if (k == lane) v = acc[k];
+                if (k == lane) v = (double)acc[k].hi + (double)acc[k].lo;
             partial[w * kRedSlots + lane] = v;
         }
     }
@@ -437,6 +437,90 @@ cudaError_t convert_planes(void* dst, int dst_storage, int dpitch, long dplane, 
                                                              static_cast<const S*>(src), spitch, splane, rows, cols);
         })
     })
+    return cudaGetLastError();
+}
+
+}  // namespace tvs
+
+namespace tvs {
+
+// ---------------------------------------------------------------------------
+// IRV2 (Section 3.3, eq. ir2dualdis) and the W^{1,1} dual (eq. IRW11:dual)
+// ---------------------------------------------------------------------------
+// Source of the potential g with grad g = tau_perp in the least-squares sense
+// over the differences between neighbouring image pixels: div v for the
+// forward-edge field v_x(i, j) = tau_2(i, j+1) (j <= n1-2), v_y(i, j) =
+// -tau_1(i+1, j) (i <= n2-2), both zero on the last column / row, with the
+// zero extension of D^-.  g = Delta^dagger div v on the n2 x n1 grid.
+__global__ void potential_src_kernel(const float* __restrict__ tau, long tplane, int tpitch, int n2, int n1,
+                                     float* __restrict__ S, int spitch) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n2 || j >= n1) return;
+    const float* t1 = tau;
+    const float* t2 = tau + tplane;
+    float s = 0.f;
+    if (j <= n1 - 2) s += __ldg(&t2[(size_t)i * tpitch + j + 1]);   // v_x(i, j)
+    if (j >= 1) s -= __ldg(&t2[(size_t)i * tpitch + j]);            // v_x(i, j-1)
+    if (i <= n2 - 2) s -= __ldg(&t1[(size_t)(i + 1) * tpitch + j]); // v_y(i, j)
+    if (i >= 1) s += __ldg(&t1[(size_t)i * tpitch + j]);            // v_y(i-1, j)
+    S[(size_t)i * spitch + j] = s;
+}
+
+// f = alpha (d0 - g), the data of eq. ir2dualdis
+__global__ void irv2_f_kernel(const float* __restrict__ d0, int d0_pitch, const float* __restrict__ g, int gpitch,
+                              int n2, int n1, float alpha, float* __restrict__ f, int fpitch) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n2 || j >= n1) return;
+    f[(size_t)i * fpitch + j] = alpha * (__ldg(&d0[(size_t)i * d0_pitch + j]) - __ldg(&g[(size_t)i * gpitch + j]));
+}
+
+// d += g (d = u + g after the ROF problem in u = d - g)
+__global__ void add_plane_kernel(float* __restrict__ d, int dpitch, const float* __restrict__ g, int gpitch, int n2,
+                                 int n1) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n2 || j >= n1) return;
+    d[(size_t)i * dpitch + j] += __ldg(&g[(size_t)i * gpitch + j]);
+}
+
+// p += sign * xi on the dense n2 x n1 two-plane field p (W^{1,1} dual p = q + xi)
+__global__ void shift_xi_kernel(float* __restrict__ p, int n2, int n1, const float* __restrict__ tau, long tplane,
+                                int tpitch, float eps, float sign) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n2 || j >= n1) return;
+    const float2 xi = xi_at(tau, tplane, tpitch, i, j, eps);
+    const size_t o = (size_t)i * n1 + j;
+    p[o] = fmaf(sign, xi.x, p[o]);
+    p[(size_t)n2 * n1 + o] = fmaf(sign, xi.y, p[(size_t)n2 * n1 + o]);
+}
+
+static inline dim3 grid_2d(int rows, int cols) { return dim3((cols + 31) / 32, (rows + 7) / 8); }
+
+cudaError_t launch_potential_src(const float* tau, long tplane, int tpitch, int n2, int n1, float* S, int spitch,
+                                 cudaStream_t s) {
+    potential_src_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(tau, tplane, tpitch, n2, n1, S, spitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_irv2_f(const float* d0, int d0_pitch, const float* g, int gpitch, int n2, int n1, float alpha,
+                          float* f, int fpitch, cudaStream_t s) {
+    irv2_f_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(d0, d0_pitch, g, gpitch, n2, n1, alpha, f, fpitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_plane(float* d, int dpitch, const float* g, int gpitch, int n2, int n1, cudaStream_t s) {
+    add_plane_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(d, dpitch, g, gpitch, n2, n1);
+    return cudaGetLastError();
+}
+
+cudaError_t irv_set_wait_limit(long long cycles) { return set_wait_limit_here(cycles); }
+
+cudaError_t launch_shift_xi(float* p, int n2, int n1, const float* tau, long tplane, int tpitch, float eps,
+                            float sign, cudaStream_t s) {
+    shift_xi_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(p, n2, n1, tau, tplane, tpitch, eps, sign);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,9 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
                               float* tau_out, int tau_pitch, long tau_plane, double* partial, unsigned* err,
                               cudaStream_t s);
 int tfs_blocks(int R, int C);
+// Limit of the bounded TMA waits of the kernels in tfs.cu / irv.cu (SM cycles).
+cudaError_t tfs_set_wait_limit(long long cycles);
+cudaError_t irv_set_wait_limit(long long cycles);
 // err: device word whose bit 0 is set if a bounded wait on the TMA boxes gave up
 cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, unsigned* err,
                               cudaStream_t s);
@@ -38,6 +41,16 @@ cudaError_t launch_irv1_update(const void* pin, void* pout, const float* f2, int
                                float t, float alpha, bool check, bool write_p, float* d_out, int d_pitch,
                                double* partial, int storage, uint32_t seed, unsigned* err, cudaStream_t s);
 int irv1_blocks(int R, int C);
+// IRV2 (eq. ir2dualdis): S <- div v, the source of the potential g of tau_perp
+// on the n2 x n1 image grid (g = Delta^dagger S); f = alpha (d0 - g); d += g.
+cudaError_t launch_potential_src(const float* tau, long tplane, int tpitch, int n2, int n1, float* S, int spitch,
+                                 cudaStream_t s);
+cudaError_t launch_irv2_f(const float* d0, int d0_pitch, const float* g, int gpitch, int n2, int n1, float alpha,
+                          float* f, int fpitch, cudaStream_t s);
+cudaError_t launch_add_plane(float* d, int dpitch, const float* g, int gpitch, int n2, int n1, cudaStream_t s);
+// W^{1,1} dual (eq. IRW11:dual): p += sign * xi on a dense two-plane n2 x n1 field
+cudaError_t launch_shift_xi(float* p, int n2, int n1, const float* tau, long tplane, int tpitch, float eps,
+                            float sign, cudaStream_t s);
 // Copy `planes` planes of rows x cols between layouts and storage formats
 // (element pitches and plane strides in elements of each side's format).
 cudaError_t convert_planes(void* dst, int dst_storage, int dpitch, long dplane, const void* src, int src_storage,

@@ -10,19 +10,14 @@
 #include "launchers.h"
 
 #include <cstdio>
-#include <mutex>
 
 namespace tvs {
 namespace {
 
 constexpr size_t kNoAllocBytes = size_t(5) << 20;   // 5 MiB
 constexpr int kNoAllocMaxSide = 1025;                  // grids up to 1025 x 1025 points (images up to 1024^2)
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
 
 size_t noalloc_need(int rows, int cols) {
     Carver cv(nullptr);
@@ -44,28 +39,16 @@ extern "C" tvs_status tvs_project_noalloc(const float* in, float* out, int rows,
                        "scratch holds");
         return TVS_ERR_UNSUPPORTED;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error("cudaGetDevice", e);
-        return TVS_ERR_CUDA;
-    }
-    if (dev < 0 || dev >= kMaxDevices) return TVS_ERR_UNSUPPORTED;
+    // Host code only knows a host-side stand-in for the array, so every call
+    // looks up its device address on the current device.  The lookup is a
+    // host-side query (the first one on a device loads the library's device
+    // code there); doing it on every call keeps the address right after the
+    // caller resets the device or its context, where a cached one would be stale.
     void* base = nullptr;
-    {
-        // First call on this device: look up the device address of the array
-        // (host code only knows a host-side stand-in for the symbol).
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                set_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
-                return TVS_ERR_CUDA;
-            }
-            g_noalloc_ptr[dev] = p;
-        }
-        base = g_noalloc_ptr[dev];
+    cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        set_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+        return TVS_ERR_CUDA;
     }
     Carver cv(base);
     PoissonPlans pp;

@@ -83,7 +83,7 @@ __device__ __forceinline__ bool tile_load(uint64_t* bar, uint32_t bytes, float* 
     if (__syncthreads_and(ok)) return true;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         atomicOr(err, 1u);
-        (void)mbar_wait(bar, 0);
+        (void)mbar_drain(bar, 0);
     }
     return false;
 }
@@ -112,7 +112,7 @@ __device__ __forceinline__ bool tile_load_early(uint64_t* bar, uint32_t bytes, f
     if (__syncthreads_and(ok)) return true;
     if (lead) {
         atomicOr(err, 1u);
-        (void)mbar_wait(bar, 0);
+        (void)mbar_drain(bar, 0);
     }
     return false;
 }
@@ -221,18 +221,20 @@ cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plan
 
 // ---------------------------------------------------------------------------
 // out = scale * (u - grad phi) for a 2-plane field u (the last step of P_K).
+// out may be u itself (each thread reads its own element of u before writing
+// it), so u and out are plain pointers read with ordinary loads.
 // ---------------------------------------------------------------------------
-__global__ void grad_sub_kernel(const float* __restrict__ u, int upitch, long uplane,
+__global__ void grad_sub_kernel(const float* u, int upitch, long uplane,
                                 const float* __restrict__ phi, int ppitch, int R, int C, float scale,
-                                float* __restrict__ out, int opitch, long oplane) {
+                                float* out, int opitch, long oplane) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= R || j >= C) return;
     const float pc = __ldg(&phi[(size_t)i * ppitch + j]);
     const float gx = (j < C - 1) ? __ldg(&phi[(size_t)i * ppitch + j + 1]) - pc : 0.f;
     const float gy = (i < R - 1) ? __ldg(&phi[(size_t)(i + 1) * ppitch + j]) - pc : 0.f;
-    const float ux = __ldg(&u[(size_t)i * upitch + j]);
-    const float uy = __ldg(&u[uplane + (size_t)i * upitch + j]);
+    const float ux = u[(size_t)i * upitch + j];
+    const float uy = u[uplane + (size_t)i * upitch + j];
     out[(size_t)i * opitch + j] = scale * (ux - gx);
     out[oplane + (size_t)i * opitch + j] = scale * (uy - gy);
 }
@@ -358,15 +360,17 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
         }
     }
     if (CHECK) {
-        double acc[kRedSlots];
+        FF acc[kRedSlots];
 #pragma unroll
         for (int k = 0; k < kRedSlots; ++k)
-            acc[k] = k < 4 ? ks[k].value() : (k == 4 ? (double)pmax : (k == 5 ? (double)dmax : 0.0));
-        block_reduce_store<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
+            acc[k] = k < 4 ? ks[k].pair() : FF{k == 4 ? pmax : (k == 5 ? dmax : 0.0f), 0.0f};
+        block_reduce_store_ff<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
     }
 }
 
 int tfs_blocks(int R, int C) { return ((C + kTX - 1) / kTX) * ((R + kTY - 1) / kTY); }
+
+cudaError_t tfs_set_wait_limit(long long cycles) { return set_wait_limit_here(cycles); }
 
 cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, const float* f1, int R, int C,
                               int pitch, long plane, float t, float delta, bool check, bool write_p,

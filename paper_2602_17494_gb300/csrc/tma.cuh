@@ -12,6 +12,16 @@ namespace tvs {
 
 constexpr long long kWaitCycles = 4000000000LL;   // about two seconds of SM clock before a wait gives up
 
+// Limit of the first wait on a phase, in SM cycles.  Each translation unit
+// that waits has its own copy; tvs_set_wait_limit sets all of them (a
+// diagnostic: a short limit makes waits give up on copies still in flight,
+// so the timeout path can be tested without a stuck copy).  The drain after
+// a wait gave up always uses kWaitCycles.
+static __constant__ long long c_wait_limit = kWaitCycles;
+static inline cudaError_t set_wait_limit_here(long long cycles) {
+    return cudaMemcpyToSymbol(c_wait_limit, &cycles, sizeof cycles);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -51,13 +61,44 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// One poll that never suspends the thread.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` for at most `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit) {
+    if (limit < kWaitCycles) {
+        // short (diagnostic) limit: poll without suspending
+        const long long t0 = clock64();
+        while (!mbar_test_wait(bar, parity))
+            if (clock64() - t0 > limit) return false;
+        return true;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Bounded wait for phase `parity` of `bar`; false if it did not complete
+// within the current limit (c_wait_limit, normally kWaitCycles).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, c_wait_limit);
+}
+
+// After a wait gave up: wait for the copies still in flight (kWaitCycles).
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, kWaitCycles);
 }
 
 // 2-D / 3-D tiled loads into this CTA's shared memory; x is the innermost

@@ -27,8 +27,29 @@
 // even where r is within 1e-3 of 1.  q and the powers of r that do not depend
 // on the thread come from a per-column table built in FP64 with the plan.
 //
-// Parallel form: one CTA per column pair (the pair is one 8-byte access per
-// row), each thread N consecutive rows of both columns in registers.  The
+// Chunked form (long columns, one unbatched problem): the rows are cut into
+// chunks of kTriChunk = 32 and every kernel maps a warp to 32 adjacent
+// columns of one chunk, so each row access is one coalesced 128-byte line.
+// Both recursions are linear, so a chunk is summarised by values computed
+// from a zero carry: its Horner sum h = sum_i r^(i-i0) b_i, its causal end
+// value a, and g = sum_i r^(i-i0) c_i over its causal values c from zero.
+//   tri_chunk_sum_kernel  : h, a, g per (chunk, column)
+//   tri_chunk_scan_kernel : per column, c_{-1} and w_L from the h and a sums,
+//                           the causal carry into every chunk (C_c) and the
+//                           anti-causal carry after it (W_c), using
+//                           w_{i0} = g_c + C_c sum_{m<n} r^(2m+1) + r^n W_c
+//   tri_chunk_apply_kernel: re-reads the chunk and runs both recursions from
+//                           its carries.
+// Traffic is read, read + write (12 bytes per point) against 8 for the
+// one-pass kernel below, but every access is a full line; at 8193 rows the
+// one-pass kernel's strided 8-byte accesses are latency-bound.  For k_x = 0
+// the input mean mu and the output mean enter as corrections of the
+// summaries: a -> a - mu n, g -> g - mu n(n+1)/2, and the output mean of
+// w is sum_c (K_c + C_c n(n+1)/2 + n W_c) / L with K_c = sum_i (i-i0+1) c_i.
+//
+// Parallel form of the one-pass kernel: one CTA per column pair (the pair is
+// one 8-byte access per row), each thread N consecutive rows of both columns
+// in registers.  The
 // recursions run over the N rows in registers; the chunk carries combine with
 // the constant multiplier r^N as Kogge-Stone scans within a warp and a short
 // serial pass over the warps' totals.  The start value c_{-1} and c_{L-1} come
@@ -278,7 +299,259 @@ cudaError_t launch_n(float* S, int rows, int cols, int pitch, const float4* tab,
                       pitch, tab, ba);
 }
 
+// ---------------------------------------------------------------------------
+// Chunked solve of long columns (see the header).  Summary planes in pp.tsum,
+// each [chunk][column]: 0 h, 1 a, 2 g, 3 C (causal carry into the chunk),
+// 4 W (anti-causal value just after the chunk); then K_c of column 0 [chunk]
+// and (mu, mean w) of column 0.
+// ---------------------------------------------------------------------------
+constexpr int kChunkWarps = 8;
+
+struct ChunkBufs {
+    float *h, *a, *g, *cin, *win, *k0, *par;
+};
+__host__ __device__ __forceinline__ ChunkBufs chunk_bufs(float* base, int nch, int cols) {
+    const size_t pl = (size_t)nch * cols;
+    return ChunkBufs{base, base + pl, base + 2 * pl, base + 3 * pl, base + 4 * pl, base + 5 * pl,
+                     base + 5 * pl + nch};
+}
+
+__device__ __forceinline__ float rstep1(float s, float x, float nq) { return fmaf(nq, s, s + x); }
+
+// h, a, g (and K for column 0) of chunk blockIdx.y * kChunkWarps + warp, columns 32 blockIdx.x + lane
+__global__ void __launch_bounds__(32 * kChunkWarps)
+tri_chunk_sum_kernel(const float* __restrict__ S, int rows, int cols, int pitch, const float4* __restrict__ tab,
+                     float* __restrict__ base, int nch) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int c = blockIdx.y * kChunkWarps + (threadIdx.x >> 5);
+    if (k >= cols || c >= nch) return;
+    const ChunkBufs cb = chunk_bufs(base, nch, cols);
+    const float nq = -__ldg(&tab[2 * k]).x;
+    const int i0 = c * kTriChunk;
+    const int n = min(kTriChunk, rows - i0);
+    const float* src = S + (size_t)i0 * pitch + k;
+    float v[kTriChunk];
+#pragma unroll
+    for (int i = 0; i < kTriChunk; ++i) v[i] = i < n ? __ldg(src + (size_t)i * pitch) : 0.f;
+    float h = 0.f;
+#pragma unroll
+    for (int i = kTriChunk - 1; i >= 0; --i)
+        if (i < n) h = rstep1(h, v[i], nq);
+    float p = 0.f, an = 0.f;                // an: the causal value at the chunk's last row n - 1
+#pragma unroll
+    for (int i = 0; i < kTriChunk; ++i) {
+        p = rstep1(p, v[i], nq);
+        v[i] = p;
+        if (i == n - 1) an = p;
+    }
+    float g = 0.f, kk = 0.f;
+#pragma unroll
+    for (int i = kTriChunk - 1; i >= 0; --i)
+        if (i < n) {
+            g = rstep1(g, v[i], nq);
+            kk = fmaf((float)(i + 1), v[i], kk);
+        }
+    const size_t o = (size_t)c * cols + k;
+    cb.h[o] = h;
+    cb.a[o] = an;
+    cb.g[o] = g;
+    if (k == 0) cb.k0[c] = kk;
+}
+
+// Per column: start values and the carries of every chunk.  lane = column,
+// warp w = chunks [w cpw, (w + 1) cpw).
+__global__ void __launch_bounds__(32 * kChunkWarps)
+tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float* __restrict__ base, int nch) {
+    __shared__ float sh_s1[kChunkWarps][32], sh_r2[kChunkWarps][32], sh_f[kChunkWarps][32], sh_m[kChunkWarps][32];
+    __shared__ float sh_b[kChunkWarps][32], sh_k[kChunkWarps];
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    const bool live = k < cols;
+    const ChunkBufs cb = chunk_bufs(base, nch, cols);
+    const int L = rows;
+    const int cpw = (nch + kChunkWarps - 1) / kChunkWarps;
+    const int c0 = min(nch, w * cpw), c1 = min(nch, c0 + cpw);
+    const float4 ta = live ? __ldg(&tab[2 * k]) : make_float4(0.f, 0.f, 1.f, 1.f);
+    const float4 tb = live ? __ldg(&tab[2 * k + 1]) : make_float4(1.f, 0.f, 0.f, 0.f);
+    const float q = ta.x, nq = -ta.x, l2 = ta.y;
+    const float rL = tb.x, dnm = tb.y, iq = tb.z;
+    const bool zero_mode = k == 0;
+    // r^n and sum_{m<n} r^(2m+1) for a full chunk and for the last one
+    const int nlast = L - (nch - 1) * kTriChunk;
+    float rfull = 1.f, rlast = 1.f, kfull = 0.f, klast = 0.f;
+    {
+        float pw = 1.f;
+        for (int m = 0; m < kTriChunk; ++m) {
+            const float r = 1.f - q;
+            if (m == nlast) {
+                rlast = pw;
+                klast = kfull;
+            }
+            kfull = fmaf(pw * pw, r, kfull);   // + r^(2m+1)
+            pw = fmaf(nq, pw, pw);             // * r
+        }
+        rfull = pw;
+        if (nlast == kTriChunk) {
+            rlast = rfull;
+            klast = kfull;
+        }
+    }
+    // phase 1: S1 = sum r^(i0) h, R2 = sum r^(L-1-e) a, and the range's forward composite
+    float s1 = 0.f, r2 = 0.f, f = 0.f, mw = 1.f;
+    if (live) {
+        for (int c = c0; c < c1; ++c) {
+            const size_t o = (size_t)c * cols + k;
+            const int i0 = c * kTriChunk;
+            const int n = c == nch - 1 ? nlast : kTriChunk;
+            const float rn = c == nch - 1 ? rlast : rfull;
+            const float a = cb.a[o];
+            s1 = fmaf(exp2f((float)i0 * l2), cb.h[o], s1);
+            r2 = fmaf(exp2f((float)(L - i0 - n) * l2), a, r2);
+            f = fmaf(rn, f, a);
+            mw *= rn;
+        }
+    }
+    sh_s1[w][lane] = s1;
+    sh_r2[w][lane] = r2;
+    sh_f[w][lane] = f;
+    sh_m[w][lane] = mw;
+    __syncthreads();
+    float S1 = 0.f, R2 = 0.f;
+    for (int x = 0; x < kChunkWarps; ++x) {
+        S1 += sh_s1[x][lane];
+        R2 += sh_r2[x][lane];
+    }
+    const float mu = zero_mode ? S1 / (float)L : 0.f;   // k_x = 0: the input loses its mean
+    // composite of range x with the mean removed (r = 1 there, so it is a plain sum)
+    auto fx = [&](int x) {
+        const int xc0 = min(nch, x * cpw), xc1 = min(nch, xc0 + cpw);
+        int nr = 0;
+        for (int c = xc0; c < xc1; ++c) nr += c == nch - 1 ? nlast : kTriChunk;
+        return zero_mode ? sh_f[x][lane] - mu * (float)nr : sh_f[x][lane];
+    };
+    const float u0 = (S1 + rL * R2) * dnm;                 // c_{-1} (0 for k_x = 0)
+    float carry = u0;
+    for (int x = 0; x < w; ++x) carry = fmaf(sh_m[x][lane], carry, fx(x));
+    float call = u0;
+    for (int x = 0; x < kChunkWarps; ++x) call = fmaf(sh_m[x][lane], call, fx(x));
+    const float wL = call * iq;                            // w_L (0 for k_x = 0)
+
+    // phase 2: causal carries into each chunk of the range
+    if (live) {
+        for (int c = c0; c < c1; ++c) {
+            const size_t o = (size_t)c * cols + k;
+            const int n = c == nch - 1 ? nlast : kTriChunk;
+            const float rn = c == nch - 1 ? rlast : rfull;
+            cb.cin[o] = carry;
+            const float a = zero_mode ? cb.a[o] - mu * (float)n : cb.a[o];
+            carry = fmaf(rn, carry, a);
+        }
+    }
+    // phase 3: the range's anti-causal composite from zero after its last chunk
+    float bsum = 0.f;
+    if (live) {
+        for (int c = c1 - 1; c >= c0; --c) {
+            const size_t o = (size_t)c * cols + k;
+            const int n = c == nch - 1 ? nlast : kTriChunk;
+            const float rn = c == nch - 1 ? rlast : rfull;
+            const float kn = c == nch - 1 ? klast : kfull;
+            const float g = zero_mode ? cb.g[o] - mu * 0.5f * (float)n * (float)(n + 1) : cb.g[o];
+            bsum = fmaf(rn, bsum, fmaf(cb.cin[o], kn, g));
+        }
+    }
+    __syncthreads();
+    sh_b[w][lane] = bsum;
+    __syncthreads();
+    float wa = wL;                                         // w just after the range
+    for (int x = kChunkWarps - 1; x > w; --x) wa = fmaf(sh_m[x][lane], wa, sh_b[x][lane]);
+    float ksum = 0.f;
+    if (live) {
+        for (int c = c1 - 1; c >= c0; --c) {
+            const size_t o = (size_t)c * cols + k;
+            const int n = c == nch - 1 ? nlast : kTriChunk;
+            const float rn = c == nch - 1 ? rlast : rfull;
+            const float kn = c == nch - 1 ? klast : kfull;
+            cb.win[o] = wa;
+            const float cin = cb.cin[o];
+            const float g = zero_mode ? cb.g[o] - mu * 0.5f * (float)n * (float)(n + 1) : cb.g[o];
+            if (zero_mode) {
+                const float nf = (float)n;
+                const float kc = cb.k0[c] - mu * nf * (nf + 1.f) * (2.f * nf + 1.f) / 6.f;
+                ksum += kc + cin * 0.5f * nf * (nf + 1.f) + nf * wa;
+            }
+            wa = fmaf(rn, wa, fmaf(cin, kn, g));
+        }
+    }
+    if (blockIdx.x == 0 && lane == 0) sh_k[w] = ksum;   // lane 0 of block 0 is column 0 in every warp
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int x = 0; x < kChunkWarps; ++x) tot += sh_k[x];
+        cb.par[0] = mu;
+        cb.par[1] = tot / (float)L;
+    }
+}
+
+// Both recursions of one chunk from its carries; y = -r w (k_x = 0: the
+// output mean is removed).
+__global__ void __launch_bounds__(32 * kChunkWarps)
+tri_chunk_apply_kernel(float* __restrict__ S, int rows, int cols, int pitch, const float4* __restrict__ tab,
+                       const float* __restrict__ base, int nch) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int c = blockIdx.y * kChunkWarps + (threadIdx.x >> 5);
+    if (k >= cols || c >= nch) return;
+    const ChunkBufs cb = chunk_bufs(const_cast<float*>(base), nch, cols);
+    const float q = __ldg(&tab[2 * k]).x, nq = -q;
+    const int i0 = c * kTriChunk;
+    const int n = min(kTriChunk, rows - i0);
+    const size_t o = (size_t)c * cols + k;
+    float mu = 0.f, shift = 0.f;
+    if (k == 0) {
+        mu = __ldg(&cb.par[0]);
+        shift = __ldg(&cb.par[1]);
+    }
+    float* row = S + (size_t)i0 * pitch + k;
+    float v[kTriChunk];
+#pragma unroll
+    for (int i = 0; i < kTriChunk; ++i) v[i] = i < n ? row[(size_t)i * pitch] - mu : 0.f;
+    float p = __ldg(&cb.cin[o]);
+#pragma unroll
+    for (int i = 0; i < kTriChunk; ++i) {
+        p = rstep1(p, v[i], nq);
+        v[i] = p;
+    }
+    float wv = __ldg(&cb.win[o]);
+#pragma unroll
+    for (int i = kTriChunk - 1; i >= 0; --i)
+        if (i < n) {
+            wv = rstep1(wv, v[i], nq);
+            row[(size_t)i * pitch] = fmaf(q, wv, -wv) + shift;
+        }
+}
+
 }  // namespace
+
+cudaError_t launch_tri_cols_chunked(float* S, int rows, int cols, int pitch, const PoissonPlans& pp,
+                                    cudaStream_t s) {
+    if (!pp.tsum || pp.tnch != tri_chunks(rows) || cols < 1) return cudaErrorInvalidValue;
+    const int nch = pp.tnch;
+    const dim3 blk(32 * kChunkWarps);
+    const dim3 grd((cols + 31) / 32, (nch + kChunkWarps - 1) / kChunkWarps);
+    cudaError_t e = launch_pdl(tri_chunk_sum_kernel, grd, blk, 0, s, (const float*)S, rows, cols, pitch,
+                               (const float4*)pp.tri, pp.tsum, nch);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(tri_chunk_scan_kernel, dim3((cols + 31) / 32), blk, 0, s, rows, cols, (const float4*)pp.tri,
+                   pp.tsum, nch);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(tri_chunk_apply_kernel, grd, blk, 0, s, S, rows, cols, pitch, (const float4*)pp.tri,
+                      (const float*)pp.tsum, nch);
+}
 
 cudaError_t build_tri_table(float4* tab, int rows, int cols, cudaStream_t s) {
     const int n = rows_per_thread(rows);

@@ -123,7 +123,21 @@ struct PoissonPlans {
     DctPlan row;         // length cols (x transforms)
     int rows = 0;        // y length; the y pass is a tridiagonal solve per column
     float4* tri = nullptr;  // its per-column coefficients, two float4 per column (tri_solve.cu)
+    // Long columns (rows >= kTriChunkRows) are solved in chunks of 32 rows
+    // with coalesced row accesses (tri_solve.cu); tsum holds the per-chunk
+    // summaries and carries (tri_chunk_floats(rows, cols) floats), tnch the
+    // number of chunks.  nullptr / 0 for short columns.
+    float* tsum = nullptr;
+    int tnch = 0;
 };
+constexpr int kTriChunk = 32;          // rows per chunk of the chunked column solve
+constexpr int kTriChunkRows = 1537;    // shortest column solved in chunks
+inline int tri_chunks(int rows) { return (rows + kTriChunk - 1) / kTriChunk; }
+// five [chunk][column] planes, the k_x = 0 column's weighted sums [chunk] and two scalars
+inline size_t tri_chunk_floats(int rows, int cols) {
+    const size_t n = (size_t)tri_chunks(rows);
+    return 5 * n * (size_t)cols + n + 2;
+}
 void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols);
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s);
 
@@ -170,6 +184,20 @@ cudaError_t finalize_red(const RedBuf& rb, int nblocks, cudaStream_t s);
 // result lands in out[0..kRedSlots) (written by threads 0..kRedSlots-1).
 __device__ __forceinline__ bool red_is_max(int k) { return k == 4 || k == 5; }
 
+// An FP32 value with its rounding error carried separately (hi + lo); ff_add
+// is the error-free two-sum followed by a renormalisation.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = e + (a.lo + b.lo);
+    const float h = s + lo;
+    return FF{h, lo - (h - s)};
+}
+
 // Per-thread compensated (Kahan) FP32 sum: the check kernels add FP32
 // per-pixel terms here and hand the total to FP64 for the cross-thread
 // reduction, so no FP64 arithmetic runs per pixel.
@@ -182,6 +210,7 @@ struct KSum {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ FF pair() const { return FF{s, -c}; }
 };
 
 template <int NT>
@@ -204,6 +233,35 @@ __device__ __forceinline__ void block_reduce_store(double v[kRedSlots], double* 
         double x = red_sm[0][k];
         for (int w = 1; w < NT / 32; ++w) x = red_is_max(k) ? fmax(x, red_sm[w][k]) : x + red_sm[w][k];
         out[k] = x;
+    }
+}
+
+// The same block reduction with the sums carried as unevaluated pairs of
+// FP32 values (hi + lo, combined with the error-free two-sum), so the
+// per-block partial keeps about 44 significant bits without FP64 arithmetic
+// per thread; each block writes its kRedSlots values as doubles.  v[k] =
+// (hi, lo) of slot k; max slots use hi only.  Deterministic: fixed shuffle
+// pattern and warp order.
+template <int NT>
+__device__ __forceinline__ void block_reduce_store_ff(FF v[kRedSlots], double* out, int tid) {
+    __shared__ FF red_ff[NT / 32][kRedSlots];
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < kRedSlots; ++k) {
+        FF x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const FF y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+            x = red_is_max(k) ? FF{fmaxf(x.hi, y.hi), 0.0f} : ff_add(x, y);
+        }
+        if (lane == 0) red_ff[wid][k] = x;
+    }
+    __syncthreads();
+    if (tid < kRedSlots) {
+        const int k = tid;
+        FF x = red_ff[0][k];
+        for (int w = 1; w < NT / 32; ++w) x = red_is_max(k) ? FF{fmaxf(x.hi, red_ff[w][k].hi), 0.0f} : ff_add(x, red_ff[w][k]);
+        out[k] = (double)x.hi + (double)x.lo;
     }
 }
 

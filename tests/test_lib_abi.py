@@ -142,3 +142,27 @@ def test_tuner_workspace_and_argument_checks(lib):
     fake = ctypes.c_void_p(0x1000)
     assert L.tvs_tune_schwarz2(fake, fake, 64, 64, 10.0, 1e-3, ctypes.byref(it), T, 2, O, 2, arr([4]), 1, fake,
                                1 << 30, None, best, None) == 1
+
+
+def test_irv2_and_w11_argument_checks(lib):
+    L = lib.lib()
+    it = lib.make_iter(10)
+    rep = lib.TvsReport()
+    fake = ctypes.c_void_p(0x1000)
+    # IRV2 workspace: plans and the potential on the image grid on top of step 2
+    assert lib.workspace_bytes(5, 256, 300) > lib.workspace_bytes(2, 256, 300)
+    dd = lib.make_decomp(4, 4, 4, 8)
+    assert lib.workspace_bytes(5, 256, 300, dd) > lib.workspace_bytes(5, 256, 300)
+    assert L.tvs_workspace_bytes(5, 2, 300, None, 0) == 0          # the potential needs n2, n1 >= 3
+    # IRV2: alpha <= 0, n < 3, workspace too small
+    assert L.tvs_irv2(fake, fake, 64, 64, 0.0, ctypes.byref(it), None, fake, None, None, fake, 1 << 30, None,
+                      ctypes.byref(rep)) == 1
+    assert L.tvs_irv2(fake, fake, 2, 64, 10.0, ctypes.byref(it), None, fake, None, None, fake, 1 << 30, None,
+                      ctypes.byref(rep)) == 1
+    assert L.tvs_irv2(fake, fake, 64, 64, 10.0, ctypes.byref(it), None, fake, None, None, fake, 16, None,
+                      ctypes.byref(rep)) == 2
+    # W^{1,1}: p is required, eps > 0
+    assert L.tvs_step2_w11(fake, fake, 64, 64, 10.0, 1e-3, ctypes.byref(it), fake, None, None, fake, 1 << 30,
+                           None, ctypes.byref(rep)) == 1
+    assert L.tvs_step2_w11(fake, fake, 64, 64, 10.0, 0.0, ctypes.byref(it), fake, fake, None, fake, 1 << 30,
+                           None, ctypes.byref(rep)) == 1

@@ -49,6 +49,18 @@ def test_noalloc_matches_workspace_projection_twice(B, shape):
         assert (out - ref).abs().max().item() <= 2e-5 * scale, call
 
 
+def test_noalloc_in_place(B):
+    # in == out is allowed: the projection overwrites its own input
+    rng = np.random.default_rng(11)
+    tau = torch.from_numpy(rng.standard_normal((2, 257, 190)).astype(np.float32)).cuda()
+    ref = B.tvs_project(tau)
+    for call in range(2):
+        buf = tau.clone()
+        assert _call_noalloc(B, buf, buf) == 0, B.lib().tvs_last_error()
+        torch.cuda.synchronize()
+        assert (buf - ref).abs().max().item() <= 2e-5 * tau.abs().max().item(), call
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch(B):
     tau = torch.zeros((2, 1026, 1100), dtype=torch.float32, device="cuda")
     out = torch.empty_like(tau)
