@@ -1,20 +1,25 @@
 """Benchmark of the TV-Stokes hot path on GB300 (one JSON line on stdout).
 
-Workload: a 1024 x 1024 seeded synthetic scene (rectangles, discs, a linear
-ramp and two sinusoidal textures, Gaussian noise sigma = 0.1).  One step is
-one full TV-Stokes denoise through the C ABI (tvs_denoise):
-  step 1: tau0, f1 = P_K tau0 / delta, 300 global TFS updates (Algorithm 1);
+Workload (the line's headline): the 8192 x 8192 seeded synthetic scene
+(rectangles, discs, a linear ramp and two sinusoidal textures, Gaussian noise
+sigma = 0.1).  One step is one full TV-Stokes denoise through the C ABI
+(tvs_denoise), each dual run to relative duality gap 1e-4:
+  step 1: tau0, f1 = P_K tau0 / delta and global TFS updates (Algorithm 1),
+          gap checked every 10 updates;
   step 2: xi, f2, then IRV1 under the overlapping Schwarz decomposition with
-          4 x 4 subdomains, overlap 8 px, k = 10 inner updates per outer
-          iteration, 30 outer iterations (Algorithms 2 and 3).
-Unit: dual updates of one grid point per second (Gpixel-iter/s), counting the
-extended grid for step 1 and each image pixel once per inner update for
-step 2.  The state (~60 MB) fits in L2, so L2 is flushed between timed steps.
+          64 x 64 subdomain cores, overlap 4 px, k = 16 inner updates per
+          outer iteration (Algorithms 2 and 3), gap checked every 2 outer
+          iterations.
+Unit: dual updates of one grid point per second (Gpixel-iter/s), counting
+the extended grid for each step-1 update and each image pixel once per inner
+update for step 2; the per-step counts are those the step performs (the same
+every step for this input).  The state (about 5 GB) is far larger than L2.
 
-Also reported: time to relative duality gap 1e-4 (ms per Mpixel) for global
-step 1, global step 2 and Schwarz step 2; per-kernel device time from CUDA
-events; the roofline fraction of the dominant kernel; the FP64 oracle on the
-host cores (``cpu_baseline``).  ``--impl reference`` times the oracle alone.
+Also reported: ms per Mpixel of the denoise; the same step with global
+FP32 step 2; the former 1024^2 fixed-count step (secondary); per-kernel device
+time from CUDA events; the roofline of the dominant kernel; large-image,
+batched, serving and quality sections; the FP64 oracle on the host cores
+(``cpu_baseline``).  ``--impl reference`` times the oracle alone.
 """
 from __future__ import annotations
 
@@ -31,13 +36,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N = 1024
 DELTA, ALPHA, EPS, T = 0.05, 10.0, 1e-3, 0.125
-ITERS1 = 300
-M2 = M1 = 4
-OVERLAP, K_INNER, OUTER = 8, 10, 30
 SIGMA = 0.1
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+TOL = 1e-4
+# headline: the 8192^2 scene to rel. gap 1e-4, step 2 under 64^2 Schwarz cores
+N = 8192
+CHECK1, CHECK2 = 10, 2
+CORE, OVERLAP, K_INNER = 64, 4, 16
+# secondary: the 1024^2 fixed-count step (300 TFS updates, Schwarz 4 x 4, overlap 8, k 10, 30 outer)
+SEC_N, SEC_ITERS1, SEC_M, SEC_OVERLAP, SEC_K, SEC_OUTER = 1024, 300, 4, 8, 10, 30
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of each kernel at 8193^2, as the kernels stand (None: no capture)
+TRAFFIC_8192 = {"dct_rows_fwd": 478.14e6, "dct_rows_inv": 478.02e6}
 
 
 def parse():
@@ -47,15 +57,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-gap-runs", action="store_true")
+    ap.add_argument("--no-gap-runs", action="store_true", help="skip the secondary 1024^2 time-to-gap runs")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving sections")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the quality sweep")
     ap.add_argument("--batch-count", type=int, default=256, help="images of the batched section")
-    ap.add_argument("--serve-count", type=int, default=32, help="requests per arrival rate (serving section)")
+    ap.add_argument("--serve-count", type=int, default=200, help="requests per arrival rate (serving section)")
     ap.add_argument("--large-n", type=int, default=8192,
-                    help="side of the large-image measurements (0 = skip them)")
-    ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise", "bench_step"], default=None,
-                    help="run one API call of this step (profiling target) instead of the benchmark")
-    ap.add_argument("--n", type=int, default=N, help="image side for --case")
+                    help="side of the large-image kernel measurements (0 = skip them)")
+    ap.add_argument("--case", choices=["step1", "step2", "schwarz2", "denoise", "bench_step", "head_step"],
+                    default=None, help="run one API call of this step (profiling target) instead of the benchmark")
+    ap.add_argument("--n", type=int, default=SEC_N, help="image side for --case")
     ap.add_argument("--iters", type=int, default=3, help="updates (or outer iterations) for --case")
     ap.add_argument("--repeat", type=int, default=2, help="calls for --case")
     ap.add_argument("--storage", type=int, default=0, choices=[0, 1, 2, 3],
@@ -66,31 +77,45 @@ def parse():
     return ap.parse_args()
 
 
-def make_input(rank: int = 0):
+def make_input(n: int, seed: int = 0):
     from synth import SceneSpec, noisy_scene
-    _, d0 = noisy_scene(SceneSpec(N, N, seed=rank, sigma=SIGMA, texture=True))
+    _, d0 = noisy_scene(SceneSpec(n, n, seed=seed, sigma=SIGMA, texture=True))
     return d0
 
 
-def work_units() -> float:
-    return float((N + 1) * (N + 1) * ITERS1 + N * N * K_INNER * OUTER)
+def head_iters(B):
+    it1 = B.make_iter(20000, T, TOL, CHECK1)
+    it2 = B.make_iter(5000, T, TOL, CHECK2)
+    return it1, it2
 
 
-def replica_value(local_total_ms: float, world: int, steps: int, dist=None, device=None):
-    """Whole-job throughput of `world` independent replicas.
+def head_decomp(B, n):
+    m = n // CORE
+    return B.make_decomp(m, m, OVERLAP, K_INNER)
 
-    Each rank ran `steps` steps on its own image; the job took as long as its
-    slowest rank, so the time is the maximum over ranks (a host-side timing
-    reduction, not part of the data path).  Returns (value in Gpixel-iter/s,
-    max total ms).
-    """
+
+def head_units(n: int, iters1: int, outer: int) -> float:
+    """Dual updates of one grid point in one headline step."""
+    return float((n + 1) * (n + 1) * iters1 + n * n * K_INNER * outer)
+
+
+def replica_total(local_total_ms: float, world: int, dist=None, device=None) -> float:
+    """The job's time over `world` independent replicas: the slowest rank's
+    (a host-side timing reduction, not part of the data path)."""
     total = float(local_total_ms)
     if world > 1:
         import torch
         t = torch.tensor([total], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total = float(t.item())
-    return work_units() * world * steps / (total / 1e3) / 1e9, total
+    return total
+
+
+def replica_value(local_total_ms: float, world: int, steps: int, units: float, dist=None, device=None):
+    """Whole-job throughput (Gpixel-iter/s) of `world` replicas that each ran
+    `steps` steps of `units` dual updates, and the max total ms."""
+    total = replica_total(local_total_ms, world, dist, device)
+    return units * world * steps / (total / 1e3) / 1e9, total
 
 
 # ---------------------------------------------------------------------------
@@ -156,27 +181,91 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle timing (host cores)
 # ---------------------------------------------------------------------------
-def oracle_sample(d0: np.ndarray, iters1: int, iters2: int):
-    """Run the FP64 oracle on the same image for a bounded number of updates."""
+CROP1 = 2048      # the oracle's step-1 sample: the top-left 2048^2 crop of the benchmark image
+CROP2 = 256       # its step-2 sample: the top-left 256^2 crop (4 x 4 subdomains of 64^2)
+
+
+def host_cpu() -> dict:
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            txt = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            model = next((l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("Model name")), None)
+        except OSError:
+            model = None
+    return {"cores": len(os.sched_getaffinity(0)), "model": model}
+
+
+def oracle_sample(d0: np.ndarray, iters1: int = 1, outer: int = 1):
+    """The FP64 oracle, as it stands, on bounded samples of the benchmark's
+    workload: `iters1` global TFS updates on the top-left CROP1^2 crop of the
+    image, and `outer` Schwarz outer iterations of IRV1 (64^2 cores, overlap
+    4, k = 16) on the CROP2^2 crop (its tau from 5 untimed TFS updates).
+    The oracle's Schwarz step loops over subdomains on full-grid arrays, so
+    it is sampled on the smaller crop.  SciPy's FFTs run on all host cores
+    (scipy.fft.set_workers); NumPy's elementwise work is single-threaded.
+    Returns ((updates, seconds) of step 1, (updates, seconds) of step 2)."""
+    import scipy.fft
     from oracle import schwarz as osch, tvs as otvs
-    t0 = time.perf_counter()
-    tau, _, _ = otvs.tfs(d0, DELTA, T, iters1)
-    t1 = time.perf_counter()
-    f2 = otvs.irv1_data(d0, otvs.normal_field(tau, N, N, EPS), ALPHA)
-    dd = osch.Decomp(N, N, M2, M1, OVERLAP, False)
-    osch.schwarz_irv1(f2, ALPHA, dd, T, iters2, K_INNER)
-    t2 = time.perf_counter()
-    units = (N + 1) * (N + 1) * iters1 + N * N * K_INNER * iters2
-    return units, t2 - t0, (t1 - t0, t2 - t1)
+    a = np.ascontiguousarray(d0[:CROP1, :CROP1])
+    b = np.ascontiguousarray(d0[:CROP2, :CROP2])
+    with scipy.fft.set_workers(len(os.sched_getaffinity(0))):
+        t0 = time.perf_counter()
+        otvs.tfs(a, DELTA, T, iters1)
+        s1 = time.perf_counter() - t0
+        tau, _, _ = otvs.tfs(b, DELTA, T, 5)
+        f2 = otvs.irv1_data(b, otvs.normal_field(tau, CROP2, CROP2, EPS), ALPHA)
+        dd = osch.Decomp(CROP2, CROP2, CROP2 // CORE, CROP2 // CORE, OVERLAP, False)
+        t0 = time.perf_counter()
+        osch.schwarz_irv1(f2, ALPHA, dd, T, outer, K_INNER)
+        s2 = time.perf_counter() - t0
+    u1 = float((CROP1 + 1) ** 2 * iters1)
+    u2 = float(CROP2 * CROP2 * K_INNER * outer)
+    return (u1, s1), (u2, s2)
 
 
-def cpu_baseline(d0: np.ndarray) -> dict:
-    units, secs, parts = oracle_sample(d0, 8, 1)
-    return {"value": units / secs / 1e9, "unit": "Gpixel-iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle on the same 1024^2 image: 8 global TFS updates + 1 Schwarz outer "
-                      f"iteration (16 subdomains x {K_INNER} inner updates); {secs:.1f} s single-threaded "
-                      f"NumPy/SciPy",
-            "seconds": secs}
+def oracle_time_to_gap(n: int = 64) -> dict:
+    """The oracle's time to rel. gap 1e-4 on the 64 x 64 scene of the parity
+    workload (global step 1, then global IRV1; gaps checked every 10)."""
+    import scipy.fft
+    from synth import SceneSpec, noisy_scene
+    from oracle import tvs as otvs
+    d0 = noisy_scene(SceneSpec(n, n, 0, SIGMA))[1]
+    with scipy.fft.set_workers(len(os.sched_getaffinity(0))):
+        t0 = time.perf_counter()
+        tau, _, r1 = otvs.tfs(d0, DELTA, T, 20000, rel_gap_tol=TOL, check_every=CHECK1)
+        f2 = otvs.irv1_data(d0, otvs.normal_field(tau, n, n, EPS), ALPHA)
+        _, _, r2 = otvs.irv1(f2, ALPHA, T, 50000, rel_gap_tol=TOL, check_every=CHECK1)
+        secs = time.perf_counter() - t0
+    return {"image": [n, n], "seconds": secs, "ms_per_mpixel": secs * 1e3 / (n * n / 1e6),
+            "iters_step1": r1.iters, "iters_step2": r2.iters, "rel_gap": [r1.rel_gap, r2.rel_gap]}
+
+
+def sample_text(cores: int) -> str:
+    return (f"FP64 oracle, 1 global TFS update on the top-left {CROP1}^2 crop of the 8192^2 benchmark image + 1 "
+            f"Schwarz outer iteration of IRV1 ({CORE}^2 cores, overlap {OVERLAP}, k {K_INNER}) on its {CROP2}^2 "
+            f"crop; value = their dual updates / their seconds; SciPy FFTs on {cores} cores, NumPy single-threaded")
+
+
+def cpu_baseline(d0: np.ndarray, units1: float, units2: float) -> dict:
+    (u1, s1), (u2, s2) = oracle_sample(d0, 1, 1)
+    cpu = host_cpu()
+    # the same mix of step-1 and step-2 updates as the GPU step
+    mixed = (units1 + units2) / (units1 * s1 / u1 + units2 * s2 / u2) / 1e9
+    return {"value": (u1 + u2) / (s1 + s2) / 1e9, "unit": "Gpixel-iter/s", "cores": cpu["cores"], "kind": "oracle",
+            "cpu_model": cpu["model"], "sample": sample_text(cpu["cores"]), "seconds": s1 + s2,
+            "step1_gpixel_iter_per_s": u1 / s1 / 1e9, "step2_gpixel_iter_per_s": u2 / s2 / 1e9,
+            "at_the_gpu_steps_mix": {"value": mixed, "note": "per-update rates of the two samples weighted by the "
+                                                             "GPU step's step-1 and step-2 update counts"},
+            "time_to_rel_gap_1e-4_64x64": oracle_time_to_gap(64)}
 
 
 # ---------------------------------------------------------------------------
@@ -189,26 +278,59 @@ def fft_flops(L: int) -> float:
     return 5.0 * m * np.log2(m)
 
 
-def algorithmic(name: str, launches: int) -> tuple[str, float, str]:
-    R = C = N + 1
-    if name == "irv1_update":
-        return "hbm", 20.0 * N * N, "bytes"
-    if name == "tfs_update":
-        # read p (16 B), phi (4), f1 (8); write p (16) per grid point
-        return "hbm", 44.0 * R * C, "bytes"
-    if name == "schwarz_combine":
-        return "hbm", (8 + 8 + 8 * 1.03) * N * N, "bytes"
+def algorithmic(name: str, n: int, k: int) -> tuple[float, float]:
+    """(algorithmic HBM bytes, FP32 flops) of one launch of a kernel class on
+    an n x n image (extended grid (n+1)^2); k = Schwarz inner updates."""
+    R = C = n + 1
     if name in ("dct_rows_fwd", "dct_rows_inv"):
-        # one packed Bluestein transform (2 FFTs of length M) per pair of rows
-        return "alu", ((R + 1) // 2) * 2 * fft_flops(C), "flops"
+        # read and write every point once; one packed Bluestein transform
+        # (two FFTs of length M) per pair of rows
+        return 8.0 * R * C, ((R + 1) // 2) * 2 * fft_flops(C)
     if name == "tri_cols_solve":
-        # one Neumann tridiagonal solve per column, in place: read and write 4 B per point
-        return "hbm", 8.0 * R * C, "bytes"
+        return 8.0 * R * C, 0.0           # one tridiagonal solve per column, read and write once
+    if name in ("tfs_update", "tfs_check"):
+        return 44.0 * R * C, 0.0          # read p 16, phi 4, f1 8; write p 16
+    if name == "stencil_other":
+        return 20.0 * R * C, 0.0          # div(vecdiv p): read p 16, write 4
+    if name == "irv1_update":
+        return 20.0 * n * n, 0.0
     if name == "schwarz_tile":
-        # per inner update and pixel: div (4 add), residual (1), grad (2), norm (3 + sqrt),
-        # update (2 mul + 2 fma + 2 div ~ 8) -- ~20 flops
-        return "alu", 20.0 * K_INNER * (N + 8 * (M1 - 1)) * (N + 8 * (M2 - 1)), "flops"
-    return "hbm", 0.0, "bytes"
+        return 39.0 * n * n, 0.0          # of the ~44 B/pixel of an outer iteration (the strip combine has ~5)
+    if name == "schwarz_combine":
+        return 5.0 * n * n, 0.0
+    return 0.0, 0.0
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def roofline_of(prof: dict, steps: int, n: int, sm_count: int, sm_mhz: float | None) -> dict:
+    """Roofline of the kernel class with the largest device time: HBM
+    fraction from its algorithmic bytes and CUDA-event launch time; for the
+    row transforms also the FP32 rate against SMs x 128 lanes x 2 x clock."""
+    pk = peaks()
+    name, (nl, ms) = max(((k, v) for k, v in prof.items() if v[0]), key=lambda kv: kv[1][1])
+    nbytes, flops = algorithmic(name, n, K_INNER)
+    avg_s = ms / max(nl, 1) / 1e3
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    achieved = nbytes / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
+            "traffic": TRAFFIC_8192.get(name) if n == 8192 else None, "kernel": name,
+            "bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6, "launches_per_step": nl // steps}
+    if flops:
+        mhz = sm_mhz or float(pk.get("sm_max_mhz", 2070.0))
+        fp32 = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+        roof["fp32"] = {"achieved_tflops": flops / avg_s / 1e12, "peak_tflops": fp32,
+                        "frac": flops / avg_s / 1e12 / fp32,
+                        "peak_source": f"derived: {sm_count} SMs (queried) x 128 FP32 lanes x 2 x {mhz:.0f} MHz "
+                                       f"(max SM clock seen)"}
+    return roof
 
 
 def run_gpu(args):
@@ -227,15 +349,16 @@ def run_gpu(args):
     ge.build()
     from paper_2602_17494_gb300 import binding as B
 
-    d0_np = make_input(rank)
+    n = N
+    d0_np = make_input(n, rank)
     d0 = torch.from_numpy(d0_np.astype(np.float32)).to(dev)
-    tau = torch.empty((2, N + 1, N + 1), dtype=torch.float32, device=dev)
-    d = torch.empty((N, N), dtype=torch.float32, device=dev)
-    dd = B.make_decomp(M2, M1, OVERLAP, K_INNER)
-    it1, it2 = B.make_iter(ITERS1, T), B.make_iter(OUTER, T)
-    ws = B.workspace(0, N, N, dd, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tau = torch.empty((2, n + 1, n + 1), dtype=torch.float32, device=dev)
+    d = torch.empty((n, n), dtype=torch.float32, device=dev)
+    it1, it2 = head_iters(B)
+    dd = head_decomp(B, n)
+    ws = B.workspace(0, n, n, dd, device=dev)
     stream = torch.cuda.current_stream(dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def step():
         return B.tvs_denoise(d0, DELTA, ALPHA, EPS, it1, it2, dd, tau=tau, d=d, ws=ws)
@@ -245,43 +368,47 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
-        step()
+    reps = None
+    for _ in range(max(args.warmup, 1)):
+        _, _, reps, st = step()
     barrier()
+    iters1, outer = int(reps[0]["iters"]), int(reps[1]["iters"])
+    units = head_units(n, iters1, outer)
 
-    # ---- device-timed steps (inputs resident in HBM) -------------------------
+    # ---- device-timed steps (inputs resident in HBM, state >> L2) ----------
     times = []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
-            flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             barrier()
             e0.record(stream)
-            step()
+            _, _, r, st = step()
             e1.record(stream)
             torch.cuda.synchronize(dev)
             times.append(e0.elapsed_time(e1))
+            assert (int(r[0]["iters"]), int(r[1]["iters"])) == (iters1, outer)
     clocks = clk.summary()
-    value, total_ms = replica_value(float(np.sum(times)), world, args.steps, dist, dev)
+    value, total_ms = replica_value(float(np.sum(times)), world, args.steps, units, dist, dev)
     ms_step = total_ms / args.steps
 
     # ---- per-kernel device time (CUDA events around each launch) ----------
     B.tvs_profile_enable(True)
     for _ in range(args.steps):
-        flush.zero_()
         step()
     torch.cuda.synchronize(dev)
     prof = B.tvs_profile_read()
     B.tvs_profile_enable(False)
     launches = sum(v[0] for v in prof.values()) // args.steps
+    kernels = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": v[1] / args.steps,
+                   "us_per_launch": 1e3 * v[1] / v[0]} for k, v in prof.items() if v[0]}
+    roof = roofline_of(prof, args.steps, n, sm_count, clocks.get("sm_max_mhz"))
 
     # ---- end to end through the API with pinned host buffers -------------
     d0_host = torch.from_numpy(d0_np.astype(np.float32)).pin_memory()
-    d_host = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    d_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
     d0_dev = torch.empty_like(d0)
     e2e_ms = []
     for _ in range(args.steps):
-        flush.zero_()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -291,78 +418,41 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = float(np.sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = work_units() * world * args.steps / (e2e_total / 1e3) / 1e9
+    e2e_value, _ = replica_value(float(np.sum(e2e_ms)), world, args.steps, units, dist, dev)
 
-    # ---- roofline of the dominant kernel ----------------------------------
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, ms) = dom
-    bound, amount, kind = algorithmic(name, nl)
-    avg_s = ms / max(nl, 1) / 1e3
-    if bound == "hbm":
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        achieved = amount / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-    else:
-        peak = FP32_PEAK_TFLOPS
-        achieved = amount / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-    # capture of the current kernel at this workload; the 1025^2 grid stays in L2
-    traffic = {"dct_rows_fwd": 4418560.0, "dct_rows_inv": 4415488.0, "tri_cols_solve": 4380928.0}.get(name) if N == 1024 else None
-    roof.update({"frac": achieved / peak, "traffic": traffic, "kernel": name,
-                 "avg_launch_us": avg_s * 1e6, "launches_per_step": nl // args.steps})
+    # ---- the same step with global FP32 step 2 (the plain global iteration) ----
+    glob = None
+    if rank == 0:
+        ws_g = B.workspace(0, n, n, None, device=dev)
+        it2g = B.make_iter(50000, T, TOL, 20)
+        B.tvs_denoise(d0, DELTA, ALPHA, EPS, it1, it2g, None, tau=tau, d=d, ws=ws_g)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, rg, _ = B.tvs_denoise(d0, DELTA, ALPHA, EPS, it1, it2g, None, tau=tau, d=d, ws=ws_g)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        gms = e0.elapsed_time(e1)
+        glob = {"ms": gms, "ms_per_mpixel": gms / (n * n / 1e6), "iters_step1": rg[0]["iters"],
+                "iters_step2": rg[1]["iters"], "rel_gap": [rg[0]["rel_gap"], rg[1]["rel_gap"]],
+                "step2": "global FP32 IRV1, gap checked every 20 updates"}
+        del ws_g
+        torch.cuda.empty_cache()
 
-    kernels = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": v[1] / args.steps}
-               for k, v in prof.items() if v[0]}
-
-    # ---- time to relative gap 1e-4 (rank 0 only; not part of the step) ----
-    gap = None
-    if rank == 0 and not args.no_gap_runs:
-        gap = {}
-        mpx = N * N / 1e6
-
-        def timed(fn):
-            barrier()
-            t0 = time.perf_counter()
-            r = fn()
-            torch.cuda.synchronize(dev)
-            return (time.perf_counter() - t0) * 1e3, r
-
-        ms1, r1 = timed(lambda: B.tvs_step1(d0, DELTA, B.make_iter(20000, T, 1e-4, 10), tau=tau))
-        gap["step1_global"] = {"ms_per_mpixel": ms1 / mpx, "iters": r1.report["iters"],
-                               "rel_gap": r1.report["rel_gap"]}
-        ms2, r2 = timed(lambda: B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(50000, T, 1e-4, 10), d=d))
-        gap["step2_global"] = {"ms_per_mpixel": ms2 / mpx, "iters": r2.report["iters"],
-                               "rel_gap": r2.report["rel_gap"]}
-        ms3, r3 = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(5000, T, 1e-4, 2), out=d))
-        gap["step2_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms3 / mpx, "outer_iters": r3.report["iters"],
-                                            "rel_gap": r3.report["rel_gap"]}
-        # step 1 under Schwarz (Algorithm 2 with the localized Algorithm 5)
-        tau_s = torch.empty_like(tau)
-        ms4, r4 = timed(lambda: B.tvs_schwarz(1, d0, None, DELTA, EPS, dd, B.make_iter(400, T, 1e-4, 2), out=tau_s))
-        gap["step1_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms4 / mpx, "outer_iters": r4.report["iters"],
-                                            "rel_gap": r4.report["rel_gap"]}
+    secondary = None
+    if rank == 0:
+        secondary = run_secondary(args, B, dev, torch)
 
     large = None
     if rank == 0 and args.large_n > 0:
+        del ws
+        torch.cuda.empty_cache()
         large = run_large(args, B, dev, torch)
     batched = serving = sweep = None
     if rank == 0 and not args.no_serving:
         batched = run_batched(args, B, dev, torch)
         serving = run_serving(args, B, dev, torch)
+    if rank == 0 and not args.no_sweep:
         sweep = run_sweep(args, B, dev, torch)
 
     line = None
@@ -371,26 +461,106 @@ def run_gpu(args):
             "metric": "Gpixel-iter/s", "value": value, "unit": "Gpixel-iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "tvstokes-1024x1024-textured-sigma0.1",
-                       "step": f"tvs_denoise: global TFS {ITERS1} updates + IRV1 Schwarz {M2}x{M1} "
-                               f"overlap {OVERLAP} k {K_INNER} x {OUTER} outer",
-                       "image": [N, N], "delta": DELTA, "alpha": ALPHA, "eps": EPS, "t": T,
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "config": {"workload": "tvstokes-8192x8192-textured-sigma0.1-to-relgap-1e-4",
+                       "step": f"tvs_denoise to rel. gap {TOL:g} in both steps: global TFS (gap every {CHECK1} "
+                               f"updates) + IRV1 under Schwarz, {CORE}^2 cores ({n // CORE}x{n // CORE} "
+                               f"subdomains), overlap {OVERLAP}, k {K_INNER} (gap every {CHECK2} outer)",
+                       "image": [n, n], "delta": DELTA, "alpha": ALPHA, "eps": EPS, "t": T,
+                       "iters_per_step": {"step1_updates": iters1, "step2_outer": outer,
+                                          "step2_inner_updates": outer * K_INNER},
+                       "pixel_iters_per_step": units,
+                       "l2": "state (about 5 GB) far larger than L2; no flush", "parallelism": f"replicas x{world}"},
+            "ms_per_mpixel_to_gap": ms_step / (n * n / 1e6),
+            "global_step2_same_tolerance": glob,
             "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": N * N * 4,
-                    "d2h_bytes_per_step": N * N * 4},
-            "time_to_rel_gap_1e-4": gap,
+            "e2e": {"value": e2e_value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": n * n * 4,
+                    "d2h_bytes_per_step": n * n * 4},
+            "secondary_1024": secondary,
             "large": large,
             "batched": batched,
             "serving": serving,
             "quality_sweep": sweep,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(d0_np)
+            line["cpu_baseline"] = cpu_baseline(d0_np, float((n + 1) * (n + 1) * iters1),
+                                                float(n * n * K_INNER * outer))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def run_secondary(args, B, dev, torch):
+    """The 1024^2 fixed-count step (300 global TFS updates, then IRV1 under
+    Schwarz 4 x 4, overlap 8, k = 10, 30 outer iterations); the grid is
+    L2-resident, so L2 is flushed between timed steps.  Plus the times to
+    rel. gap 1e-4 on that image (global and Schwarz, both steps)."""
+    n = SEC_N
+    d0 = torch.from_numpy(make_input(n, 0).astype(np.float32)).to(dev)
+    tau = torch.empty((2, n + 1, n + 1), dtype=torch.float32, device=dev)
+    d = torch.empty((n, n), dtype=torch.float32, device=dev)
+    dd = B.make_decomp(SEC_M, SEC_M, SEC_OVERLAP, SEC_K)
+    it1, it2 = B.make_iter(SEC_ITERS1, T), B.make_iter(SEC_OUTER, T)
+    ws = B.workspace(0, n, n, dd, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    step = lambda: B.tvs_denoise(d0, DELTA, ALPHA, EPS, it1, it2, dd, tau=tau, d=d, ws=ws)
+    for _ in range(3):
+        step()
+    times = []
+    for _ in range(max(args.steps, 3)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    units = float((n + 1) * (n + 1) * SEC_ITERS1 + n * n * SEC_K * SEC_OUTER)
+    B.tvs_profile_enable(True)
+    for _ in range(3):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    prof = B.tvs_profile_read()
+    B.tvs_profile_enable(False)
+    out = {"workload": "tvstokes-1024x1024-textured-sigma0.1",
+           "step": f"tvs_denoise: global TFS {SEC_ITERS1} updates + IRV1 Schwarz {SEC_M}x{SEC_M} overlap "
+                   f"{SEC_OVERLAP} k {SEC_K} x {SEC_OUTER} outer",
+           "value": units / (ms / 1e3) / 1e9, "unit": "Gpixel-iter/s", "ms_per_step": ms,
+           "l2": "flushed between timed steps (256 MB write); the grid is L2-resident",
+           "kernels": {k: {"launches_per_step": v[0] // 3, "us_per_launch": 1e3 * v[1] / v[0]}
+                       for k, v in prof.items() if v[0]}}
+    if not args.no_gap_runs:
+        gap = {}
+        mpx = n * n / 1e6
+
+        def timed(fn):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize(dev)
+            return (time.perf_counter() - t0) * 1e3, r
+
+        ms1, r1 = timed(lambda: B.tvs_step1(d0, DELTA, B.make_iter(20000, T, TOL, CHECK1), tau=tau))
+        gap["step1_global"] = {"ms_per_mpixel": ms1 / mpx, "iters": r1.report["iters"],
+                               "rel_gap": r1.report["rel_gap"]}
+        ms2, r2 = timed(lambda: B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(50000, T, TOL, 10), d=d))
+        gap["step2_global"] = {"ms_per_mpixel": ms2 / mpx, "iters": r2.report["iters"],
+                               "rel_gap": r2.report["rel_gap"]}
+        ms3, r3 = timed(lambda: B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, B.make_iter(5000, T, TOL, 2), out=d))
+        gap["step2_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms3 / mpx, "outer_iters": r3.report["iters"],
+                                            "rel_gap": r3.report["rel_gap"]}
+        tau_s = torch.empty_like(tau)
+        ms4, r4 = timed(lambda: B.tvs_schwarz(1, d0, None, DELTA, EPS, dd, B.make_iter(400, T, TOL, 2), out=tau_s))
+        gap["step1_schwarz_4x4_s8_k10"] = {"ms_per_mpixel": ms4 / mpx, "outer_iters": r4.report["iters"],
+                                            "rel_gap": r4.report["rel_gap"]}
+        out["time_to_rel_gap_1e-4"] = gap
+    del ws, flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_large(args, B, dev, torch):
@@ -435,6 +605,24 @@ def run_large(args, B, dev, torch):
     del ws1
     torch.cuda.empty_cache()
 
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3, r
+
+    # step 1 to rel. gap 1e-4 per storage of the dual (FP32 last: its tau feeds step 2 below)
+    out["step1_to_gap"] = {}
+    for st, name in ((1, "bf16"), (2, "f16"), (3, "s16"), (0, "f32")):
+        ws1s = B.workspace(1, n, n, device=dev, storage=st)
+        it = B.make_iter(3000, T, TOL, CHECK1, storage=st)
+        ms, r = timed(lambda: B.tvs_step1(d0, DELTA, it, tau=tau, ws=ws1s))
+        out["step1_to_gap"][name] = {"ms_per_mpixel": ms / mpx, "iters": r.report["iters"],
+                                     "rel_gap": r.report["rel_gap"], "reached": r.status == 0}
+        del ws1s
+        torch.cuda.empty_cache()
+
     # step 2 global: roofline of the update kernel
     ws2 = B.workspace(2, n, n, device=dev)
     B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(3, T), d=d, ws=ws2)
@@ -470,17 +658,17 @@ def run_large(args, B, dev, torch):
                                                "gpix_iter_per_s": n * n / avg_s / 1e9}
         del ws16
 
-    # time to relative gap 1e-4: global vs Schwarz
-    def timed(fn):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        r = fn()
-        torch.cuda.synchronize(dev)
-        return (time.perf_counter() - t0) * 1e3, r
-
+    # time to relative gap 1e-4: global (FP32 and 16-bit duals) vs Schwarz
     ms_g, r_g = timed(lambda: B.tvs_step2(d0, tau, ALPHA, EPS, B.make_iter(100000, T, 1e-4, 20), d=d, ws=ws2))
     out["step2_to_gap"] = {"global": {"ms_per_mpixel": ms_g / mpx, "iters": r_g.report["iters"],
                                       "rel_gap": r_g.report["rel_gap"]}}
+    for st, name in ((3, "s16"), (2, "f16"), (1, "bf16")):
+        ws16 = B.workspace(2, n, n, device=dev, storage=st)
+        it = B.make_iter(6000, T, 1e-4, 20, storage=st)
+        ms16, r16 = timed(lambda: B.tvs_step2(d0, tau, ALPHA, EPS, it, d=d, ws=ws16))
+        out["step2_to_gap"][f"global_{name}"] = {"ms_per_mpixel": ms16 / mpx, "iters": r16.report["iters"],
+                                                 "rel_gap": r16.report["rel_gap"], "reached": r16.status == 0}
+        del ws16
     del ws2
     torch.cuda.empty_cache()
     m = n // 64
@@ -661,7 +849,7 @@ def run_serving(args, B, dev, torch):
     out = {"requests_per_rate": n, "mpixel_per_request_mean": mpx / n, "sides": "log-uniform [256, 4096] per axis",
            "hbm_budget_gb": 64, "engine": "tile 64, overlap 4, k 16, FP32",
            "closed_loop": {"images_per_s": cap, "p50_s": _pct(lat0, 50), "p99_s": _pct(lat0, 99)}, "rates": []}
-    for frac in (0.5, 0.9):
+    for frac in (0.25, 0.5, 0.9, 1.25, 2.0):
         rate = frac * cap
         arr = poisson_arrivals(n, rate, seed=4000)
         le, se = serve_engine(arr)
@@ -706,27 +894,30 @@ def run_sweep(args, B, dev, torch):
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores on bounded samples of the headline
+    workload (see oracle_sample), in the headline's unit."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return None
-    d0 = make_input(0)
+    d0 = np.ascontiguousarray(make_input(N, 0)[:CROP1, :CROP1])
     for _ in range(args.warmup):
-        oracle_sample(d0, 2, 1)
+        oracle_sample(d0, 1, 1)
     tot_units, tot_s = 0.0, 0.0
     for _ in range(args.steps):
-        u, s, _ = oracle_sample(d0, 4, 1)
-        tot_units += u
-        tot_s += s
+        (u1, s1), (u2, s2) = oracle_sample(d0, 1, 1)
+        tot_units += u1 + u2
+        tot_s += s1 + s2
     value = tot_units / tot_s / 1e9
+    cpu = host_cpu()
+    sample = "per step: " + sample_text(cpu["cores"])
     return {"impl": "reference", "metric": "Gpixel-iter/s", "value": value, "unit": "Gpixel-iter/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "tvstokes-1024x1024-textured-sigma0.1",
-                       "step": "FP64 oracle sample: 4 global TFS updates + 1 Schwarz outer iteration (4x4, s 8, k 10)"},
-            "cpu_baseline": {"value": value, "unit": "Gpixel-iter/s", "cores": 1, "kind": "oracle",
-                             "sample": "4 TFS updates + 1 Schwarz outer iteration per step, single-threaded"},
+            "config": {"workload": "tvstokes-8192x8192-textured-sigma0.1-to-relgap-1e-4", "step": sample},
+            "cpu_baseline": {"value": value, "unit": "Gpixel-iter/s", "cores": cpu["cores"], "kind": "oracle",
+                             "cpu_model": cpu["model"], "sample": sample},
             "e2e": {"value": value, "unit": "Gpixel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -741,8 +932,8 @@ def run_case(args):
     d0 = torch.from_numpy(noisy_scene(SceneSpec(n, n, 0, SIGMA, True))[1].astype(np.float32)).cuda()
     tau = torch.zeros((2, n + 1, n + 1), dtype=torch.float32, device="cuda")
     m = max(1, n // args.tile)
-    ov = args.overlap if args.overlap >= 0 else (OVERLAP if n // m >= 2 * OVERLAP else 4)
-    dd = B.make_decomp(m, m, ov, args.k if args.k > 0 else K_INNER)
+    ov = args.overlap if args.overlap >= 0 else (SEC_OVERLAP if n // m >= 2 * SEC_OVERLAP else 4)
+    dd = B.make_decomp(m, m, ov, args.k if args.k > 0 else SEC_K)
     it = B.make_iter(args.iters, T)
     it2 = B.make_iter(args.iters, T, storage=args.storage)
     t0 = time.perf_counter()
@@ -754,9 +945,13 @@ def run_case(args):
         elif args.case == "schwarz2":
             r = B.tvs_schwarz(2, d0, tau, ALPHA, EPS, dd, it2)
         elif args.case == "bench_step":
-            # exactly one timed step of the default benchmark (on an n x n scene)
-            B.tvs_denoise(d0, DELTA, ALPHA, EPS, B.make_iter(ITERS1, T), B.make_iter(OUTER, T),
-                          B.make_decomp(M2, M1, OVERLAP, K_INNER), tau=tau)
+            # one step of the secondary 1024^2 fixed-count benchmark (on an n x n scene)
+            B.tvs_denoise(d0, DELTA, ALPHA, EPS, B.make_iter(SEC_ITERS1, T), B.make_iter(SEC_OUTER, T),
+                          B.make_decomp(SEC_M, SEC_M, SEC_OVERLAP, SEC_K), tau=tau)
+        elif args.case == "head_step":
+            # one step of the headline benchmark (to rel. gap 1e-4) on an n x n scene
+            it1, it2 = head_iters(B)
+            B.tvs_denoise(d0, DELTA, ALPHA, EPS, it1, it2, head_decomp(B, n), tau=tau)
         else:
             r = B.tvs_denoise(d0, DELTA, ALPHA, EPS, it, it, dd, tau=tau)
     torch.cuda.synchronize()

@@ -73,12 +73,16 @@ typedef struct {
     int    check_every;  /* updates between gap checks; <= 0 means only at the end      */
     int    storage;      /* tvs_storage of the dual fields kept between updates:
                           * TVS_F32 everywhere; TVS_BF16, TVS_F16 or TVS_S16 for
-                          * step 2 (tvs_step2, tvs_schwarz step 2, tvs_denoise
-                          * it2), where p and the Schwarz warm starts q are
-                          * stored in 16 bits and widened to FP32 for every
-                          * update.  The caller's p stays FP32.
-                          * Step 1 with a 16-bit storage: TVS_ERR_UNSUPPORTED;
-                          * any other value: TVS_ERR_ARG.                        */
+                          * the global step 1 (tvs_step1, tvs_denoise it1) and
+                          * for step 2 (tvs_step2, tvs_schwarz step 2,
+                          * tvs_denoise it2, tvs_irv2, tvs_step2_w11), where p
+                          * and the Schwarz warm starts q are stored in 16 bits
+                          * and widened to FP32 for every update.  The caller's
+                          * p stays FP32.  tvs_denoise keeps tau, when the
+                          * caller passes none, as FP16 (it1 FP16 or fixed
+                          * point) or BF16 (it1 BF16).  Schwarz step 1 and the
+                          * engine's step 1 with a 16-bit storage:
+                          * TVS_ERR_UNSUPPORTED; any other value: TVS_ERR_ARG. */
 } tvs_iter;
 
 /* Values at the returned dual iterate p (duality gap per Appendix A):
@@ -118,8 +122,9 @@ const char* tvs_last_error(void);
  *   tvs_schwarz(step=2) / tvs_step2_w11; step = 0: tvs_denoise (covers
  *   both); step = 3: tvs_project; step = 4: tvs_quality; step = 5: tvs_irv2.
  *   dd = NULL means the global iteration.  storage: the tvs_iter.storage of
- *   the (step-2) call.  Returns 0 for invalid sizes or a storage the step
- *   does not support. */
+ *   the call (for step 0: of it2; the size covers an FP32 step-1 dual and
+ *   tau, which a 16-bit it1 also fits).  Returns 0 for invalid sizes or a
+ *   storage the step does not support. */
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage);
 
 /* Divergence-free projection P_K = I - grad Delta^dagger div on a grid of

@@ -218,7 +218,7 @@ def tvs_step1(d0: torch.Tensor, delta: float, it: TvsIter, tau: torch.Tensor | N
               p: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> Result:
     n2, n1 = d0.shape
     tau = torch.empty((2, n2 + 1, n1 + 1), dtype=torch.float32, device=d0.device) if tau is None else tau
-    ws = workspace(1, n2, n1, device=d0.device) if ws is None else ws
+    ws = workspace(1, n2, n1, device=d0.device, storage=it.storage) if ws is None else ws
     rep = TvsReport()
     st = _lib.tvs_step1(_ptr(d0), n2, n1, float(delta), ctypes.byref(it), _ptr(tau), _ptr(p),
                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(d0.device), ctypes.byref(rep))

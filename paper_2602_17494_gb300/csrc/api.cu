@@ -24,14 +24,16 @@ void set_error(const char* what, cudaError_t e) {
 
 void set_error_text(const char* msg) { g_last_error = msg; }
 
-size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L) {
+size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L, int storage) {
     L.R = n2 + 1;
     L.C = n1 + 1;
     L.P = round_up(L.C, kPitchAlign);
     L.plane = (long)L.R * L.P;
+    L.st = storage;
     carve_poisson(cv, L.pp, L.R, L.C);
-    L.pa = cv.take<float>(4 * (size_t)L.plane);
-    L.pb = cv.take<float>(4 * (size_t)L.plane);
+    // the dual in its storage format (4 planes, element pitch L.P)
+    L.pa = reinterpret_cast<float*>(cv.take<char>(4 * (size_t)L.plane * storage_bytes(storage)));
+    L.pb = reinterpret_cast<float*>(cv.take<char>(4 * (size_t)L.plane * storage_bytes(storage)));
     L.f1 = cv.take<float>(2 * (size_t)L.plane);
     L.S = cv.take<float>((size_t)L.plane);
     carve_red(cv, L.red, tfs_blocks(L.R, L.C));
@@ -180,7 +182,7 @@ static void key_plan(GraphKey& k, const DctPlan& pl) {
     k.add((uint64_t)pl.L).add((uint64_t)pl.M).ptr(pl.chirp).ptr(pl.rot).ptr(pl.post).ptr(pl.tw).ptr(pl.bhat).ptr(pl.sig2);
 }
 
-// `count` plain TFS iterations from cur on stream st (cur and nxt alternate).
+// `count` plain TFS iterations from cur on stream st (cur and nxt alternate; FP32 dual).
 static cudaError_t tfs_iters(const Step1Layout& L, float* cur, float* nxt, int count, float t, float fd,
                              cudaStream_t st) {
     for (int i = 0; i < count; ++i) {
@@ -194,13 +196,26 @@ static cudaError_t tfs_iters(const Step1Layout& L, float* cur, float* nxt, int c
     return cudaSuccess;
 }
 
+// The caller's dense FP32 step-1 dual into / out of the state (any storage).
+static cudaError_t p1_in(const Step1Layout& L, const float* src, cudaStream_t s) {
+    if (L.st == TVS_F32) return to_pitched(L.pa, L.P, src, L.R, L.C, 4, s);
+    return convert_planes(L.pa, L.st, L.P, L.plane, src, TVS_F32, L.C, (long)L.R * L.C, L.R, L.C, 4, s);
+}
+static cudaError_t p1_out(const Step1Layout& L, float* dst, const float* cur, cudaStream_t s) {
+    if (L.st == TVS_F32) return from_pitched(dst, cur, L.P, L.R, L.C, 4, s);
+    return convert_planes(dst, TVS_F32, L.C, (long)L.R * L.C, cur, L.st, L.P, L.plane, L.R, L.C, 4, s);
+}
+
+// tau (2 planes on the extended grid, pitch tau_pitch) is written as
+// tau_storage: TVS_F32, or TVS_F16 / TVS_BF16 for tau kept in the workspace
+// with a 16-bit dual.
 static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1, double delta, const tvs_iter& it,
-                          float* tau, int tau_pitch, long tau_plane, float* p_user, cudaStream_t s,
+                          void* tau, int tau_storage, int tau_pitch, long tau_plane, float* p_user, cudaStream_t s,
                           tvs_report* rep) {
     tvs_status st = tfs_setup(L, d0, n2, n1, delta, s);
     if (st != TVS_OK) return st;
-    if (p_user) TVS_CUDA(to_pitched(L.pa, L.P, p_user, L.R, L.C, 4, s));
-    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 4 * (size_t)L.plane * sizeof(float), s));
+    if (p_user) TVS_CUDA(p1_in(L, p_user, s));
+    else TVS_CUDA(cudaMemsetAsync(L.pa, 0, 4 * (size_t)L.plane * storage_bytes(L.st), s));
     float* cur = L.pa;
     float* nxt = L.pb;
     const int nb = tfs_blocks(L.R, L.C);
@@ -211,7 +226,9 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
     double r[kRedSlots];
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
-        const int run = ck ? 0 : plain_run(check_loop, n, it);
+        // FP32 dual only: 16-bit stores draw their rounding bits from the update
+        // number, which a replayed graph would repeat
+        const int run = (ck || L.st != TVS_F32) ? 0 : plain_run(check_loop, n, it);
         if (run >= 4) {
             GraphKey key;
             key.add(1).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.S).ptr(L.f1).add((uint64_t)L.R).add((uint64_t)L.C)
@@ -222,9 +239,9 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             n += run;
             continue;
         }
-        TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
-        TVS_CUDA(launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
-                                   L.red.partial, L.red.err, s));
+        TVS_CUDA(tfs_phi_st(cur, L.st, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
+        TVS_CUDA(launch_tfs_update_st(cur, nxt, L.st, (uint32_t)n + 1u, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck,
+                                      true, nullptr, TVS_F32, 0, 0, L.red.partial, L.red.err, s));
         std::swap(cur, nxt);
         ++n;
         if (ck) {
@@ -238,15 +255,15 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             }
         }
     }
-    TVS_CUDA(tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
-    TVS_CUDA(launch_tfs_update(cur, nullptr, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau, tau_pitch,
-                               tau_plane, L.red.partial, L.red.err, s));
+    TVS_CUDA(tfs_phi_st(cur, L.st, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
+    TVS_CUDA(launch_tfs_update_st(cur, nullptr, L.st, 0u, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau,
+                                  tau_storage, tau_pitch, tau_plane, L.red.partial, L.red.err, s));
     st = read_result(L.red, nb, s, r);
     if (st != TVS_OK) return st;
     tvs_report fin;
     report_tfs(r, delta, n, &fin);
     if (rep) *rep = fin;
-    if (p_user) TVS_CUDA(from_pitched(p_user, cur, L.P, L.R, L.C, 4, s));
+    if (p_user) TVS_CUDA(p1_out(L, p_user, cur, s));
     if (check_loop && !converged && fin.rel_gap > it.rel_gap_tol) return TVS_ERR_NOT_CONVERGED;
     return TVS_OK;
 }
@@ -317,11 +334,12 @@ static tvs_status run_irv1_loop(const Step2Layout& L, int n1, double alpha, cons
     return TVS_OK;
 }
 
-static tvs_status run_irv1(const Step2Layout& L, const float* d0, const float* tau, int n2, int n1, double alpha,
+static tvs_status run_irv1(const Step2Layout& L, const float* d0, const void* tau, int n2, int n1, double alpha,
                            double eps, const tvs_iter& it, float* d, float* p_user, cudaStream_t s,
-                           tvs_report* rep) {
+                           tvs_report* rep, int tau_storage = TVS_F32) {
     const int R = n2 + 1, C = n1 + 1;
-    TVS_CUDA(launch_xi_f2(d0, n1, tau, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P, s));
+    TVS_CUDA(launch_xi_f2_st(d0, n1, tau, tau_storage, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L.f2, L.P,
+                             s));
     return run_irv1_loop(L, n1, alpha, it, d, p_user, s, rep);
 }
 
@@ -469,7 +487,7 @@ tvs_status tvs_set_wait_limit(long long cycles) {
 
 size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int storage) {
     if (storage_bytes(storage) == 0) return 0;
-    if (storage != TVS_F32 && (step == 1 || step == 3)) return 0;   // step 1 keeps an FP32 dual
+    if (storage != TVS_F32 && (step == 3 || (step == 1 && dd))) return 0;   // Schwarz step 1 keeps an FP32 dual
     Carver cv(nullptr);
     if (step == 3) {
         if (n2 < 2 || n1 < 2 || n2 + 1 > kMaxSide + 1 || n1 + 1 > kMaxSide + 1) return 0;
@@ -479,7 +497,7 @@ size_t tvs_workspace_bytes(int step, int n2, int n1, const tvs_decomp* dd, int s
     if (!side_ok(n2) || !side_ok(n1)) return 0;
     if (step == 1) {
         Step1Layout L;
-        size_t b = layout_step1(cv, n2, n1, L);
+        size_t b = layout_step1(cv, n2, n1, L, storage);
         if (dd) {
             if (schwarz1_check(n2, n1, *dd) != TVS_OK) return 0;
             b = schwarz1_extend(cv, n2, n1, *dd, L.P);
@@ -538,15 +556,15 @@ tvs_status tvs_project(const float* in, float* out, int rows, int cols, void* ws
 tvs_status tvs_step1(const float* d0, int n2, int n1, double delta, const tvs_iter* it, float* tau, float* p,
                      void* ws, size_t ws_bytes, cudaStream_t stream, tvs_report* rep) {
     if (!d0 || !tau || !side_ok(n2) || !side_ok(n1) || !(delta > 0.0)) return TVS_ERR_ARG;
-    tvs_status st = check_iter(it, false);
+    tvs_status st = check_iter(it, true);
     if (st != TVS_OK) return st;
     Carver cv0(nullptr);
     Step1Layout L;
-    st = check_ws(ws, ws_bytes, layout_step1(cv0, n2, n1, L));
+    st = check_ws(ws, ws_bytes, layout_step1(cv0, n2, n1, L, it->storage));
     if (st != TVS_OK) return st;
     Carver cv(ws);
-    layout_step1(cv, n2, n1, L);
-    return run_tfs(L, d0, n2, n1, delta, *it, tau, n1 + 1, (long)(n2 + 1) * (n1 + 1), p, stream, rep);
+    layout_step1(cv, n2, n1, L, it->storage);
+    return run_tfs(L, d0, n2, n1, delta, *it, tau, TVS_F32, n1 + 1, (long)(n2 + 1) * (n1 + 1), p, stream, rep);
 }
 
 tvs_status tvs_step2(const float* d0, const float* tau, int n2, int n1, double alpha, double eps,
@@ -674,7 +692,7 @@ tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alp
                        cudaStream_t stream, tvs_report* rep) {
     if (!d0 || !d || !side_ok(n2) || !side_ok(n1) || !(delta > 0.0) || !(alpha > 0.0) || !(eps > 0.0))
         return TVS_ERR_ARG;
-    tvs_status st = check_iter(it1, false);
+    tvs_status st = check_iter(it1, true);
     if (st != TVS_OK) return st;
     st = check_iter(it2, true);
     if (st != TVS_OK) return st;
@@ -685,15 +703,21 @@ tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alp
     const size_t need = tvs_workspace_bytes(0, n2, n1, dd2, it2->storage);
     st = check_ws(ws, ws_bytes, need);
     if (st != TVS_OK) return st;
+    // the workspace is laid out for an FP32 step-1 dual and tau (tvs_workspace_bytes
+    // step 0); a 16-bit step-1 dual uses the front part of its slots
     Carver cv(ws);
     Step1Layout L1;
     layout_step1(cv, n2, n1, L1);
+    L1.st = it1->storage;
     float* tau_ws = cv.take<float>(2 * (size_t)(n2 + 1) * (n1 + 1));
-    float* tau_use = tau ? tau : tau_ws;
+    // tau kept in the workspace follows the step-1 dual: FP16 for an FP16 or
+    // fixed-point dual (tau is not bounded by 1), BF16 for a BF16 dual
+    const int tau_st = tau ? TVS_F32 : (it1->storage == TVS_BF16 ? TVS_BF16 : (it1->storage == TVS_F32 ? TVS_F32 : TVS_F16));
+    void* tau_use = tau ? static_cast<void*>(tau) : static_cast<void*>(tau_ws);
     Step2Layout L2;
     layout_step2(cv, n2, n1, L2, it2->storage);
     tvs_report r1{}, r2{};
-    tvs_status s1 = run_tfs(L1, d0, n2, n1, delta, *it1, tau_use, n1 + 1, (long)(n2 + 1) * (n1 + 1), nullptr,
+    tvs_status s1 = run_tfs(L1, d0, n2, n1, delta, *it1, tau_use, tau_st, n1 + 1, (long)(n2 + 1) * (n1 + 1), nullptr,
                             stream, &r1);
     if (s1 != TVS_OK && s1 != TVS_ERR_NOT_CONVERGED) return s1;
     tvs_status s2;
@@ -701,11 +725,11 @@ tvs_status tvs_denoise(const float* d0, int n2, int n1, double delta, double alp
         Schwarz2State S2;
         schwarz2_carve(cv, n2, n1, *dd2, L2.P, it2->storage, S2);
         const int R = n2 + 1, C = n1 + 1;
-        TVS_CUDA(launch_xi_f2(d0, n1, tau_use, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L2.f2, L2.P,
-                              stream));
+        TVS_CUDA(launch_xi_f2_st(d0, n1, tau_use, tau_st, (long)R * C, C, n2, n1, (float)alpha, (float)eps, L2.f2,
+                                 L2.P, stream));
         s2 = run_schwarz2(L2, S2, n2, n1, alpha, *it2, d, nullptr, stream, &r2);
     } else {
-        s2 = run_irv1(L2, d0, tau_use, n2, n1, alpha, eps, *it2, d, nullptr, stream, &r2);
+        s2 = run_irv1(L2, d0, tau_use, n2, n1, alpha, eps, *it2, d, nullptr, stream, &r2, tau_st);
     }
     if (rep) {
         rep[0] = r1;

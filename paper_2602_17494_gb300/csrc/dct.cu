@@ -104,6 +104,7 @@ void carve_poisson(Carver& cv, PoissonPlans& pp, int rows, int cols) {
 }
 
 cudaError_t build_poisson(const PoissonPlans& pp, cudaStream_t s) {
+    ProfScope ps(kProfSetup, s, 3);
     const cudaError_t e = build_plan(pp.row, s);
     if (e != cudaSuccess) return e;
     return build_tri_table(pp.tri, pp.rows, pp.row.L, s);
@@ -129,8 +130,9 @@ static cudaError_t poisson_launch(float* S, int rows, int cols, int pitch, const
     if (e != cudaSuccess) return e;
     e = cudaErrorInvalidValue;
     {
-        ProfScope ps(kProfCols, s);
-        if (pp.tsum && nbatch == 1 && !ranges) e = launch_tri_cols_chunked(S, rows, cols, pitch, pp, s);
+        const bool chunked = pp.tsum && nbatch == 1 && !ranges;
+        ProfScope ps(kProfCols, s, chunked ? 3 : 1);
+        if (chunked) e = launch_tri_cols_chunked(S, rows, cols, pitch, pp, s);
         else e = launch_tri_cols(S, rows, cols, pitch, pp.tri, ba, nbatch, s);
     }
     if (e != cudaSuccess) return e;

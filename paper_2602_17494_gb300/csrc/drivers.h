@@ -24,6 +24,7 @@ constexpr int kMaxSide = 8192;   // transform length <= 8193 keeps one FFT line 
 struct Step1Layout {
     int R, C, P;
     long plane;
+    int st = TVS_F32;   // tvs_storage of the dual p (pa, pb; 4 planes each)
     PoissonPlans pp;
     float *pa, *pb, *f1, *S;
     RedBuf red;
@@ -46,7 +47,7 @@ struct ProjLayout {
     float *u, *S;
 };
 
-size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L);
+size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L, int storage = TVS_F32);
 size_t layout_step2(Carver& cv, int n2, int n1, Step2Layout& L, int storage);
 size_t layout_project(Carver& cv, int rows, int cols, ProjLayout& L);
 bool side_ok(int n);

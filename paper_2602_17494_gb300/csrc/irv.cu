@@ -20,15 +20,18 @@ namespace tvs {
 // ---------------------------------------------------------------------------
 // xi and f2 (eq. defXi2:discrete, eq. ir1dualdis)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 xi_at(const float* __restrict__ tau, long tplane, int tpitch,
+// tau is stored as TT (float, or a 16-bit float type for tau kept inside the library)
+template <class TT = float>
+__device__ __forceinline__ float2 xi_at(const TT* __restrict__ tau, long tplane, int tpitch,
                                         int i, int j, float eps) {
-    const float tp1 = __ldg(&tau[tplane + (size_t)i * tpitch + j]);    // tau_2
-    const float tp2 = -__ldg(&tau[(size_t)i * tpitch + j]);            // -tau_1
+    const float tp1 = Stor<TT>::ld1(&tau[tplane + (size_t)i * tpitch + j]);    // tau_2
+    const float tp2 = -Stor<TT>::ld1(&tau[(size_t)i * tpitch + j]);            // -tau_1
     const float den = sqrtf(tp1 * tp1 + tp2 * tp2 + eps);
     return make_float2(tp1 / den, tp2 / den);
 }
 
-__global__ void xi_f2_kernel(const float* __restrict__ d0, int d0_pitch, const float* __restrict__ tau,
+template <class TT>
+__global__ void xi_f2_kernel(const float* __restrict__ d0, int d0_pitch, const TT* __restrict__ tau,
                              long tplane, int tpitch, int R, int C, float alpha, float eps,
                              float* __restrict__ f2, int fpitch) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,11 +46,27 @@ __global__ void xi_f2_kernel(const float* __restrict__ d0, int d0_pitch, const f
     f2[(size_t)i * fpitch + j] = alpha * __ldg(&d0[(size_t)i * d0_pitch + j]) - divxi;
 }
 
+cudaError_t launch_xi_f2_st(const float* d0, int d0_pitch, const void* tau, int tau_storage, long tplane,
+                            int tpitch, int R, int C, float alpha, float eps, float* f2, int fpitch, cudaStream_t s) {
+    dim3 blk(32, 8), grd((C + 31) / 32, (R + 7) / 8);
+    ProfScope ps(kProfSetup, s);
+    if (tau_storage == TVS_F16)
+        xi_f2_kernel<__half><<<grd, blk, 0, s>>>(d0, d0_pitch, static_cast<const __half*>(tau), tplane, tpitch, R,
+                                                 C, alpha, eps, f2, fpitch);
+    else if (tau_storage == TVS_BF16)
+        xi_f2_kernel<__nv_bfloat16><<<grd, blk, 0, s>>>(d0, d0_pitch, static_cast<const __nv_bfloat16*>(tau),
+                                                        tplane, tpitch, R, C, alpha, eps, f2, fpitch);
+    else if (tau_storage == TVS_F32)
+        xi_f2_kernel<float><<<grd, blk, 0, s>>>(d0, d0_pitch, static_cast<const float*>(tau), tplane, tpitch, R, C,
+                                                alpha, eps, f2, fpitch);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long tplane, int tpitch,
                          int R, int C, float alpha, float eps, float* f2, int fpitch, cudaStream_t s) {
-    dim3 blk(32, 8), grd((C + 31) / 32, (R + 7) / 8);
-    xi_f2_kernel<<<grd, blk, 0, s>>>(d0, d0_pitch, tau, tplane, tpitch, R, C, alpha, eps, f2, fpitch);
-    return cudaGetLastError();
+    return launch_xi_f2_st(d0, d0_pitch, tau, TVS_F32, tplane, tpitch, R, C, alpha, eps, f2, fpitch, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -430,6 +449,7 @@ __global__ void convert_planes_kernel(SD* __restrict__ dst, int dpitch, long dpl
 cudaError_t convert_planes(void* dst, int dst_storage, int dpitch, long dplane, const void* src, int src_storage,
                            int spitch, long splane, int rows, int cols, int planes, cudaStream_t s) {
     const dim3 blk(32, 8), grd((cols + 31) / 32, (rows + 7) / 8, planes);
+    ProfScope ps(kProfSetup, s);
     TVS_STORAGE_SWITCH(dst_storage, {
         using SD = S;
         TVS_STORAGE_SWITCH(src_storage, {
@@ -501,17 +521,20 @@ static inline dim3 grid_2d(int rows, int cols) { return dim3((cols + 31) / 32, (
 
 cudaError_t launch_potential_src(const float* tau, long tplane, int tpitch, int n2, int n1, float* S, int spitch,
                                  cudaStream_t s) {
+    ProfScope ps(kProfSetup, s);
     potential_src_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(tau, tplane, tpitch, n2, n1, S, spitch);
     return cudaGetLastError();
 }
 
 cudaError_t launch_irv2_f(const float* d0, int d0_pitch, const float* g, int gpitch, int n2, int n1, float alpha,
                           float* f, int fpitch, cudaStream_t s) {
+    ProfScope ps(kProfSetup, s);
     irv2_f_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(d0, d0_pitch, g, gpitch, n2, n1, alpha, f, fpitch);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_plane(float* d, int dpitch, const float* g, int gpitch, int n2, int n1, cudaStream_t s) {
+    ProfScope ps(kProfSetup, s);
     add_plane_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(d, dpitch, g, gpitch, n2, n1);
     return cudaGetLastError();
 }
@@ -520,6 +543,7 @@ cudaError_t irv_set_wait_limit(long long cycles) { return set_wait_limit_here(cy
 
 cudaError_t launch_shift_xi(float* p, int n2, int n1, const float* tau, long tplane, int tpitch, float eps,
                             float sign, cudaStream_t s) {
+    ProfScope ps(kProfSetup, s);
     shift_xi_kernel<<<grid_2d(n2, n1), dim3(32, 8), 0, s>>>(p, n2, n1, tau, tplane, tpitch, eps, sign);
     return cudaGetLastError();
 }

@@ -15,6 +15,13 @@ cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, c
                               int pitch, long plane, float t, float delta, bool check, bool write_p,
                               float* tau_out, int tau_pitch, long tau_plane, double* partial, unsigned* err,
                               cudaStream_t s);
+// The same for a dual p stored as `storage` (tvs_storage; pin and pout in that
+// format, 16-bit stores rounded stochastically with `seed`), tau_out in
+// `tau_storage` (TVS_F32, or TVS_F16 / TVS_BF16 for a 16-bit dual).
+cudaError_t launch_tfs_update_st(const void* pin, void* pout, int storage, uint32_t seed, const float* phi,
+                                 const float* f1, int R, int C, int pitch, long plane, float t, float delta,
+                                 bool check, bool write_p, void* tau_out, int tau_storage, int tau_pitch,
+                                 long tau_plane, double* partial, unsigned* err, cudaStream_t s);
 int tfs_blocks(int R, int C);
 // Limit of the bounded TMA waits of the kernels in tfs.cu / irv.cu (SM cycles).
 cudaError_t tfs_set_wait_limit(long long cycles);
@@ -22,7 +29,17 @@ cudaError_t irv_set_wait_limit(long long cycles);
 // err: device word whose bit 0 is set if a bounded wait on the TMA boxes gave up
 cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, unsigned* err,
                               cudaStream_t s);
-// S <- Delta^dagger div(vecdiv p) on the extended grid (phi of the TFS iteration)
+cudaError_t launch_div_vecdiv_st(const void* p, int storage, int R, int C, int pitch, long plane, float* dst,
+                                 unsigned* err, cudaStream_t s);
+// S <- Delta^dagger div(vecdiv p) on the extended grid (phi of the TFS iteration);
+// p stored as `storage`
+inline cudaError_t tfs_phi_st(const void* p, int storage, float* S, int R, int C, int pitch, long plane,
+                              const PoissonPlans& pp, unsigned* err, cudaStream_t s) {
+    cudaError_t e = launch_div_vecdiv_st(p, storage, R, C, pitch, plane, S, err, s);
+    if (e != cudaSuccess) return e;
+    RowSrcArgs sa{S, 0, pitch};
+    return poisson_solve(S, R, C, pitch, pp, RowSource::Plain, sa, s);
+}
 inline cudaError_t tfs_phi(const float* p, float* S, int R, int C, int pitch, long plane, const PoissonPlans& pp,
                            unsigned* err, cudaStream_t s) {
     cudaError_t e = launch_div_vecdiv(p, R, C, pitch, plane, S, err, s);
@@ -34,6 +51,9 @@ inline cudaError_t tfs_phi(const float* p, float* S, int R, int C, int pitch, lo
 // irv.cu
 cudaError_t launch_xi_f2(const float* d0, int d0_pitch, const float* tau, long tplane, int tpitch, int R, int C,
                          float alpha, float eps, float* f2, int fpitch, cudaStream_t s);
+// the same with tau stored as tau_storage (TVS_F32, TVS_F16 or TVS_BF16)
+cudaError_t launch_xi_f2_st(const float* d0, int d0_pitch, const void* tau, int tau_storage, long tplane,
+                            int tpitch, int R, int C, float alpha, float eps, float* f2, int fpitch, cudaStream_t s);
 // p (pin, pout) is stored as `storage` (tvs_storage); everything else is float.
 // seed: update counter for the stochastic rounding of 16-bit stores; err:
 // device word that gets bit 0 set if a bounded wait inside the kernel gave up.

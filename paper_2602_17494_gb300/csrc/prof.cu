@@ -13,13 +13,13 @@ namespace tvs {
 
 static const char* kNames[kProfClasses] = {"dct_rows_fwd",     "tri_cols_solve", "dct_rows_inv", "tfs_update",
                                            "irv1_update",      "schwarz_tile",   "schwarz_combine", "stencil_other",
-                                           "tfs_check",        "irv1_check"};
+                                           "tfs_check",        "irv1_check",     "setup"};
 
 namespace {
 std::atomic<int> g_on{0};
 std::mutex g_mu;
 struct Pair {
-    int cls;
+    int cls, kernels;
     cudaEvent_t a, b;
 };
 std::vector<Pair> g_pending;
@@ -41,7 +41,7 @@ cudaEvent_t get_event() {
 
 bool prof_enabled() { return g_on.load(std::memory_order_relaxed) != 0; }
 
-ProfScope::ProfScope(ProfClass cls, cudaStream_t s) : cls_(cls), s_(s), a_(nullptr) {
+ProfScope::ProfScope(ProfClass cls, cudaStream_t s, int kernels) : cls_(cls), kernels_(kernels), s_(s), a_(nullptr) {
     if (!g_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = get_event();
@@ -53,7 +53,7 @@ ProfScope::~ProfScope() {
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEvent_t b = get_event();
     cudaEventRecord(b, s_);
-    g_pending.push_back(Pair{cls_, a_, b});
+    g_pending.push_back(Pair{cls_, kernels_, a_, b});
 }
 
 }  // namespace tvs
@@ -82,7 +82,7 @@ int tvs_profile_read(tvs_kernel_time* out, int cap) {
         if (cudaEventSynchronize(p.b) == cudaSuccess) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                g_launches[p.cls] += 1;
+                g_launches[p.cls] += p.kernels;
                 g_ms[p.cls] += ms;
             }
         }

@@ -18,23 +18,26 @@ enum ProfClass : int {
     kProfOther = 7,
     kProfTfsCheck = 8,
     kProfIrv1Check = 9,
-    kProfClasses = 10
+    kProfSetup = 10,        // once-per-call kernels: tables, tau0, xi and f2, the last P_K step, reductions
+    kProfClasses = 11
 };
 
 // True while per-kernel profiling is on.
 bool prof_enabled();
 
 // Records an event on `s` at construction and at destruction when profiling
-// is enabled; a no-op otherwise.
+// is enabled; a no-op otherwise.  `kernels` is the number of kernel launches
+// the scope covers (the launch count of its class grows by that much).
 class ProfScope {
 public:
-    ProfScope(ProfClass cls, cudaStream_t s);
+    ProfScope(ProfClass cls, cudaStream_t s, int kernels = 1);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;
 
 private:
     ProfClass cls_;
+    int kernels_;
     cudaStream_t s_;
     cudaEvent_t a_;
 };

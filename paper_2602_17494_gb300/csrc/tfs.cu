@@ -6,6 +6,9 @@
 //                  psi_k = grad z_k, p_k <- (p_k + t psi_k) / (1 + t |psi_k|)
 //   tau = P_K tau0 - delta P_K vecdiv p = -delta z
 // Arrays live on the extended grid R x C = (N2+1) x (N1+1) with a padded pitch.
+// The dual p may be stored as FP32 or in 16 bits (tvs_storage, Stor<S>): it
+// is widened to FP32 when its box is read, the arithmetic is FP32, and 16-bit
+// stores of the updated p round stochastically (seed = update number).
 #include "tvs_internal.cuh"
 #include "prof.h"
 #include "tma.cuh"
@@ -29,17 +32,29 @@ constexpr int kBoxC = 4;          // box column of grid column j0
 constexpr int kBoxR = 2;          // box row of grid row i0
 constexpr int kBoxFloats = kBW * kBH;
 
-// Cached tensor maps of one field: rebuilt only when the base, sizes or
-// plane count change.
+// Box of the dual p in storage S: columns j0 - C0 .. j0 + kTX + C0 - 1, so
+// that the box starts on a 16-byte boundary for 4- and 2-byte elements.
+template <class S>
+struct PBox {
+    static constexpr int C0 = 16 / (int)sizeof(S);
+    static constexpr int W = kTX + 2 * C0;
+    static constexpr int ELEMS = W * kBH;                        // one plane
+    static constexpr int BYTES = 4 * ELEMS * (int)sizeof(S);     // four planes
+    static constexpr int BYTES_AL = (BYTES + 127) / 128 * 128;
+};
+inline int pbox_width(int storage) { return kTX + 2 * (16 / (int)storage_bytes(storage)); }
+
+// Cached tensor maps of one field: rebuilt only when the base, sizes, plane
+// count or storage change.
 struct MapCache {
     const void* base = nullptr;
-    int R = 0, C = 0, pitch = 0, planes = 0;
+    int R = 0, C = 0, pitch = 0, planes = 0, st = 0;
     long plane = 0;
     CUtensorMap map;
-    bool get(const void* b, int r, int c, int pt, long pl, int np, CUtensorMap* out) {
-        if (b != base || r != R || c != C || pt != pitch || pl != plane || np != planes) {
-            if (!make_tensor_map(&map, b, TVS_F32, r, c, pt, pl, np, kBW, kBH)) return false;
-            base = b; R = r; C = c; pitch = pt; plane = pl; planes = np;
+    bool get(const void* b, int r, int c, int pt, long pl, int np, CUtensorMap* out, int storage = TVS_F32) {
+        if (b != base || r != R || c != C || pt != pitch || pl != plane || np != planes || storage != st) {
+            if (!make_tensor_map(&map, b, storage, r, c, pt, pl, np, pbox_width(storage), kBH)) return false;
+            base = b; R = r; C = c; pitch = pt; plane = pl; planes = np; st = storage;
         }
         *out = map;
         return true;
@@ -56,9 +71,9 @@ static MapCache* map_slot(MapCache* c, int n, int* next, const void* base) {
     return r;
 }
 
-static bool tile_maps(const float* p, const float* phi, const float* f1, int R, int C, int pitch, long plane,
-                      CUtensorMap* mp, CUtensorMap* mphi, CUtensorMap* mf) {
-    if (!map_slot(g_map_p, 4, &g_map_next[0], p)->get(p, R, C, pitch, plane, 4, mp)) return false;
+static bool tile_maps(const void* p, int storage, const float* phi, const float* f1, int R, int C, int pitch,
+                      long plane, CUtensorMap* mp, CUtensorMap* mphi, CUtensorMap* mf) {
+    if (!map_slot(g_map_p, 4, &g_map_next[0], p)->get(p, R, C, pitch, plane, 4, mp, storage)) return false;
     if (phi && !map_slot(g_map_phi, 2, &g_map_next[1], phi)->get(phi, R, C, pitch, (long)R * pitch, 1, mphi))
         return false;
     if (f1 && !map_slot(g_map_f1, 2, &g_map_next[2], f1)->get(f1, R, C, pitch, plane, 2, mf)) return false;
@@ -67,14 +82,14 @@ static bool tile_maps(const float* p, const float* phi, const float* f1, int R, 
 
 // One thread issues the box loads of a tile; every thread waits (bounded).
 // Returns false (after recording the error and draining) if a box never came.
-__device__ __forceinline__ bool tile_load(uint64_t* bar, uint32_t bytes, float* sp, const CUtensorMap* mp,
+__device__ __forceinline__ bool tile_load(uint64_t* bar, uint32_t bytes, void* sp, const CUtensorMap* mp, int xp,
                                           float* sphi, const CUtensorMap* mphi, float* sf, const CUtensorMap* mf,
                                           int x, int y, unsigned* err) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         mbar_init(bar, 1);
         mbar_init_fence();
         mbar_expect_tx(bar, bytes);
-        tma_load_3d(sp, mp, x, y, 0, bar);
+        tma_load_3d(sp, mp, xp, y, 0, bar);
         if (sphi) tma_load_2d(sphi, mphi, x, y, bar);
         if (sf) tma_load_3d(sf, mf, x, y, 0, bar);
     }
@@ -93,15 +108,15 @@ __device__ __forceinline__ bool tile_load(uint64_t* bar, uint32_t bytes, float* 
 // grid may start) are issued before griddepcontrol.wait and overlap the tail
 // of the previous kernel; the box of phi, which the previous launch writes,
 // is issued after it.
-__device__ __forceinline__ bool tile_load_early(uint64_t* bar, uint32_t bytes, float* sp, const CUtensorMap* mp,
-                                                float* sphi, const CUtensorMap* mphi, float* sf,
+__device__ __forceinline__ bool tile_load_early(uint64_t* bar, uint32_t bytes, void* sp, const CUtensorMap* mp,
+                                                int xp, float* sphi, const CUtensorMap* mphi, float* sf,
                                                 const CUtensorMap* mf, int x, int y, unsigned* err) {
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     if (lead) {
         mbar_init(bar, 1);
         mbar_init_fence();
         mbar_expect_tx(bar, bytes);
-        tma_load_3d(sp, mp, x, y, 0, bar);
+        tma_load_3d(sp, mp, xp, y, 0, bar);
         tma_load_3d(sf, mf, x, y, 0, bar);
     }
     pdl_wait();
@@ -146,6 +161,7 @@ __global__ void tau0_kernel(const float* __restrict__ d0, int d_pitch, int n2, i
 cudaError_t launch_tau0(const float* d0, int d_pitch, int n2, int n1, float* tau, int pitch, long plane,
                         cudaStream_t s) {
     dim3 blk(32, 8), grd((n1 + 1 + 31) / 32, (n2 + 1 + 7) / 8);
+    ProfScope ps(kProfSetup, s);
     tau0_kernel<<<grd, blk, 0, s>>>(d0, d_pitch, n2, n1, tau, pitch, long(plane));
     return cudaGetLastError();
 }
@@ -156,29 +172,35 @@ cudaError_t launch_tau0(const float* d0, int d_pitch, int n2, int n1, float* tau
 // w = vecdiv p on a one-point halo, then s.  D^- reads its argument as zero in
 // the last column (x-part) or row (y-part) and outside the grid.
 // ---------------------------------------------------------------------------
-constexpr size_t kDivSmem = (size_t)4 * kBoxFloats * 4 + (size_t)2 * (kTY + 1) * (kTX + 1) * 4 + 256;
+template <class SP>
+constexpr size_t div_smem() {
+    return (size_t)PBox<SP>::BYTES_AL + (size_t)2 * (kTY + 1) * (kTX + 1) * 4 + 256;
+}
 
+template <class SP>
 __global__ void __launch_bounds__(kTX * kBY)
 div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pitch, float* __restrict__ S,
                   unsigned* __restrict__ err) {
+    using PB = PBox<SP>;
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
+    unsigned char* base = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    const SP* sp = reinterpret_cast<const SP*>(base);   // [4][BH][PB::W]
     constexpr int WH = kTY + 1, WW = kTX + 1;      // w region: rows i0-1.., cols j0-1..
-    float* sw = sp + 4 * kBoxFloats;               // [2][WH][WW]
+    float* sw = reinterpret_cast<float*>(base + PB::BYTES_AL);   // [2][WH][WW]
     uint64_t* bar = reinterpret_cast<uint64_t*>(sw + 2 * WH * WW + 1) ;
     bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(bar) + 7) & ~static_cast<uintptr_t>(7));
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTX + tx;
     constexpr int NT = kTX * kBY;
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
-    if (!tile_load(bar, 4 * kBoxFloats * 4, sp, &pmap, nullptr, nullptr, nullptr, nullptr, j0 - kBoxC, i0 - kBoxR,
-                   err))
+    if (!tile_load(bar, PB::BYTES, base, &pmap, j0 - PB::C0, nullptr, nullptr, nullptr, nullptr, j0 - kBoxC,
+                   i0 - kBoxR, err))
         return;
     // box value of plane q at grid (i, j) with the D^- rule
     auto P = [&](int q, int i, int j) -> float {
-        const float v = sp[(q * kBH + (i - i0 + kBoxR)) * kBW + (j - j0 + kBoxC)];
+        const float v = Stor<SP>::ld1c(sp + (q * kBH + (i - i0 + kBoxR)) * PB::W + (j - j0 + PB::C0));
         const bool ok = (q & 1) == 0 ? j <= C - 2 : i <= R - 2;
         return ok ? v : 0.f;
     };
@@ -206,17 +228,28 @@ div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pi
     }
 }
 
-cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, unsigned* err,
-                              cudaStream_t s) {
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(div_vecdiv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDivSmem);
-    });
+cudaError_t launch_div_vecdiv_st(const void* p, int storage, int R, int C, int pitch, long plane, float* dst,
+                                 unsigned* err, cudaStream_t s) {
     CUtensorMap mp, unused;
-    if (!tile_maps(p, nullptr, nullptr, R, C, pitch, plane, &mp, &unused, &unused)) return cudaErrorInvalidValue;
+    if (!tile_maps(p, storage, nullptr, nullptr, R, C, pitch, plane, &mp, &unused, &unused))
+        return cudaErrorInvalidValue;
     dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
     ProfScope ps(kProfOther, s);
-    return launch_pdl(div_vecdiv_kernel, grd, blk, kDivSmem, s, mp, R, C, pitch, S, err);
+    cudaError_t e = cudaErrorInvalidValue;
+    TVS_STORAGE_SWITCH(storage, {
+        static std::once_flag once;
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(div_vecdiv_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)div_smem<S>());
+        });
+        e = launch_pdl(div_vecdiv_kernel<S>, grd, blk, div_smem<S>(), s, mp, R, C, pitch, dst, err);
+    })
+    return e;
+}
+
+cudaError_t launch_div_vecdiv(const float* p, int R, int C, int pitch, long plane, float* S, unsigned* err,
+                              cudaStream_t s) {
+    return launch_div_vecdiv_st(p, TVS_F32, R, C, pitch, plane, S, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,6 +275,7 @@ __global__ void grad_sub_kernel(const float* u, int upitch, long uplane,
 cudaError_t launch_grad_sub(const float* u, int upitch, long uplane, const float* phi, int ppitch, int R,
                             int C, float scale, float* out, int opitch, long oplane, cudaStream_t s) {
     dim3 blk(32, 8), grd((C + 31) / 32, (R + 7) / 8);
+    ProfScope ps(kProfSetup, s);
     grad_sub_kernel<<<grd, blk, 0, s>>>(u, upitch, uplane, phi, ppitch, R, C, scale, out, opitch, oplane);
     return cudaGetLastError();
 }
@@ -253,20 +287,27 @@ cudaError_t launch_grad_sub(const float* u, int upitch, long uplane, const float
 // the TY x TX outputs.
 // ---------------------------------------------------------------------------
 constexpr int kZH = kTY + 2, kZW = kTX + 2;   // z region: rows i0-1.., cols j0-1..
-constexpr size_t kUpdSmem = (size_t)7 * kBoxFloats * 4 + (size_t)2 * kZH * kZW * 4 + 256;
+template <class SP>
+constexpr size_t upd_smem() {
+    return (size_t)PBox<SP>::BYTES_AL + (size_t)3 * kBoxFloats * 4 + (size_t)2 * kZH * kZW * 4 + 256;
+}
 
-template <bool CHECK, bool WRITE_P, bool WRITE_TAU>
+// SP: storage of p (in and out); TT: type of tau_out (float, or a 16-bit
+// float type for tau kept inside the library).
+template <class SP, bool CHECK, bool WRITE_P, bool WRITE_TAU, class TT = float>
 __global__ void __launch_bounds__(kTX * kBY)
 tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap phimap,
-                  const __grid_constant__ CUtensorMap fmap, float* __restrict__ pout, int R, int C, int pitch,
-                  long plane, float t, float delta, float* __restrict__ tau_out, int tau_pitch, long tau_plane,
-                  double* __restrict__ partial, unsigned* __restrict__ err) {
+                  const __grid_constant__ CUtensorMap fmap, SP* __restrict__ pout, int R, int C, int pitch,
+                  long plane, float t, float delta, TT* __restrict__ tau_out, int tau_pitch, long tau_plane,
+                  double* __restrict__ partial, uint32_t seed, unsigned* __restrict__ err) {
     // every caller launches this right after the Poisson solve that writes phi
     // (four launches that read p and write only phi's plane and the error word),
     // so p and f1 may be read before griddepcontrol.wait (tile_load_early)
+    using PB = PBox<SP>;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    float* sp = reinterpret_cast<float*>(smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u));   // [4][BH][BW]
-    float* sphi = sp + 4 * kBoxFloats;             // [BH][BW]
+    unsigned char* base = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    const SP* sp = reinterpret_cast<const SP*>(base);                  // [4][BH][PB::W]
+    float* sphi = reinterpret_cast<float*>(base + PB::BYTES_AL);      // [BH][BW]
     float* sf = sphi + kBoxFloats;                 // [2][BH][BW]
     float* sz = sf + 2 * kBoxFloats;               // [2][ZH][ZW]
     uint64_t* bar = reinterpret_cast<uint64_t*>(sz + 2 * kZH * kZW);   // 8-byte aligned (even float count)
@@ -274,10 +315,14 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
     const int tid = ty * kTX + tx;
     constexpr int NT = kTX * kBY;
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
-    if (!tile_load_early(bar, 7 * kBoxFloats * 4, sp, &pmap, sphi, &phimap, sf, &fmap, j0 - kBoxC, i0 - kBoxR, err))
+    if (!tile_load_early(bar, PB::BYTES + 3 * kBoxFloats * 4, base, &pmap, j0 - PB::C0, sphi, &phimap, sf, &fmap,
+                         j0 - kBoxC, i0 - kBoxR, err))
         return;
-    // box offsets of grid point (i, j)
+    // box offsets of grid point (i, j): phi and f1, and p (widened to float)
     auto B = [&](int i, int j) -> int { return (i - i0 + kBoxR) * kBW + (j - j0 + kBoxC); };
+    auto PV = [&](int q, int i, int j) -> float {
+        return Stor<SP>::ld1c(sp + (q * kBH + (i - i0 + kBoxR)) * PB::W + (j - j0 + PB::C0));
+    };
 
     // z = w - grad phi - f1 on the z region (zero outside the grid); w = vecdiv p
     // with D^- reading x-parts as zero in the last column and y-parts in the last row
@@ -289,9 +334,8 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
             const int o = B(i, j);
             const float xm = (j <= C - 2) ? 1.f : 0.f;   // x-part at (i, j) read as zero in the last column
             const float ym = (i <= R - 2) ? 1.f : 0.f;   // y-part at (i, j) read as zero in the last row
-            const float w1 = (sp[o] * xm - sp[o - 1]) + (sp[kBoxFloats + o] * ym - sp[kBoxFloats + o - kBW]);
-            const float w2 = (sp[2 * kBoxFloats + o] * xm - sp[2 * kBoxFloats + o - 1]) +
-                             (sp[3 * kBoxFloats + o] * ym - sp[3 * kBoxFloats + o - kBW]);
+            const float w1 = (PV(0, i, j) * xm - PV(0, i, j - 1)) + (PV(1, i, j) * ym - PV(1, i - 1, j));
+            const float w2 = (PV(2, i, j) * xm - PV(2, i, j - 1)) + (PV(3, i, j) * ym - PV(3, i - 1, j));
             const float pc = sphi[o];
             const float gx = (j < C - 1) ? sphi[o + 1] - pc : 0.f;
             const float gy = (i < R - 1) ? sphi[o + kBW] - pc : 0.f;
@@ -321,7 +365,7 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
                 gy[k] = (i < R - 1) ? zk[(r + 1) * kZW + c] - zc[k] : 0.f;
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) pv[q] = sp[q * kBoxFloats + ob];
+            for (int q = 0; q < 4; ++q) pv[q] = PV(q, i, j);
             if (WRITE_P) {
                 // |psi_k| = s2 rsqrt(s2) (the 1e-30 keeps it finite at psi = 0, far
                 // below the resolution of |psi|), one reciprocal per channel
@@ -329,13 +373,14 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
                 for (int k = 0; k < 2; ++k) {
                     const float s2 = fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1e-30f));
                     const float inv = rcp_ftz(fmaf(t, s2 * rsqrt_ftz(s2), 1.0f));
-                    pout[(size_t)(2 * k) * plane + o] = fmaf(t, gx[k], pv[2 * k]) * inv;
-                    pout[(size_t)(2 * k + 1) * plane + o] = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
+                    const float vx = fmaf(t, gx[k], pv[2 * k]) * inv, vy = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
+                    Stor<SP>::st1(pout + (size_t)(2 * k) * plane + o, vx, rkey(seed, o, 2 * k));
+                    Stor<SP>::st1(pout + (size_t)(2 * k + 1) * plane + o, vy, rkey(seed, o, 2 * k + 1));
                 }
             }
             if (WRITE_TAU) {
-                tau_out[(size_t)i * tau_pitch + j] = -delta * zc[0];
-                tau_out[tau_plane + (size_t)i * tau_pitch + j] = -delta * zc[1];
+                tau_out[(size_t)i * tau_pitch + j] = TT(-delta * zc[0]);
+                tau_out[tau_plane + (size_t)i * tau_pitch + j] = TT(-delta * zc[1]);
             }
             if (CHECK) {
 #pragma unroll
@@ -372,34 +417,62 @@ int tfs_blocks(int R, int C) { return ((C + kTX - 1) / kTX) * ((R + kTY - 1) / k
 
 cudaError_t tfs_set_wait_limit(long long cycles) { return set_wait_limit_here(cycles); }
 
+template <class SP, bool CK, bool WP, bool WT, class TT>
+static cudaError_t tfs_update_go(dim3 grd, dim3 blk, cudaStream_t s, const CUtensorMap& mp, const CUtensorMap& mphi,
+                                 const CUtensorMap& mf, void* pout, int R, int C, int pitch, long plane, float t,
+                                 float delta, void* tau_out, int tau_pitch, long tau_plane, double* partial,
+                                 uint32_t seed, unsigned* err) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(tfs_update_kernel<SP, CK, WP, WT, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)upd_smem<SP>());
+    });
+    return launch_pdl(tfs_update_kernel<SP, CK, WP, WT, TT>, grd, blk, upd_smem<SP>(), s, mp, mphi, mf,
+                      static_cast<SP*>(pout), R, C, pitch, plane, t, delta, static_cast<TT*>(tau_out), tau_pitch,
+                      tau_plane, partial, seed, err);
+}
+
+cudaError_t launch_tfs_update_st(const void* pin, void* pout, int storage, uint32_t seed, const float* phi,
+                                 const float* f1, int R, int C, int pitch, long plane, float t, float delta,
+                                 bool check, bool write_p, void* tau_out, int tau_storage, int tau_pitch,
+                                 long tau_plane, double* partial, unsigned* err, cudaStream_t s) {
+    CUtensorMap mp, mphi, mf;
+    if (!tile_maps(pin, storage, phi, f1, R, C, pitch, plane, &mp, &mphi, &mf)) return cudaErrorInvalidValue;
+    dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
+    const bool wt = tau_out != nullptr;
+    ProfScope ps((check || !write_p) ? kProfTfsCheck : kProfTfsUpdate, s);
+#define TVS_TFS(SP, CK, WP, WT, TT)                                                                       \
+    return tfs_update_go<SP, CK, WP, WT, TT>(grd, blk, s, mp, mphi, mf, pout, R, C, pitch, plane, t, delta,  \
+                                             tau_out, tau_pitch, tau_plane, partial, seed, err)
+    if (storage == TVS_F32) {
+        if (wt && tau_storage != TVS_F32) return cudaErrorInvalidValue;
+        if (!check && write_p && !wt) TVS_TFS(float, false, true, false, float);
+        if (check && write_p && !wt) TVS_TFS(float, true, true, false, float);
+        if (check && !write_p && wt) TVS_TFS(float, true, false, true, float);
+        if (check && !write_p && !wt) TVS_TFS(float, true, false, false, float);
+        if (!check && !write_p && wt) TVS_TFS(float, false, false, true, float);
+        TVS_TFS(float, true, true, true, float);
+    }
+    // 16-bit duals: the plain and checked updates and the final report with tau
+    TVS_STORAGE_SWITCH(storage, {
+        if (!check && write_p && !wt) TVS_TFS(S, false, true, false, float);
+        if (check && write_p && !wt) TVS_TFS(S, true, true, false, float);
+        if (check && !write_p && wt) {
+            if (tau_storage == TVS_F32) TVS_TFS(S, true, false, true, float);
+            if (tau_storage == TVS_F16) TVS_TFS(S, true, false, true, __half);
+            if (tau_storage == TVS_BF16) TVS_TFS(S, true, false, true, __nv_bfloat16);
+        }
+    })
+#undef TVS_TFS
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_tfs_update(const float* pin, float* pout, const float* phi, const float* f1, int R, int C,
                               int pitch, long plane, float t, float delta, bool check, bool write_p,
                               float* tau_out, int tau_pitch, long tau_plane, double* partial, unsigned* err,
                               cudaStream_t s) {
-    CUtensorMap mp, mphi, mf;
-    if (!tile_maps(pin, phi, f1, R, C, pitch, plane, &mp, &mphi, &mf)) return cudaErrorInvalidValue;
-    dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
-    const bool wt = tau_out != nullptr;
-    ProfScope ps((check || !write_p) ? kProfTfsCheck : kProfTfsUpdate, s);
-    cudaError_t e = cudaSuccess;
-#define TVS_TFS(CK, WP, WT)                                                                                   \
-    do {                                                                                                      \
-        static std::once_flag once;                                                                          \
-        std::call_once(once, [] {                                                                            \
-            cudaFuncSetAttribute(tfs_update_kernel<CK, WP, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 (int)kUpdSmem);                                                             \
-        });                                                                                                   \
-        e = launch_pdl(tfs_update_kernel<CK, WP, WT>, grd, blk, kUpdSmem, s, mp, mphi, mf, pout, R, C, pitch,   \
-                       plane, t, delta, tau_out, tau_pitch, tau_plane, partial, err);                        \
-    } while (0)
-    if (!check && write_p && !wt) TVS_TFS(false, true, false);
-    else if (check && write_p && !wt) TVS_TFS(true, true, false);
-    else if (check && !write_p && wt) TVS_TFS(true, false, true);
-    else if (check && !write_p && !wt) TVS_TFS(true, false, false);
-    else if (!check && !write_p && wt) TVS_TFS(false, false, true);
-    else TVS_TFS(true, true, true);
-#undef TVS_TFS
-    return e;
+    return launch_tfs_update_st(pin, pout, TVS_F32, 0u, phi, f1, R, C, pitch, plane, t, delta, check, write_p,
+                                tau_out, TVS_F32, tau_pitch, tau_plane, partial, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,6 +501,7 @@ void carve_red(Carver& cv, RedBuf& rb, int cap) {
 }
 
 cudaError_t finalize_red(const RedBuf& rb, int nblocks, cudaStream_t s) {
+    ProfScope ps(kProfSetup, s);
     finalize_red_kernel<<<1, 256, 0, s>>>(rb.partial, nblocks, rb.result);
     return cudaGetLastError();
 }

@@ -163,3 +163,50 @@ def test_step2_16bit_formats_at_512(B, storage, decomp):
     assert np.abs(host(res.out) - d_o).max() <= dtol
     assert rel(res.report["primal_E"], rep_o.primal_E) <= etol
     assert np.abs(host(p)).max() <= 1.0 + 2.0 ** -8
+
+
+# ---------------------------------------------------------------------------
+# 16-bit storage of the step-1 dual (and of tau kept inside tvs_denoise)
+# ---------------------------------------------------------------------------
+# bounds on max|tau - tau_oracle| and the relative primal energy after 300 updates
+STEP1_NARROW = {3: (1e-4, EREL), 2: (1e-3, 5e-5), 1: (5e-3, 1e-3)}
+
+
+@pytest.mark.parametrize("storage", [3, 2, 1])
+def test_step1_16bit_storage_error_against_oracle(B, storage):
+    n2, n1, iters = 64, 72, 300
+    d0 = f32(image(n2, n1, 26, texture=True))
+    tau_o, _, rep_o = otvs.tfs(d0, 0.05, 0.125, iters)
+    p = torch.zeros((4, n2 + 1, n1 + 1), dtype=torch.float32, device="cuda")
+    res = B.tvs_step1(cuda(d0), 0.05, B.make_iter(iters, storage=storage), p=p)
+    ttol, etol = STEP1_NARROW[storage]
+    assert np.abs(host(res.out) - tau_o).max() <= ttol
+    assert rel(res.report["primal_E"], rep_o.primal_E) <= etol
+    assert res.report["div_res_max"] <= 1e-4
+    assert np.abs(host(p)).max() <= 1.0 + 2.0 ** -5
+
+
+@pytest.mark.parametrize("storage", [3, 2, 1])
+def test_denoise_16bit_step1_and_tau(B, storage):
+    # tvs_denoise with a 16-bit step-1 dual and no tau buffer keeps tau in 16
+    # bits (FP16, or BF16 for a BF16 dual); d against the FP64 pipeline
+    n, it = 64, 200
+    d0 = f32(image(n, n, 27, texture=True))
+    d_o, _, _, r2 = otvs.denoise(d0, 0.05, 10.0, 1e-3, 0.125, it, it)
+    d, _, reps, st = B.tvs_denoise(cuda(d0), 0.05, 10.0, 1e-3, B.make_iter(it, storage=storage), B.make_iter(it))
+    dtol = {3: 2e-4, 2: 1e-3, 1: 5e-3}[storage]
+    assert np.abs(host(d) - d_o).max() <= dtol
+    assert rel(reps[1]["primal_E"], r2.primal_E) <= 10 * STEP1_NARROW[storage][1]
+
+
+def test_step1_16bit_is_reproducible_and_converges(B):
+    d0 = cuda(image(256, 256, 28, texture=True))
+    a = B.tvs_step1(d0, 0.05, B.make_iter(40, storage=3)).out
+    b = B.tvs_step1(d0, 0.05, B.make_iter(40, storage=3)).out
+    assert torch.equal(a, b)
+    its = {}
+    for st in (0, 3):
+        r = B.tvs_step1(d0, 0.05, B.make_iter(5000, rel_gap_tol=1e-4, check_every=10, storage=st))
+        assert r.status == 0 and r.report["rel_gap"] <= 1e-4
+        its[st] = r.report["iters"]
+    assert its[3] <= 1.1 * its[0] + 20

@@ -56,7 +56,10 @@ def test_workspace_sizes(lib):
     L = lib.lib()
     assert L.tvs_workspace_bytes(1, 1, 64, None, 0) == 0          # too small
     assert L.tvs_workspace_bytes(1, 8193, 64, None, 0) == 0       # too large
-    assert L.tvs_workspace_bytes(1, 64, 64, None, 1) == 0         # step 1 keeps an FP32 dual
+    # a 16-bit step-1 dual needs less; Schwarz step 1 keeps an FP32 dual
+    assert 0 < L.tvs_workspace_bytes(1, 64, 64, None, 1) < L.tvs_workspace_bytes(1, 64, 64, None, 0)
+    dd4 = lib.make_decomp(2, 2, 4, 4)
+    assert L.tvs_workspace_bytes(1, 64, 64, ctypes.byref(dd4), 1) == 0
     assert L.tvs_workspace_bytes(2, 64, 64, None, 7) == 0         # no such storage
     assert L.tvs_workspace_bytes(2, 64, 64, None, 3) == lib.workspace_bytes(2, 64, 64, storage=1)
     # 16-bit storage halves the two step-2 dual buffers (and the Schwarz warm starts)
@@ -91,10 +94,10 @@ def test_bad_arguments_rejected_before_any_device_work(lib):
     dd = lib.make_decomp(4, 4, 8, 5)
     assert L.tvs_schwarz(2, fake, fake, 20, 20, 10.0, 1e-3, ctypes.byref(dd), ctypes.byref(it), fake, None, fake,
                          1 << 30, None, ctypes.byref(rep)) == 1
-    # 16-bit storage is a step-2 option; unknown storage values are argument errors
+    # a 16-bit dual is not an option of Schwarz step 1; unknown storage values are argument errors
     bf = lib.make_iter(10, storage=1)
-    assert L.tvs_step1(fake, 8, 8, 0.05, ctypes.byref(bf), fake, None, fake, 1 << 30, None, ctypes.byref(rep)) == 6
-    assert L.tvs_denoise(fake, 8, 8, 0.05, 10.0, 1e-3, ctypes.byref(bf), ctypes.byref(it), None, None, fake, fake,
+    dd2 = lib.make_decomp(2, 2, 2, 2)
+    assert L.tvs_schwarz(1, fake, None, 16, 16, 0.05, 1e-3, ctypes.byref(dd2), ctypes.byref(bf), fake, None, fake,
                          1 << 30, None, ctypes.byref(rep)) == 6
     odd = lib.make_iter(10, storage=9)
     assert L.tvs_step2(fake, fake, 8, 8, 10.0, 1e-3, ctypes.byref(odd), fake, None, fake, 1 << 30, None,

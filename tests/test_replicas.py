@@ -27,8 +27,9 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     local_ms = 100.0 * (rank + 1)                    # rank 1 is the slow one
-    value, total = bench.replica_value(local_ms, world, 4, dist, torch.device("cpu"))
-    img = bench.make_input(rank)
+    units = bench.head_units(bench.N, 250, 70)      # dual updates of one headline step (example counts)
+    value, total = bench.replica_value(local_ms, world, 4, units, dist, torch.device("cpu"))
+    img = bench.make_input(64, rank)
     out.put((rank, value, total, float(img[:8, :8].sum())))
     dist.barrier()
     dist.destroy_process_group()
@@ -46,7 +47,7 @@ def test_two_gloo_replicas_take_the_slowest_rank():
         p.join(timeout=60)
         assert p.exitcode == 0
     import bench
-    want = bench.work_units() * 2 * 4 / (200.0 / 1e3) / 1e9
+    want = bench.head_units(bench.N, 250, 70) * 2 * 4 / (200.0 / 1e3) / 1e9
     for rank, value, total, _ in res:
         assert total == 200.0
         assert value == pytest.approx(want, rel=1e-12)
@@ -55,6 +56,7 @@ def test_two_gloo_replicas_take_the_slowest_rank():
 
 def test_single_replica_needs_no_process_group():
     import bench
-    value, total = bench.replica_value(50.0, 1, 2)
+    units = bench.head_units(bench.N, 250, 70)
+    value, total = bench.replica_value(50.0, 1, 2, units)
     assert total == 50.0
-    assert value == pytest.approx(bench.work_units() * 2 / 0.05 / 1e9)
+    assert value == pytest.approx(units * 2 / 0.05 / 1e9)
