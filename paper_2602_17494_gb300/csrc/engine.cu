@@ -6,8 +6,12 @@
 //   * step 1 (TFS, Algorithm 1): each request runs its own chunk of updates,
 //     spread over a few side streams so that small images overlap;
 //   * step 2 (IRV1 under Algorithm 2 with Algorithm 3): all live step-2
-//     requests share every launch -- one small-subdomain tile launch and one
-//     strip launch per outer iteration cover the subdomains of all of them;
+//     requests share one persistent cooperative launch per engine step that
+//     sweeps the subdomain tiles of all of them for check_every outer
+//     iterations (grid barriers between the tile and strip phases); with an
+//     even check_every that launch and every request's check are captured
+//     once per set of resident step-2 requests into a CUDA graph, replayed
+//     while the set is unchanged;
 //   * every engine step ends with one stream synchronization; requests whose
 //     relative duality gap reached the tolerance move on (or finish: d is
 //     written to the caller's buffer and the pool block is released).
@@ -27,6 +31,7 @@ namespace tvs {
 namespace {
 
 constexpr int kSideStreams = 16;
+constexpr int kCapStreams = 8;    // private streams of the captured step-2 checks
 
 // First-fit allocator over [0, size) of the caller's pool (256-byte units).
 class PoolAlloc {
@@ -146,6 +151,13 @@ struct EngineImpl {
     double* host_red = nullptr;       // pinned [max_live][kRedSlots]
     TileImg* host_imgs = nullptr;     // pinned [2 * max_live]
     TileImg* dev_imgs = nullptr;      // head of the pool
+    unsigned* dev_sync = nullptr;     // pool head: [0, 2) grid barrier, [2] error word, [3] rounding-seed counter
+    unsigned* host_err = nullptr;     // pinned copy of the error word
+    cudaStream_t cap[kCapStreams] = {};
+    cudaStream_t gcap = nullptr;      // private stream the step-2 chunk is captured on
+    cudaEvent_t ev_cap[kCapStreams] = {};
+    cudaGraphExec_t g2 = nullptr;     // captured step-2 chunk of the set g2_set
+    std::vector<uintptr_t> g2_set;    // per request: id, both dual buffers, result slot
     std::vector<int> free_slots;
     int next_side = 0;
 
@@ -178,7 +190,7 @@ static tvs_status engine_check_cfg(const tvs_engine_config* c) {
 }
 
 static size_t engine_header_bytes(const tvs_engine_config* c) {
-    return round_up_sz(2 * (size_t)c->max_live * sizeof(TileImg), 256);
+    return round_up_sz(2 * (size_t)c->max_live * sizeof(TileImg), 256) + 256;   // descriptors, sync words
 }
 
 extern "C" {
@@ -210,12 +222,21 @@ tvs_status tvs_engine_create(const tvs_engine_config* cfg, void* pool, size_t po
     e->pool_bytes = pool_bytes - head;
     e->stream = stream;
     e->dev_imgs = static_cast<TileImg*>(pool);
+    e->dev_sync = reinterpret_cast<unsigned*>(static_cast<char*>(pool) +
+                                              round_up_sz(2 * (size_t)cfg->max_live * sizeof(TileImg), 256));
     bool ok = cudaHostAlloc(reinterpret_cast<void**>(&e->host_red), (size_t)cfg->max_live * kRedSlots * sizeof(double),
                             cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(reinterpret_cast<void**>(&e->host_imgs), 2 * (size_t)cfg->max_live * sizeof(TileImg),
                             cudaHostAllocDefault) == cudaSuccess &&
               cudaEventCreateWithFlags(&e->ev_main, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&e->ev_s2, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&e->ev_s2, cudaEventDisableTiming) == cudaSuccess &&
+              cudaHostAlloc(reinterpret_cast<void**>(&e->host_err), sizeof(unsigned), cudaHostAllocDefault) ==
+                  cudaSuccess &&
+              cudaMemsetAsync(e->dev_sync, 0, 4 * sizeof(unsigned), stream) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&e->gcap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < kCapStreams; ++i)
+        ok = cudaStreamCreateWithFlags(&e->cap[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->ev_cap[i], cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < kSideStreams; ++i)
         ok = cudaStreamCreateWithFlags(&e->side[i], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&e->ev_side[i], cudaEventDisableTiming) == cudaSuccess;
@@ -263,6 +284,16 @@ void tvs_engine_destroy(tvs_engine* h) {
             }
             if (e->ev_side[i]) cudaEventDestroy(e->ev_side[i]);
         }
+        if (e->g2) cudaGraphExecDestroy(e->g2);
+        for (int i = 0; i < kCapStreams; ++i) {
+            if (e->cap[i]) {
+                cudaStreamSynchronize(e->cap[i]);
+                cudaStreamDestroy(e->cap[i]);
+            }
+            if (e->ev_cap[i]) cudaEventDestroy(e->ev_cap[i]);
+        }
+        if (e->gcap) cudaStreamDestroy(e->gcap);
+        if (e->host_err) cudaFreeHost(e->host_err);
         if (e->ev_main) cudaEventDestroy(e->ev_main);
         if (e->ev_s2) cudaEventDestroy(e->ev_s2);
         if (e->host_red) cudaFreeHost(e->host_red);
@@ -384,18 +415,70 @@ static tvs_status step1_to_step2(EngineImpl* e, Request* r) {
     return TVS_OK;
 }
 
-// All live step-2 requests: check_every outer iterations in shared launches,
-// then one check per request.
-static tvs_status step2_chunk(EngineImpl* e, std::vector<Request*>& rs) {
-    if (rs.empty()) return TVS_OK;
+// Enqueues one step-2 chunk of the requests rs: the persistent sweep of n
+// outer iterations on the main stream, then each request's check (update
+// kernel in check mode, reduction, copy of the result row to pinned memory)
+// on a side stream (cap: the private capture streams, joined back into the
+// main stream).  The checks read p where the chunk leaves it (cur2 after an
+// even n, nxt2 after an odd one).
+static tvs_status step2_enqueue(EngineImpl* e, const std::vector<Request*>& rs, int nsub, int tx, int ty, int n,
+                                bool cap, cudaStream_t ms) {
     const tvs_engine_config& c = e->cfg;
+    const int nimg = (int)rs.size();
+    TVS_CUDA(schwarz2_persist_multi(c.it2.storage, e->dev_imgs, nimg, nsub, tx, ty, c.k_inner, (float)c.it2.t, n,
+                                    e->dev_sync, e->dev_sync + 2, e->dev_sync + 3, ms));
+    TVS_CUDA(cudaEventRecord(e->ev_s2, ms));
+    bool waited[kSideStreams] = {};
+    for (int i = 0; i < nimg; ++i) {
+        Request* r = rs[i];
+        const Step2Layout& L = r->L2;
+        const int si = cap ? i % kCapStreams : r->side;
+        cudaStream_t ss = cap ? e->cap[si] : e->side[si];
+        if (!waited[si]) {
+            TVS_CUDA(cudaStreamWaitEvent(ss, e->ev_s2, 0));
+            waited[si] = true;
+        }
+        void* p = (n & 1) ? r->nxt2 : r->cur2;
+        TVS_CUDA(launch_irv1_update(p, nullptr, L.f2, L.R, L.C, L.P, L.plane, (float)c.it2.t, (float)c.alpha, true,
+                                    false, nullptr, 0, L.red.partial, L.st, 0u, L.red.err, ss));
+        TVS_CUDA(finalize_red(L.red, irv1_blocks(L.R, L.C), ss));
+        TVS_CUDA(cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ss));
+    }
+    if (cap)
+        for (int si = 0; si < kCapStreams; ++si)
+            if (waited[si]) {
+                TVS_CUDA(cudaEventRecord(e->ev_cap[si], e->cap[si]));
+                TVS_CUDA(cudaStreamWaitEvent(ms, e->ev_cap[si], 0));
+            }
+    return TVS_OK;
+}
+
+// All live step-2 requests: check_every outer iterations in one persistent
+// launch, then one check per request.  With an even check_every the
+// descriptors of a set of requests do not change from step to step, so the
+// chunk is captured into a CUDA graph the second time the same set comes
+// round and replayed while the set lasts.
+static tvs_status step2_chunk(EngineImpl* e, std::vector<Request*>& rs) {
+    if (rs.empty()) {
+        if (e->g2) TVS_CUDA(cudaGraphExecDestroy(e->g2));
+        e->g2 = nullptr;
+        e->g2_set.clear();
+        return TVS_OK;
+    }
+    const tvs_engine_config& c = e->cfg;
+    std::vector<uintptr_t> key;
+    for (Request* r : rs) {
+        key.push_back((uintptr_t)r->id);
+        key.push_back(reinterpret_cast<uintptr_t>(r->cur2));
+        key.push_back(reinterpret_cast<uintptr_t>(r->nxt2));
+        key.push_back((uintptr_t)r->slot);
+    }
     const int nimg = (int)rs.size();
     int nsub = 0, tx = 1, ty = 1;
     // every request advances check_every outer iterations (its cap may be
     // passed by less than one chunk)
     const int n = c.it2.check_every;
-    uint32_t seed = 0;
-    for (Request* r : rs) seed = hash32(seed ^ (uint32_t)r->it2 ^ (uint32_t)r->id);
     for (int i = 0; i < nimg; ++i) {
         Request* r = rs[i];
         const Schwarz2State& S2 = r->S2;
@@ -411,29 +494,44 @@ static tvs_status step2_chunk(EngineImpl* e, std::vector<Request*>& rs) {
         tx = std::max(tx, S2.tx);
         ty = std::max(ty, S2.ty);
     }
-    TVS_CUDA(cudaMemcpyAsync(e->dev_imgs, e->host_imgs, 2 * (size_t)nimg * sizeof(TileImg), cudaMemcpyHostToDevice,
-                             e->stream));
-    // the host array is rewritten next step, after this step's synchronization
-    TVS_CUDA(schwarz2_iterate_multi(c.it2.storage, e->dev_imgs, nimg, nsub, tx, ty, c.k_inner, (float)c.it2.t, n,
-                                    seed, e->stream));
-    // the per-request checks are independent small launches: they run on the
-    // requests' side streams, after the shared launches, so that they overlap
-    TVS_CUDA(cudaEventRecord(e->ev_s2, e->stream));
-    bool waited[kSideStreams] = {};
+    const bool graph_ok = graphs_enabled() && (n & 1) == 0;
+    if (graph_ok && e->g2 && e->g2_set == key) {
+        TVS_CUDA(cudaGraphLaunch(e->g2, e->stream));       // descriptors already in place for this set
+    } else {
+        const bool capture = graph_ok && e->g2_set == key;  // the same set a second time: capture it
+        if (e->g2) {
+            TVS_CUDA(cudaGraphExecDestroy(e->g2));
+            e->g2 = nullptr;
+        }
+        // the host array is rewritten next step, after this step's synchronization
+        TVS_CUDA(cudaMemcpyAsync(e->dev_imgs, e->host_imgs, 2 * (size_t)nimg * sizeof(TileImg),
+                                 cudaMemcpyHostToDevice, e->stream));
+        if (capture) {
+            // captured on a private stream (the caller's may be the legacy
+            // default stream, which cannot be captured), launched on the caller's
+            cudaGraph_t g = nullptr;
+            TVS_CUDA(cudaStreamBeginCapture(e->gcap, cudaStreamCaptureModeThreadLocal));
+            const tvs_status st = step2_enqueue(e, rs, nsub, tx, ty, n, true, e->gcap);
+            const cudaError_t ce = cudaStreamEndCapture(e->gcap, &g);
+            if (st != TVS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            TVS_CUDA(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&e->g2, g, 0);
+            cudaGraphDestroy(g);
+            TVS_CUDA(ie);
+            TVS_CUDA(cudaGraphLaunch(e->g2, e->stream));
+        } else {
+            const tvs_status st = step2_enqueue(e, rs, nsub, tx, ty, n, false, e->stream);
+            if (st != TVS_OK) return st;
+        }
+        e->g2_set = key;
+    }
+    TVS_CUDA(cudaMemcpyAsync(e->host_err, e->dev_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, e->stream));
     for (Request* r : rs) {
         if (n & 1) std::swap(r->cur2, r->nxt2);
         r->it2 += n;
-        const Step2Layout& L = r->L2;
-        cudaStream_t ss = e->side[r->side];
-        if (!waited[r->side]) {
-            TVS_CUDA(cudaStreamWaitEvent(ss, e->ev_s2, 0));
-            waited[r->side] = true;
-        }
-        TVS_CUDA(launch_irv1_update(r->cur2, nullptr, L.f2, L.R, L.C, L.P, L.plane, (float)c.it2.t, (float)c.alpha,
-                                    true, false, nullptr, 0, L.red.partial, L.st, 0u, L.red.err, ss));
-        TVS_CUDA(finalize_red(L.red, irv1_blocks(L.R, L.C), ss));
-        TVS_CUDA(cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
-                                 cudaMemcpyDeviceToHost, ss));
         r->checked = true;
     }
     return TVS_OK;
@@ -468,6 +566,10 @@ extern "C" tvs_status tvs_engine_step(tvs_engine* h, long long* done_ids, tvs_re
         TVS_CUDA(cudaStreamWaitEvent(e->stream, e->ev_side[i], 0));
     }
     TVS_CUDA(cudaStreamSynchronize(e->stream));
+    if (!s2.empty() && *e->host_err) {
+        set_error_text("a grid barrier of the persistent Schwarz sweep gave up");
+        return TVS_ERR_TIMEOUT;
+    }
     // transitions
     std::vector<Request*> finished;
     for (Request* r : e->live) {

@@ -116,6 +116,14 @@ struct TileImg {
 // swapped).  tx, ty: thread block covering the largest subdomain.
 cudaError_t schwarz2_iterate_multi(int storage, const TileImg* imgs_dev, int nimg, int nsub_total, int tx, int ty,
                                    int k, float t, int n_outer, uint32_t seed0, cudaStream_t s);
+// The same n_outer outer iterations as one persistent cooperative launch (grid
+// barriers between the tile and strip phases); bar: 2 device words (zeroed by
+// the call), err: bit 1 set if a barrier wait gave up, seed_ctr: device
+// counter of the 16-bit rounding seeds (advanced by n_outer).  Capturable in
+// a CUDA graph.
+cudaError_t schwarz2_persist_multi(int storage, const TileImg* imgs_dev, int nimg, int nsub_total, int tx, int ty,
+                                   int k, float t, int n_outer, unsigned* bar, unsigned* err, uint32_t* seed_ctr,
+                                   cudaStream_t s);
 // Block shape of the small-subdomain kernel for subdomains up to hmax x wmax
 // (0 if they need the cluster kernel); q row pitch and shared memory bytes.
 int small_tile_shape(int hmax, int wmax, int* tx, int* ty, int* qp, size_t* smem);

@@ -239,13 +239,13 @@ struct SmallTileArgs {
     uint32_t seed;
 };
 
-// Index of the image of this CTA in a multi-image launch: the largest first <= blockIdx.x.
+// Index of the image of work item vb in a multi-image launch: the largest first <= vb.
 template <class S>
-__device__ __forceinline__ int tile_index(const SmallTileArgs<S>& a) {
+__device__ __forceinline__ int tile_index(const SmallTileArgs<S>& a, int vb) {
     int lo = 0, hi = a.nimg - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (a.imgs[mid].first <= (int)blockIdx.x) lo = mid;
+        if (a.imgs[mid].first <= vb) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -261,15 +261,9 @@ __device__ __forceinline__ float ramp_theta(const Axis& A, int k, int start, int
 }
 
 template <bool MULTI, class S>
-__device__ __forceinline__ const TileImg& tile_image(const SmallTileArgs<S>& a) {
+__device__ __forceinline__ const TileImg& tile_image(const SmallTileArgs<S>& a, int vb) {
     if (!MULTI) return a.one;   // parameter space: no indirection
-    int lo = 0, hi = a.nimg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.imgs[mid].first <= (int)blockIdx.x) lo = mid;
-        else hi = mid - 1;
-    }
-    return a.imgs[lo];
+    return a.imgs[tile_index(a, vb)];
 }
 
 // Rows of core k that no other subdomain's Gamma reaches: [excl_lo, excl_hi).
@@ -361,13 +355,18 @@ __device__ __forceinline__ void small_tile_update(float2 (&VX)[RP][CW], float2 (
 // RH * TY rows; the CTAs exchange the halo rows (v_y of the row above, z of
 // the row below) through distributed shared memory, with a cluster barrier
 // in place of the CTA barrier.
-template <class S, int MAXT, int MINB, bool MULTI, bool CL>
-__global__ void __launch_bounds__(MAXT, MINB)
-schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
+// The body of one CTA's work: vb is the work item (the CTA index of a
+// one-pass launch, a loop index of the persistent kernel); sm4 the dynamic
+// shared memory, hdr 8 shared ints.  COH: p^n and q are read through L2
+// (ld.global.cg) because other CTAs of the same launch wrote them.
+template <class S, bool MULTI, bool CL, bool COH>
+__device__ __forceinline__ void small_tile_body(const SmallTileArgs<S>& a, int vb, float4* sm4, int* hdr) {
     using St = Stor<S>;
+    auto ldp4 = [](const S* p) { return COH ? St::ld4g(p) : St::ld4(p); };
+    auto ldp1 = [](const S* p) { return COH ? St::ld1g(p) : St::ld1(p); };
+    auto ldq4 = [](const S* p) { return COH ? St::ld4g(p) : St::ld4c(p); };
     constexpr int RH = kSmallRH, CW = kSmallCW, RP = RH / 2;
     static_assert(RH % 2 == 0 && CW == 4, "vertical pixel pairs, one float4 of q per row");
-    extern __shared__ float4 sm4[];
     const int TX = blockDim.x, TY = blockDim.y;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NB = TY * RH * TX;                  // float4 slots per array
@@ -383,23 +382,20 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     float* sthy = sthx + CW * TX + 1;             // theta_y of rows y0 - 1 .. y0 + 4 TY - 1
 
     static_assert(!(CL && MULTI), "cluster mode runs one image");
-    pdl_wait();
-    pdl_trigger();
     int rank = 0, ncl = 1;
     if (CL) {
         const cg::cluster_group cl = cg::this_cluster();
         rank = (int)cl.block_rank();
         ncl = (int)cl.num_blocks();
     }
-    // the subdomain and its extents, once per CTA: [0] image, [1] sub, [2] my,
-    // [3] mx, [4] y0, [5] y1, [6] x0, [7] x1
-    __shared__ int hdr[8];
+    // the subdomain and its extents, once per work item: [0] image, [1] sub,
+    // [2] my, [3] mx, [4] y0, [5] y1, [6] x0, [7] x1
     {
         const int tid = ty * TX + tx;
         if (tid < 4) {
-            const int img = MULTI ? tile_index(a) : 0;
+            const int img = MULTI ? tile_index(a, vb) : 0;
             const TileImg& I = MULTI ? a.imgs[img] : a.one;
-            const int sub = CL ? (int)blockIdx.x / ncl : (int)blockIdx.x - I.first;
+            const int sub = CL ? vb / ncl : vb - I.first;
             const int my = sub / I.ax.M, mx = sub - my * I.ax.M;
             const int v = tid == 0 ? I.ay.start(my) : tid == 1 ? I.ay.end(my) : tid == 2 ? I.ax.start(mx) : I.ax.end(mx);
             hdr[4 + tid] = v;
@@ -475,7 +471,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         for (int c = 0; c < CW; ++c) {
             const int i = ib - 1, j = jb + c;
             wyu[c] = (i >= 0 && i <= N2 - 2 && j < N1)
-                         ? (1.0f - thyu * thx[c]) * St::ld1(py + (size_t)i * im.pitch + j) : 0.0f;
+                         ? (1.0f - thyu * thx[c]) * ldp1(py + (size_t)i * im.pitch + j) : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
@@ -485,8 +481,8 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
             if (row_ok) {
                 const size_t o = (size_t)i * im.pitch + jb;
                 if (vec) {
-                    const float4 u = St::ld4(px + o);
-                    const float4 w = St::ld4(py + o);
+                    const float4 u = ldp4(px + o);
+                    const float4 w = ldp4(py + o);
                     const float4 f = __ldg(reinterpret_cast<const float4*>(im.f2 + o));
                     vpx[0] = u.x; vpx[1] = u.y; vpx[2] = u.z; vpx[3] = u.w;
                     vpy[0] = w.x; vpy[1] = w.y; vpy[2] = w.z; vpy[3] = w.w;
@@ -495,8 +491,8 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
 #pragma unroll
                     for (int c = 0; c < CW; ++c)
                         if (jb + c < N1) {
-                            vpx[c] = St::ld1(px + o + c);
-                            vpy[c] = St::ld1(py + o + c);
+                            vpx[c] = ldp1(px + o + c);
+                            vpy[c] = ldp1(py + o + c);
                             vf[c] = __ldg(im.f2 + o + c);
                         }
                 }
@@ -505,7 +501,7 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
             spy[(r * TY + ty) * TX + tx] = make_float4(vpy[0], vpy[1], vpy[2], vpy[3]);
             float wl = 0.0f;
             if (row_ok && jb >= 1 && jb - 1 <= N1 - 2)
-                wl = (1.0f - thy[r] * thxl) * St::ld1(px + (size_t)i * im.pitch + jb - 1);
+                wl = (1.0f - thy[r] * thxl) * ldp1(px + (size_t)i * im.pitch + jb - 1);
             float gr[CW];
 #pragma unroll
             for (int c = 0; c < CW; ++c) {
@@ -544,8 +540,8 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         float4 ux = make_float4(0.f, 0.f, 0.f, 0.f), uy = ux;
         if (ib + r < y1 && tx * CW < im.qp) {   // (a multi-image block may be wider than this image's rows)
             const size_t qo = (size_t)(ib + r - y0) * im.qp + tx * CW;
-            ux = St::ld4c(qx + qo);
-            uy = St::ld4c(qy + qo);
+            ux = ldq4(qx + qo);
+            uy = ldq4(qy + qo);
         }
         const float ax4[CW] = {ux.x, ux.y, ux.z, ux.w}, ay4[CW] = {uy.x, uy.y, uy.z, uy.w};
         // D^- reads v_x as zero in the last column and v_y in the last row;
@@ -683,6 +679,16 @@ schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     }
 }
 
+template <class S, int MAXT, int MINB, bool MULTI, bool CL>
+__global__ void __launch_bounds__(MAXT, MINB)
+schwarz2_small_tile_kernel(const __grid_constant__ SmallTileArgs<S> a) {
+    extern __shared__ float4 sm4[];
+    __shared__ int hdr[8];
+    pdl_wait();
+    pdl_trigger();
+    small_tile_body<S, MULTI, CL, false>(a, (int)blockIdx.x, sm4, hdr);
+}
+
 // Sum over the subdomains l whose Gamma_l contains (i, j) of q_l(i, j), for a
 // pixel of core (my, mx): only the 3 x 3 subdomains around it can reach it.
 struct QNeighbours {
@@ -746,7 +752,7 @@ static int sm_count() {
 // p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum_l q_l on up to NB pixels of
 // one column (rows i, i + di, ...): every load is issued before the first
 // store, so a thread keeps NB pixels' loads in flight.
-template <class S>
+template <class S, bool COH = false>
 struct StripCombine {
     static constexpr int NB = 4;
     const S* __restrict__ pin;
@@ -761,6 +767,7 @@ struct StripCombine {
     __device__ __forceinline__ void run(const int (&nby)[3][2], const int (&nbx)[3][3], int i, int di, int n,
                                         int j) const {
         using St = Stor<S>;
+        auto ld = [](const S* p) { return COH ? St::ld1g(p) : St::ld1(p); };
         float sx[NB], sy[NB], ux[NB], uy[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -768,8 +775,8 @@ struct StripCombine {
             if (b >= n) continue;
             const int ii = i + b * di;
             const size_t o = (size_t)ii * pitch + j;
-            ux[b] = St::ld1(pin + o);
-            uy[b] = St::ld1(pin + plane + o);
+            ux[b] = ld(pin + o);
+            uy[b] = ld(pin + plane + o);
 #pragma unroll
             for (int da = 0; da < 3; ++da) {
                 if (ii < nby[da][0] || ii >= nby[da][1]) continue;
@@ -778,8 +785,8 @@ struct StripCombine {
                     if (j < nbx[db][0] || j >= nbx[db][2]) continue;
                     const int l = (my - 1 + da) * M1 + (mx - 1 + db);
                     const size_t off = ((size_t)l * 2 * hmax + (ii - nby[da][0])) * qp + (j - nbx[db][1]);
-                    sx[b] += St::ld1(q + off);
-                    sy[b] += St::ld1(q + off + qplane);
+                    sx[b] += ld(q + off);
+                    sy[b] += ld(q + off + qplane);
                 }
             }
         }
@@ -793,14 +800,12 @@ struct StripCombine {
         }
     }
 };
-template <class S, bool MULTI>
-__global__ void __launch_bounds__(kStripThreads, 8)
-schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
-    pdl_wait();
-    pdl_trigger();
-    using St = Stor<S>;
-    __shared__ int nbx[3][3], nby[3][2];   // columns: start, start & ~3, end; rows: start, end (mx-1..mx+1, my-1..my+1)
-    const TileImg& im = tile_image<MULTI>(a);
+// The strip work of subdomain work item vb, chunk ch of nch, with threads
+// t = 0 .. nthr - 1 of the CTA (nbx, nby: shared).  COH as for the tile body.
+template <class S, bool MULTI, bool COH>
+__device__ __forceinline__ void strip_body(const SmallTileArgs<S>& a, int vb, int ch, int nch, int t, int nthr,
+                                           int (&nbx)[3][3], int (&nby)[3][2]) {
+    const TileImg& im = tile_image<MULTI>(a, vb);
     const S* __restrict__ pin = static_cast<const S*>(im.p);
     S* __restrict__ pout = static_cast<S*>(im.pnext);
     const S* __restrict__ q = static_cast<const S*>(im.q);
@@ -808,9 +813,8 @@ schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
     const long plane = im.plane;
     const Axis& ay = im.ay;
     const Axis& ax = im.ax;
-    const int sub = blockIdx.x - im.first;
+    const int sub = vb - im.first;
     const int my = sub / ax.M, mx = sub - my * ax.M;
-    const int t = threadIdx.x;
     if (t < 6) {   // one extent per thread
         const int d = t % 3, b = (t < 3 ? mx : my) - 1 + d;
         const Axis& A = t < 3 ? ax : ay;
@@ -826,9 +830,8 @@ schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         }
     }
     __syncthreads();
-    StripCombine<S> cb{pin, pout, q, pitch, plane, (size_t)hmax * qp, hmax, qp, ax.M, my, mx, im.ahat,
-                       a.seed ^ 0xa511e9b3U};
-    const int nch = gridDim.y, ch = blockIdx.y;
+    StripCombine<S, COH> cb{pin, pout, q, pitch, plane, (size_t)hmax * qp, hmax, qp, ax.M, my, mx, im.ahat,
+                            a.seed ^ 0xa511e9b3U};
     const int cy0 = ay.core(my);
     const int cx0 = ax.core(mx), cx1 = mx == ax.M - 1 ? ax.L : ax.core(mx + 1);
     // horizontal band: s rows x this chunk's share of the core's columns;
@@ -839,22 +842,118 @@ schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
         const int j0 = cx0 + (int)((long long)W * ch / nch), j1 = cx0 + (int)((long long)W * (ch + 1) / nch);
         const int i0 = cy0 - (ay.s + 1) / 2;
         const int wc = j1 - j0, items = wc * ((ay.s + NB - 1) / NB);
-        for (int it = t; it < items; it += kStripThreads) {
+        for (int it = t; it < items; it += nthr) {
             const int g = it / wc, r = g * NB, j = j0 + (it - g * wc);
             cb.run(nby, nbx, i0 + r, 1, ay.s - r, j);
         }
     }
     // vertical band: this chunk's share of the exclusive rows x s columns;
     // a thread takes one column and up to 4 rows (rstep apart) at a time
-    if (mx > 0 && ax.s > 0 && t < (kStripThreads / ax.s) * ax.s) {
+    if (mx > 0 && ax.s > 0 && t < (nthr / ax.s) * ax.s) {
         const int ey0 = excl_lo(ay, my), ey1 = excl_hi(ay, my);
         const int H = max(ey1 - ey0, 0);
         const int r0 = ey0 + (int)((long long)H * ch / nch), r1 = ey0 + (int)((long long)H * (ch + 1) / nch);
-        const int rstep = kStripThreads / ax.s;
+        const int rstep = nthr / ax.s;
         const int j = cx0 - (ax.s + 1) / 2 + t % ax.s;
         for (int i = r0 + t / ax.s; i < r1; i += StripCombine<S>::NB * rstep)
             cb.run(nby, nbx, i, rstep, (r1 - i + rstep - 1) / rstep, j);
     }
+}
+
+template <class S, bool MULTI>
+__global__ void __launch_bounds__(kStripThreads, 8)
+schwarz2_strip_kernel(const __grid_constant__ SmallTileArgs<S> a) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ int nbx[3][3], nby[3][2];   // columns: start, start & ~3, end; rows: start, end (mx-1..mx+1, my-1..my+1)
+    strip_body<S, MULTI, false>(a, (int)blockIdx.x, (int)blockIdx.y, (int)gridDim.y, (int)threadIdx.x, kStripThreads,
+                                nbx, nby);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of the multi-image sweep: one cooperative launch runs
+// n_outer outer iterations of Algorithm 2 over the small subdomains of every
+// image.  Each CTA walks the tile work items blockIdx.x, blockIdx.x +
+// gridDim.x, ..., then all CTAs meet at a grid barrier, walk the strip work
+// items, and meet again before the next outer iteration reads p^{n+1}.
+// The launch is cooperative, so every CTA is resident and the barrier is
+// reached by all of them; its wait is still bounded (about two seconds of SM
+// clock), after which it sets bit 1 of *err and goes on.  p^n and q are read
+// through L2 (other CTAs of the launch wrote them).  The rounding seed of
+// 16-bit stores comes from *seed_ctr, which the launch advances by n_outer,
+// so a replayed graph of the launch draws new bits every time.
+// ---------------------------------------------------------------------------
+constexpr long long kBarrierCycles = 4000000000LL;   // about two seconds of SM clock
+
+template <class S>
+struct PersistArgs {
+    const TileImg* imgs;     // 2 * nimg descriptors: even / odd outer iterations
+    int nimg, nsub, k, n_outer;
+    float t;
+    unsigned* bar;           // [0] arrivals, [1] generation
+    unsigned* err;           // bit 1: a grid barrier gave up
+    uint32_t* seed_ctr;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;            // the generation before this CTA arrives
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) + 1u == nblocks) {
+            atomicExch(bar, 0u);            // the last to arrive resets the count, then releases the rest
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicOr(err, 2u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <class S, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+schwarz2_persistent_kernel(const __grid_constant__ PersistArgs<S> pa) {
+    extern __shared__ float4 sm4[];
+    __shared__ int hdr[8];
+    __shared__ int nbx[3][3], nby[3][2];
+    __shared__ uint32_t seed_base;
+    if (threadIdx.x == 0 && threadIdx.y == 0) seed_base = *(volatile uint32_t*)pa.seed_ctr;
+    __syncthreads();
+    const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int n = 0; n < pa.n_outer; ++n) {
+        SmallTileArgs<S> a{};
+        a.imgs = pa.imgs + (n & 1) * pa.nimg;
+        a.nimg = pa.nimg;
+        a.k = pa.k;
+        a.t = pa.t;
+        a.seed = hash32(seed_base + (uint32_t)n + 1u);
+        for (int vb = blockIdx.x; vb < pa.nsub; vb += gridDim.x) {
+            __syncthreads();   // the previous item's shared memory is no longer read
+            small_tile_body<S, true, false, true>(a, vb, sm4, hdr);
+        }
+        if (!grid_barrier(pa.bar, gridDim.x, pa.err)) return;
+        for (int vb = blockIdx.x; vb < pa.nsub; vb += gridDim.x) {
+            __syncthreads();
+            strip_body<S, true, true>(a, vb, 0, 1, tid, nthr, nbx, nby);
+        }
+        if (!grid_barrier(pa.bar, gridDim.x, pa.err)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) *pa.seed_ctr = seed_base + (uint32_t)pa.n_outer;
 }
 
 // p^{n+1} = (1 - alpha_hat) p^n + alpha_hat sum over the subdomains l whose
@@ -1009,6 +1108,47 @@ cudaError_t schwarz2_iterate_multi(int storage, const TileImg* imgs_dev, int nim
     if (tx * ty > kSmallMaxThreads || nimg < 1) return cudaErrorInvalidValue;
     TVS_STORAGE_SWITCH(storage, {
         return schwarz2_iterate_multi_t<S>(imgs_dev, nimg, nsub_total, tx, ty, k, t, n_outer, seed0, s);
+    })
+    return cudaErrorInvalidValue;
+}
+
+template <class S, int MAXT, int MINB>
+static cudaError_t launch_persistent_t(const PersistArgs<S>& pa, int tx, int ty, cudaStream_t s) {
+    auto kern = schwarz2_persistent_kernel<S, MAXT, MINB>;
+    const size_t smem = small_tile_smem_bytes(tx, ty);
+    static std::once_flag once;
+    std::call_once(once, [kern] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MINB == 2 ? 110 * 1024 : 200 * 1024);
+    });
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tx * ty, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(pa.nsub, per_sm * sm_count());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(tx, ty, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: the grid barriers are reached
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ProfScope ps(kProfSchwarzTile, s);
+    return cudaLaunchKernelEx(&cfg, kern, pa);
+}
+
+cudaError_t schwarz2_persist_multi(int storage, const TileImg* imgs_dev, int nimg, int nsub_total, int tx, int ty,
+                                   int k, float t, int n_outer, unsigned* bar, unsigned* err, uint32_t* seed_ctr,
+                                   cudaStream_t s) {
+    if (tx * ty > kSmallMaxThreads || nimg < 1 || n_outer < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    TVS_STORAGE_SWITCH(storage, {
+        const PersistArgs<S> pa{imgs_dev, nimg, nsub_total, k, n_outer, t, bar, err, seed_ctr};
+        if (tx * ty <= kSmallPairThreads) return launch_persistent_t<S, kSmallPairThreads, 2>(pa, tx, ty, s);
+        return launch_persistent_t<S, kSmallMaxThreads, 1>(pa, tx, ty, s);
     })
     return cudaErrorInvalidValue;
 }

@@ -347,8 +347,11 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
     }
     __syncthreads();
 
-    KSum ks[4];
-    float pmax = 0.0f, dmax = 0.0f;
+    // check sums: each thread adds the 8 terms of its 4 points and 2 channels
+    // in FP32 (relative error of a few ulp); the block reduction carries FP32
+    // pairs and the cross-block sum is FP64
+    float ks[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float pmax2 = 0.0f, dmax = 0.0f;
 #pragma unroll
     for (int rr = ty; rr < kTY; rr += kBY) {
         const int i = i0 + rr, j = j0 + tx;
@@ -374,8 +377,10 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
                     const float s2 = fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1e-30f));
                     const float inv = rcp_ftz(fmaf(t, s2 * rsqrt_ftz(s2), 1.0f));
                     const float vx = fmaf(t, gx[k], pv[2 * k]) * inv, vy = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
-                    Stor<SP>::st1(pout + (size_t)(2 * k) * plane + o, vx, rkey(seed, o, 2 * k));
-                    Stor<SP>::st1(pout + (size_t)(2 * k + 1) * plane + o, vy, rkey(seed, o, 2 * k + 1));
+                    // 16-bit dual: one hash per point, 8 random bits for each of its four planes
+                    const uint32_t h = sizeof(SP) == 4 ? 0u : rkey(seed, o, 0);
+                    Stor<SP>::st1r8(pout + (size_t)(2 * k) * plane + o, vx, (h >> (16 * k)) & 0xffU);
+                    Stor<SP>::st1r8(pout + (size_t)(2 * k + 1) * plane + o, vy, (h >> (16 * k + 8)) & 0xffU);
                 }
             }
             if (WRITE_TAU) {
@@ -386,13 +391,14 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const float a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
-                    const float ng = sqrtf(a * a + b * b);
-                    ks[0].add(ng);
-                    ks[1].add(ng - (a * px + b * py));
-                    ks[2].add(zc[k] * zc[k]);
+                    const float s2 = fmaf(a, a, fmaf(b, b, 1e-30f));
+                    const float ng = s2 * rsqrt_ftz(s2);            // |grad z_k| (hardware rsqrt, ~2 ulp)
+                    ks[0] += ng;
+                    ks[1] += ng - fmaf(a, px, b * py);
+                    ks[2] = fmaf(zc[k], zc[k], ks[2]);
                     const float zf = zc[k] + sf[k * kBoxFloats + ob];
-                    ks[3].add(zf * zf);
-                    pmax = fmaxf(pmax, sqrtf(px * px + py * py));
+                    ks[3] = fmaf(zf, zf, ks[3]);
+                    pmax2 = fmaxf(pmax2, fmaf(px, px, py * py));
                 }
                 // div z with the zero-extension rule of D^- (z_1 read as zero in
                 // the last column, z_2 in the last row)
@@ -408,7 +414,7 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
         FF acc[kRedSlots];
 #pragma unroll
         for (int k = 0; k < kRedSlots; ++k)
-            acc[k] = k < 4 ? ks[k].pair() : FF{k == 4 ? pmax : (k == 5 ? dmax : 0.0f), 0.0f};
+            acc[k] = k < 4 ? FF{ks[k], 0.0f} : FF{k == 4 ? sqrtf(pmax2) : (k == 5 ? dmax : 0.0f), 0.0f};
         block_reduce_store_ff<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
     }
 }

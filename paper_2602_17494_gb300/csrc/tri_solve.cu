@@ -305,7 +305,8 @@ cudaError_t launch_n(float* S, int rows, int cols, int pitch, const float4* tab,
 // 4 W (anti-causal value just after the chunk); then K_c of column 0 [chunk]
 // and (mu, mean w) of column 0.
 // ---------------------------------------------------------------------------
-constexpr int kChunkWarps = 8;
+constexpr int kChunkWarps = 8;    // warps (chunks) per CTA of the sum and apply kernels
+constexpr int kScanWarps = 16;    // warps (chunk ranges) per CTA of the scan kernel
 
 struct ChunkBufs {
     float *h, *a, *g, *cin, *win, *k0, *par;
@@ -333,26 +334,47 @@ tri_chunk_sum_kernel(const float* __restrict__ S, int rows, int cols, int pitch,
     const int n = min(kTriChunk, rows - i0);
     const float* src = S + (size_t)i0 * pitch + k;
     float v[kTriChunk];
+    float h = 0.f, an = 0.f, g = 0.f, kk = 0.f;   // an: the causal value at the chunk's last row n - 1
+    const bool k0 = k == 0;                        // the k_x = 0 column also needs K
+    if (n == kTriChunk) {
+        // full chunk: no row predicates
 #pragma unroll
-    for (int i = 0; i < kTriChunk; ++i) v[i] = i < n ? __ldg(src + (size_t)i * pitch) : 0.f;
-    float h = 0.f;
+        for (int i = 0; i < kTriChunk; ++i) v[i] = __ldg(src + (size_t)i * pitch);
 #pragma unroll
-    for (int i = kTriChunk - 1; i >= 0; --i)
-        if (i < n) h = rstep1(h, v[i], nq);
-    float p = 0.f, an = 0.f;                // an: the causal value at the chunk's last row n - 1
+        for (int i = kTriChunk - 1; i >= 0; --i) h = rstep1(h, v[i], nq);
+        float p = 0.f;
 #pragma unroll
-    for (int i = 0; i < kTriChunk; ++i) {
-        p = rstep1(p, v[i], nq);
-        v[i] = p;
-        if (i == n - 1) an = p;
-    }
-    float g = 0.f, kk = 0.f;
-#pragma unroll
-    for (int i = kTriChunk - 1; i >= 0; --i)
-        if (i < n) {
-            g = rstep1(g, v[i], nq);
-            kk = fmaf((float)(i + 1), v[i], kk);
+        for (int i = 0; i < kTriChunk; ++i) {
+            p = rstep1(p, v[i], nq);
+            v[i] = p;
         }
+        an = p;
+#pragma unroll
+        for (int i = kTriChunk - 1; i >= 0; --i) g = rstep1(g, v[i], nq);
+        if (k0) {
+#pragma unroll
+            for (int i = 0; i < kTriChunk; ++i) kk = fmaf((float)(i + 1), v[i], kk);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kTriChunk; ++i) v[i] = i < n ? __ldg(src + (size_t)i * pitch) : 0.f;
+#pragma unroll
+        for (int i = kTriChunk - 1; i >= 0; --i)
+            if (i < n) h = rstep1(h, v[i], nq);
+        float p = 0.f;
+#pragma unroll
+        for (int i = 0; i < kTriChunk; ++i) {
+            p = rstep1(p, v[i], nq);
+            v[i] = p;
+            if (i == n - 1) an = p;
+        }
+#pragma unroll
+        for (int i = kTriChunk - 1; i >= 0; --i)
+            if (i < n) {
+                g = rstep1(g, v[i], nq);
+                kk = fmaf((float)(i + 1), v[i], kk);
+            }
+    }
     const size_t o = (size_t)c * cols + k;
     cb.h[o] = h;
     cb.a[o] = an;
@@ -361,11 +383,12 @@ tri_chunk_sum_kernel(const float* __restrict__ S, int rows, int cols, int pitch,
 }
 
 // Per column: start values and the carries of every chunk.  lane = column,
-// warp w = chunks [w cpw, (w + 1) cpw).
-__global__ void __launch_bounds__(32 * kChunkWarps)
+// warp w = chunks [w cpw, (w + 1) cpw); kScanWarps warps, so that each
+// thread walks only a few chunks (the walks are sequential per column).
+__global__ void __launch_bounds__(32 * kScanWarps)
 tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float* __restrict__ base, int nch) {
-    __shared__ float sh_s1[kChunkWarps][32], sh_r2[kChunkWarps][32], sh_f[kChunkWarps][32], sh_m[kChunkWarps][32];
-    __shared__ float sh_b[kChunkWarps][32], sh_k[kChunkWarps];
+    __shared__ float sh_s1[kScanWarps][32], sh_r2[kScanWarps][32], sh_f[kScanWarps][32], sh_m[kScanWarps][32];
+    __shared__ float sh_b[kScanWarps][32], sh_k[kScanWarps];
     pdl_wait();
     pdl_trigger();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -373,7 +396,7 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     const bool live = k < cols;
     const ChunkBufs cb = chunk_bufs(base, nch, cols);
     const int L = rows;
-    const int cpw = (nch + kChunkWarps - 1) / kChunkWarps;
+    const int cpw = (nch + kScanWarps - 1) / kScanWarps;
     const int c0 = min(nch, w * cpw), c1 = min(nch, c0 + cpw);
     const float4 ta = live ? __ldg(&tab[2 * k]) : make_float4(0.f, 0.f, 1.f, 1.f);
     const float4 tb = live ? __ldg(&tab[2 * k + 1]) : make_float4(1.f, 0.f, 0.f, 0.f);
@@ -403,6 +426,7 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     // phase 1: S1 = sum r^(i0) h, R2 = sum r^(L-1-e) a, and the range's forward composite
     float s1 = 0.f, r2 = 0.f, f = 0.f, mw = 1.f;
     if (live) {
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
             const size_t o = (size_t)c * cols + k;
             const int i0 = c * kTriChunk;
@@ -421,7 +445,7 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     sh_m[w][lane] = mw;
     __syncthreads();
     float S1 = 0.f, R2 = 0.f;
-    for (int x = 0; x < kChunkWarps; ++x) {
+    for (int x = 0; x < kScanWarps; ++x) {
         S1 += sh_s1[x][lane];
         R2 += sh_r2[x][lane];
     }
@@ -437,11 +461,12 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     float carry = u0;
     for (int x = 0; x < w; ++x) carry = fmaf(sh_m[x][lane], carry, fx(x));
     float call = u0;
-    for (int x = 0; x < kChunkWarps; ++x) call = fmaf(sh_m[x][lane], call, fx(x));
+    for (int x = 0; x < kScanWarps; ++x) call = fmaf(sh_m[x][lane], call, fx(x));
     const float wL = call * iq;                            // w_L (0 for k_x = 0)
 
     // phase 2: causal carries into each chunk of the range
     if (live) {
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
             const size_t o = (size_t)c * cols + k;
             const int n = c == nch - 1 ? nlast : kTriChunk;
@@ -454,6 +479,7 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     // phase 3: the range's anti-causal composite from zero after its last chunk
     float bsum = 0.f;
     if (live) {
+#pragma unroll 4
         for (int c = c1 - 1; c >= c0; --c) {
             const size_t o = (size_t)c * cols + k;
             const int n = c == nch - 1 ? nlast : kTriChunk;
@@ -467,9 +493,10 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     sh_b[w][lane] = bsum;
     __syncthreads();
     float wa = wL;                                         // w just after the range
-    for (int x = kChunkWarps - 1; x > w; --x) wa = fmaf(sh_m[x][lane], wa, sh_b[x][lane]);
+    for (int x = kScanWarps - 1; x > w; --x) wa = fmaf(sh_m[x][lane], wa, sh_b[x][lane]);
     float ksum = 0.f;
     if (live) {
+#pragma unroll 4
         for (int c = c1 - 1; c >= c0; --c) {
             const size_t o = (size_t)c * cols + k;
             const int n = c == nch - 1 ? nlast : kTriChunk;
@@ -490,7 +517,7 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         float tot = 0.f;
-        for (int x = 0; x < kChunkWarps; ++x) tot += sh_k[x];
+        for (int x = 0; x < kScanWarps; ++x) tot += sh_k[x];
         cb.par[0] = mu;
         cb.par[1] = tot / (float)L;
     }
@@ -546,8 +573,8 @@ cudaError_t launch_tri_cols_chunked(float* S, int rows, int cols, int pitch, con
     cudaError_t e = launch_pdl(tri_chunk_sum_kernel, grd, blk, 0, s, (const float*)S, rows, cols, pitch,
                                (const float4*)pp.tri, pp.tsum, nch);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(tri_chunk_scan_kernel, dim3((cols + 31) / 32), blk, 0, s, rows, cols, (const float4*)pp.tri,
-                   pp.tsum, nch);
+    e = launch_pdl(tri_chunk_scan_kernel, dim3((cols + 31) / 32), dim3(32 * kScanWarps), 0, s, rows, cols,
+                   (const float4*)pp.tri, pp.tsum, nch);
     if (e != cudaSuccess) return e;
     return launch_pdl(tri_chunk_apply_kernel, grd, blk, 0, s, S, rows, cols, pitch, (const float4*)pp.tri,
                       (const float*)pp.tsum, nch);

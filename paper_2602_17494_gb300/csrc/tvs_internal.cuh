@@ -332,10 +332,14 @@ template <>
 struct Stor<float> {
     static __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
     static __device__ __forceinline__ float4 ld4c(const float* p) { return *reinterpret_cast<const float4*>(p); }
+    // L2-coherent loads (ld.global.cg) for data other CTAs of the same launch write
+    static __device__ __forceinline__ float4 ld4g(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+    static __device__ __forceinline__ float ld1g(const float* p) { return __ldcg(p); }
     static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ float ld1c(const float* p) { return *p; }
     static __device__ __forceinline__ void st4(float* p, float4 v, uint32_t) { *reinterpret_cast<float4*>(p) = v; }
     static __device__ __forceinline__ void st1(float* p, float v, uint32_t) { *p = v; }
+    static __device__ __forceinline__ void st1r8(float* p, float v, uint32_t) { *p = v; }
 };
 
 // Shared code of the 16-bit formats: D supplies to_f(uint16) and from_f<BITS>(float, random bits).
@@ -351,6 +355,10 @@ struct Stor16 {
         return D::to_f(__ldg(reinterpret_cast<const unsigned short*>(p)));
     }
     static __device__ __forceinline__ float ld1c(const T* p) { return D::to_f(*reinterpret_cast<const uint16_t*>(p)); }
+    static __device__ __forceinline__ float4 ld4g(const T* p) { return unpack(__ldcg(reinterpret_cast<const uint2*>(p))); }
+    static __device__ __forceinline__ float ld1g(const T* p) {
+        return D::to_f(__ldcg(reinterpret_cast<const unsigned short*>(p)));
+    }
     static __device__ __forceinline__ void st4(T* p, float4 v, uint32_t k) {
         uint2 u;
         u.x = (uint32_t)D::template from_f<8>(v.x, k & 0xffU) | ((uint32_t)D::template from_f<8>(v.y, (k >> 8) & 0xffU) << 16);
@@ -359,6 +367,10 @@ struct Stor16 {
     }
     static __device__ __forceinline__ void st1(T* p, float v, uint32_t k) {
         *reinterpret_cast<uint16_t*>(p) = D::template from_f<16>(v, k & 0xffffU);
+    }
+    // one element with 8 random bits (r8 < 256), for stores that share one hash
+    static __device__ __forceinline__ void st1r8(T* p, float v, uint32_t r8) {
+        *reinterpret_cast<uint16_t*>(p) = D::template from_f<8>(v, r8);
     }
 };
 struct Bf16Bits {

@@ -129,3 +129,30 @@ def test_autotuner_picks_a_converging_candidate(B):
     dd = B.make_decomp((160 + tile - 1) // tile, (192 + tile - 1) // tile, s, k)
     r = B.tvs_schwarz(2, d0, tau, 10.0, 1e-3, dd, it)
     assert r.status == 0 and r.report["rel_gap"] <= 1e-4
+
+
+def test_engine_graph_replay_matches_direct_launches(B):
+    # an even check interval: the step-2 chunk of a set of requests is
+    # captured into a CUDA graph the second time the set comes round and then
+    # replayed; results must equal direct launches bit for bit (FP32 and the
+    # fixed-point dual, whose rounding seeds come from a device counter)
+    imgs = [image(n2, n1, 100 + i) for i, (n2, n1) in enumerate(SIZES[:4])]
+    for storage in (0, 3):
+        c = cfg(B, it2=(12, 2), storage=storage)
+        on, ron = run(B, c, imgs)
+        prev = B.tvs_set_graphs(False)
+        try:
+            off, roff = run(B, c, imgs)
+        finally:
+            B.tvs_set_graphs(prev)
+        for i in range(len(imgs)):
+            assert np.array_equal(on[i], off[i]), (storage, i)
+            assert ron[i][1]["iters"] == roff[i][1]["iters"] == 12
+    outs, _ = run(B, cfg(B, it2=(12, 2)), imgs)
+    for i, im in enumerate(imgs):
+        n2, n1 = im.shape
+        d0 = torch.from_numpy(im.astype(np.float32)).cuda()
+        tau = B.tvs_step1(d0, 0.05, B.make_iter(40)).out
+        dd = B.make_decomp(max(1, (n2 + 31) // 32), max(1, (n1 + 31) // 32), 4, 4)
+        ref = B.tvs_schwarz(2, d0, tau, 10.0, 1e-3, dd, B.make_iter(12)).out.cpu().numpy()
+        assert np.abs(outs[i] - ref).max() <= 1e-6

@@ -90,7 +90,7 @@ def test_rows_then_columns_reproduce_the_oracle_pseudo_inverse():
     assert np.abs(phi - ops.inv_lap(s)).max() <= 1e-10 * np.abs(phi).max()
 
 
-def chunked(b: np.ndarray, lam: float, chunk: int = 32, ranges: int = 8) -> np.ndarray:
+def chunked(b: np.ndarray, lam: float, chunk: int = 32, ranges: int = 16) -> np.ndarray:
     """The same solve in the chunked form of the long-column kernels.
 
     Per chunk of `chunk` rows, summaries from a zero carry: h = sum r^(i-i0) b_i,
