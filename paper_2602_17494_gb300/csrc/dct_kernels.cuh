@@ -35,6 +35,7 @@
 #include "prof.h"
 
 #include <mutex>
+#include <utility>
 
 namespace tvs {
 
@@ -304,6 +305,121 @@ __device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, cons
     }
 }
 
+// All passes of an FFT but the last one (the rest of fft_from's sequence).
+template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, bool HALFIN>
+__device__ __forceinline__ void fft_until_last(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+    constexpr int REM = LOGM - LOGNS;
+    constexpr int LR = REM >= LOGUV ? LOGUV : REM;
+    if constexpr (LOGNS + LR < LOGM) {
+        stockham_pass<(1 << LR), INV, UPT, (1 << LOGM), (1 << LOGNS), (1 << LOGUV), kEpiNone, HALFIN && LOGNS == 0>(
+            buf, stride, nfft, tw, FftEpi{});
+        fft_until_last<LOGM, LOGNS + LR, INV, UPT, LOGUV, false>(buf, stride, nfft, tw);
+    }
+}
+
+// Radix-R DFT of v[OFF .. OFF + R) (natural order in and out).
+template <int R, bool INV, int OFF>
+__device__ __forceinline__ void dft_slice(float2 (&v)[16]) {
+    if constexpr (R == 16) {
+        dft16<INV>(v);
+    } else if constexpr (R == 8) {
+        dft8_at<INV, OFF>(v);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[OFF], v[OFF + 1], v[OFF + 2], v[OFF + 3]);
+    } else {
+        dft2<INV>(v[OFF], v[OFF + 1]);
+    }
+}
+
+template <int R, bool INV, int B, int... Bs>
+__device__ __forceinline__ void dft_slices(float2 (&v)[16], std::integer_sequence<int, Bs...>) {
+    (dft_slice<R, INV, Bs * R>(v), ...);
+}
+
+// The forward FFT's last pass, the product with the filter spectrum and the
+// inverse FFT's first pass, in registers.  In a Stockham sequence the last
+// pass of radix RF (NS RF = M) reads and writes, for unit uu, the points
+// uu + U m (m < UV, U = M / UV units): butterfly b takes uu + U b + NS r,
+// i.e. m = b + r (UV / RF).  The first pass of the next FFT (NS = 1, radix
+// UV) reads exactly the same points in the order m.  So the forward outputs
+// never go back to shared memory; the one barrier between the pass's reads
+// and its writes remains (the writes go to uu UV + m').
+template <int RF, int UPT, int M, int UVMAX>
+__device__ __forceinline__ void fft_mid_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
+                                             const float2* __restrict__ mul) {
+    constexpr int UV = M < UVMAX ? M : UVMAX;
+    constexpr int B = UV / RF;          // forward butterflies per unit
+    constexpr int U = M / UV;
+    constexpr int NS = M / RF;          // the forward's last pass; MR = M / RF = NS
+    static_assert(NS == U * B, "unit layout");
+    float2 v[UPT][16];
+    const int tid0 = tid_here();
+#pragma unroll
+    for (int q = 0; q < UPT; ++q) {
+        const int u = tid0 + q * blockDim.x;
+        if (u < nfft * U) {
+            const int g = u / U;
+            const int uu = u - g * U;
+            const float2* x = buf + (size_t)g * stride;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int j = b * U + uu;            // < NS, so the twiddle of input r is w^(j r)
+                float2 wb[4], wa[4];
+                wb[0] = make_float2(1.f, 0.f);
+                wb[1] = __ldg(&tw[j]);
+                wb[2] = c_mul(wb[1], wb[1]);
+                wb[3] = c_mul(wb[2], wb[1]);
+                wa[0] = make_float2(1.f, 0.f);
+                if (RF > 4) {
+                    wa[1] = __ldg(&tw[4 * j]);
+                    wa[2] = c_mul(wa[1], wa[1]);
+                    wa[3] = c_mul(wa[2], wa[1]);
+                }
+#pragma unroll
+                for (int r = 0; r < RF; ++r) {
+                    float2 a = x[pidx(j + r * NS)];
+                    if (r > 0) {
+                        const float2 w = (r >> 2) == 0 ? wb[r & 3]
+                                                       : ((r & 3) == 0 ? wa[r >> 2] : c_mul(wa[r >> 2], wb[r & 3]));
+                        a = c_mul(a, w);
+                    }
+                    v[q][b * RF + r] = a;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int tid1 = tid_here();
+#pragma unroll
+    for (int q = 0; q < UPT; ++q) {
+        const int u = tid1 + q * blockDim.x;
+        if (u < nfft * U) {
+            const int g = u / U;
+            const int uu = u - g * U;
+            float2* x = buf + (size_t)g * stride;
+            dft_slices<RF, false, B>(v[q], std::make_integer_sequence<int, B>{});
+            // forward output r of butterfly b is point m = b + r B; times the filter
+            float2 w[16];
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int r = 0; r < RF; ++r) {
+                    const int m = b + r * B;
+                    w[m] = c_mul(v[q][b * RF + r], __ldg(&mul[uu + U * m]));
+                }
+            dft_slice<UV, true, 0>(w);
+            float2* xd = x + pidx(uu * UV);
+#pragma unroll
+            for (int r = 0; r < UV; ++r) xd[r] = w[r];   // uu UV .. uu UV + UV - 1 lie in one 16-slot run
+        }
+    }
+    __syncthreads();
+}
+
+// Offset (log2) of the last pass in fft_from's sequence for M = 2^LOGM.
+template <int LOGM, int LOGUV>
+constexpr int last_pass_logns() { return (LOGM - 1) / LOGUV * LOGUV; }
+
 // Unit size and units per thread: 8-point units (radix-8 passes) up to 1024
 // points, so short transforms get twice the threads; 16-point units beyond
 // (fewer passes, and so fewer barriers, on the critical path of a line pair);
@@ -314,7 +430,8 @@ struct FftShape {
     static constexpr int LOGUV = LOGM <= 10 ? 3 : 4;
     static constexpr int UV = 1 << LOGUV;
     static constexpr int UNITS = M < UV ? 1 : M / UV;
-    static constexpr int UPT = UNITS > kDctThreads ? 2 : 1;
+    static constexpr int THREADS = fft_threads(M);
+    static constexpr int UPT = UNITS > THREADS ? 2 : 1;
 };
 
 // HALFIN: every line is zero from M/2 on.
@@ -327,7 +444,7 @@ __device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, 
 // Chirp filter spectrum: b[m] = conj(c_m) for lags m in [-(L-2), L-1] stored
 // circularly, FFT'd (natural order) and scaled by 1/M.  One block.
 template <int LOGM>
-__global__ void __launch_bounds__(kDctThreads) plan_bhat_kernel(const __grid_constant__ DctPlan pl) {
+__global__ void __launch_bounds__(fft_threads(1 << LOGM)) plan_bhat_kernel(const __grid_constant__ DctPlan pl) {
     extern __shared__ float2 sm[];
     const int L = pl.L, M = pl.M;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
@@ -362,8 +479,18 @@ __device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const 
     // then the chirp and the peeled sample (fused into its last pass)
     // the chirped input occupies [0, L - 1) with L - 1 <= M / 2, so the first
     // pass reads only the lower half
-    fft_stockham<LOGM, false, kEpiMul, true>(buf, stride, G, pl.tw, ep);
-    fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, pl.tw, ep);
+    using Sh = FftShape<LOGM>;
+    if constexpr (LOGM > Sh::LOGUV) {
+        // at least two passes each: the forward's last pass, the filter and
+        // the inverse's first pass run as one (fft_mid_pass)
+        constexpr int LN = last_pass_logns<LOGM, Sh::LOGUV>();
+        fft_until_last<LOGM, 0, false, Sh::UPT, Sh::LOGUV, true>(buf, stride, G, pl.tw);
+        fft_mid_pass<(1 << (LOGM - LN)), Sh::UPT, (1 << LOGM), Sh::UV>(buf, stride, G, pl.tw, pl.bhat);
+        fft_from<LOGM, Sh::LOGUV, true, Sh::UPT, Sh::LOGUV, kEpiOut, false>(buf, stride, G, pl.tw, ep);
+    } else {
+        fft_stockham<LOGM, false, kEpiMul, true>(buf, stride, G, pl.tw, ep);
+        fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, pl.tw, ep);
+    }
 }
 
 // Rows start on 16-byte boundaries: base and pitch (in floats) allow float4 access.
@@ -463,7 +590,7 @@ __device__ __forceinline__ float row_source(const RowSrcArgs& sa, int r, int c, 
 // Kernels
 // --------------------------------------------------------------------------
 template <RowSource SRC, int LOGM>
-__global__ void __launch_bounds__(kDctThreads)
+__global__ void __launch_bounds__(fft_threads(1 << LOGM))
 dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
                     RowSrcArgs sa, int G, const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
@@ -574,7 +701,7 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
 }
 
 template <int LOGM>
-__global__ void __launch_bounds__(kDctThreads)
+__global__ void __launch_bounds__(fft_threads(1 << LOGM))
 dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl, int G,
                     const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
@@ -662,14 +789,17 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
 // ---------------------------------------------------------------------------
 // Shared-memory limit and carve-out of a DCT kernel.  The plan tables (twiddles,
 // filter spectrum, chirp, Makhoul twiddles: about 28 M bytes) are read by every
-// CTA through L1; the carve-out is sized for at most four CTAs per SM so that
-// the rest of the unified L1/shared storage can keep them resident.
+// CTA through L1; the carve-out is sized for at most four CTAs per SM (fewer
+// when fewer fit at all: one for the 16384-point transforms) so that the rest
+// of the unified L1/shared storage can keep them resident.
 template <class K>
 inline void allow_dct_smem(K kernel, size_t smem_per_cta = 0) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 16 * 1024);
     if (smem_per_cta) {
         const size_t per_sm = 228 * 1024;
-        int pct = (int)((4 * (smem_per_cta + 1024) * 100 + per_sm - 1) / per_sm);
+        size_t ctas = per_sm / (smem_per_cta + 1024);
+        ctas = ctas < 1 ? 1 : (ctas > 4 ? 4 : ctas);
+        int pct = (int)((ctas * (smem_per_cta + 1024) * 100 + per_sm - 1) / per_sm);
         pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
         cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     }
@@ -680,7 +810,7 @@ cudaError_t launch_bhat_lm(const DctPlan& pl, cudaStream_t s) {
     static std::once_flag once;
     std::call_once(once, [] { allow_dct_smem(plan_bhat_kernel<LM>); });
     const size_t smem = (size_t)padded_len(pl.M) * sizeof(float2);
-    plan_bhat_kernel<LM><<<1, kDctThreads, smem, s>>>(pl);
+    plan_bhat_kernel<LM><<<1, fft_threads(1 << LM), smem, s>>>(pl);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,8 @@
 
 namespace tvs {
 
-constexpr int kDctThreads = 512;             // threads per DCT CTA (at most)
+constexpr int kDctThreads = 512;             // threads per DCT CTA up to 8192-point FFTs
+constexpr int kDctThreadsMax = 1024;         // threads per DCT CTA (at most)
 constexpr int kMinLogM = 2, kMaxLogM = 14;   // FFT lengths 4 .. 16384 (transform lengths 3 .. 8193)
 
 // Shared-memory FFT arrays are padded by one slot every 16 entries.
@@ -53,14 +54,12 @@ cudaError_t launch_tri_cols_chunked(float* S, int rows, int cols, int pitch, con
                                     cudaStream_t s);
 
 // Threads for a transform of length M: one per FFT unit (8 points up to 1024,
-// 16 beyond), two units per thread for the 16384-point transforms.
-inline int fft_threads(int M) {
+// 16 beyond); the 16384-point transforms have 1024 units and 1024 threads.
+__host__ __device__ constexpr int fft_threads(int M) {
     const int uv = M <= 1024 ? 8 : 16;
-    int units = M < uv ? 1 : M / uv;
-    if (units > kDctThreads) units = (units + 1) / 2;
-    int t = (units + 31) / 32 * 32;
-    if (t < 64) t = 64;
-    return t > kDctThreads ? kDctThreads : t;
+    const int units = M < uv ? 1 : M / uv;
+    const int t = (units + 31) / 32 * 32;
+    return t < 64 ? 64 : (t > kDctThreadsMax ? kDctThreadsMax : t);
 }
 
 // Runs STMT with the compile-time constant LM equal to the runtime value v.
