@@ -193,13 +193,22 @@ struct FftEpi {
     int L;
 };
 
+// Twiddle bases of a pass of radix R on sub-transforms of NS points:
+// w1 = w^tstep and w4 = w^(4 tstep), tstep = M / (R NS) jm, w = exp(-2 pi i / M).
+struct TwGlobal {                       // read from the plan's table tw[k] = w^k (global memory)
+    const float2* __restrict__ tw;
+    template <int M, int R, int NS>
+    __device__ __forceinline__ float2 w1(int jm) const { return __ldg(&tw[M / (R * NS) * jm]); }
+    template <int M, int R, int NS>
+    __device__ __forceinline__ float2 w4(int jm) const { return __ldg(&tw[4 * (M / (R * NS)) * jm]); }
+};
+
 // One Stockham pass with everything about the shape known at compile time.
 // A thread "unit" holds UV = min(16, M) points: UV / R butterflies of radix R.
 // HALFIN (first pass only): the line is zero from M/2 on, so the upper half
 // of every butterfly's inputs is the constant 0 and is not read.
-template <int R, bool INV, int UPT, int M, int NS, int UVMAX, int EPI, bool HALFIN>
-__device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
-                                              const FftEpi& ep) {
+template <int R, bool INV, int UPT, int M, int NS, int UVMAX, int EPI, bool HALFIN, class TW>
+__device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft, const TW tw, const FftEpi& ep) {
     static_assert(!HALFIN || NS == 1, "only the first pass reads the input line");
     constexpr int UV = M < UVMAX ? M : UVMAX;    // points per unit
     constexpr int B = UV / R;                    // butterflies per unit
@@ -218,16 +227,18 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
             for (int b = 0; b < B; ++b) {
                 const int j = b * U + uu;        // butterfly index in [0, M/R)
                 const int jm = j & (NS - 1);
-                const int tstep = MR / NS * jm;  // jm * M / (NS R): twiddle w^r = tw[tstep * r]
+                // twiddle of input r: w^(tstep r), tstep = jm M / (NS R), as
                 // w^r = (w^4)^(r/4) * w^(r%4) from two table entries (a few ulps each)
                 float2 wb[4], wa[4];
                 wb[0] = make_float2(1.f, 0.f);
-                wb[1] = __ldg(&tw[tstep]);
+                wb[1] = make_float2(1.f, 0.f);
+                if constexpr (NS > 1) wb[1] = tw.template w1<M, R, NS>(jm);
                 wb[2] = c_mul(wb[1], wb[1]);
                 wb[3] = c_mul(wb[2], wb[1]);
                 wa[0] = make_float2(1.f, 0.f);
-                if (R > 4) {
-                    wa[1] = __ldg(&tw[4 * tstep]);
+                wa[1] = make_float2(1.f, 0.f);
+                if constexpr (R > 4 && NS > 1) {
+                    wa[1] = tw.template w4<M, R, NS>(jm);
                     wa[2] = c_mul(wa[1], wa[1]);
                     wa[3] = c_mul(wa[2], wa[1]);
                 }
@@ -292,9 +303,8 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int stride, int nfft,
 
 // The pass sequence for M = 2^LOGM: radix 16 while at least 16 points remain
 // per sub-transform, then the remaining 8, 4 or 2.
-template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, int EPI, bool HALFIN>
-__device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
-                                         const FftEpi& ep) {
+template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, int EPI, bool HALFIN, class TW>
+__device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, const TW tw, const FftEpi& ep) {
     if constexpr (LOGNS < LOGM) {
         constexpr int REM = LOGM - LOGNS;
         constexpr int LR = REM >= LOGUV ? LOGUV : REM;
@@ -306,8 +316,8 @@ __device__ __forceinline__ void fft_from(float2* buf, int stride, int nfft, cons
 }
 
 // All passes of an FFT but the last one (the rest of fft_from's sequence).
-template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, bool HALFIN>
-__device__ __forceinline__ void fft_until_last(float2* buf, int stride, int nfft, const float2* __restrict__ tw) {
+template <int LOGM, int LOGNS, bool INV, int UPT, int LOGUV, bool HALFIN, class TW>
+__device__ __forceinline__ void fft_until_last(float2* buf, int stride, int nfft, const TW tw) {
     constexpr int REM = LOGM - LOGNS;
     constexpr int LR = REM >= LOGUV ? LOGUV : REM;
     if constexpr (LOGNS + LR < LOGM) {
@@ -344,8 +354,8 @@ __device__ __forceinline__ void dft_slices(float2 (&v)[16], std::integer_sequenc
 // UV) reads exactly the same points in the order m.  So the forward outputs
 // never go back to shared memory; the one barrier between the pass's reads
 // and its writes remains (the writes go to uu UV + m').
-template <int RF, int UPT, int M, int UVMAX>
-__device__ __forceinline__ void fft_mid_pass(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
+template <int RF, int UPT, int M, int UVMAX, class TW>
+__device__ __forceinline__ void fft_mid_pass(float2* buf, int stride, int nfft, const TW tw,
                                              const float2* __restrict__ mul) {
     constexpr int UV = M < UVMAX ? M : UVMAX;
     constexpr int B = UV / RF;          // forward butterflies per unit
@@ -366,12 +376,13 @@ __device__ __forceinline__ void fft_mid_pass(float2* buf, int stride, int nfft, 
                 const int j = b * U + uu;            // < NS, so the twiddle of input r is w^(j r)
                 float2 wb[4], wa[4];
                 wb[0] = make_float2(1.f, 0.f);
-                wb[1] = __ldg(&tw[j]);
+                wb[1] = tw.template w1<M, RF, NS>(j);
                 wb[2] = c_mul(wb[1], wb[1]);
                 wb[3] = c_mul(wb[2], wb[1]);
                 wa[0] = make_float2(1.f, 0.f);
-                if (RF > 4) {
-                    wa[1] = __ldg(&tw[4 * j]);
+                wa[1] = make_float2(1.f, 0.f);
+                if constexpr (RF > 4) {
+                    wa[1] = tw.template w4<M, RF, NS>(j);
                     wa[2] = c_mul(wa[1], wa[1]);
                     wa[3] = c_mul(wa[2], wa[1]);
                 }
@@ -416,6 +427,170 @@ __device__ __forceinline__ void fft_mid_pass(float2* buf, int stride, int nfft, 
     __syncthreads();
 }
 
+// ---- in-place decimation-in-frequency FFTs (M >= 2048) ----------------------
+//
+// For M = 2^LOGM >= 2048 the Bluestein core runs in-place radix passes with
+// one 16-point unit per thread (M / 16 threads, one line per CTA):
+//   * F = (LOGM - 1) / 4 full radix-16 passes on blocks of N = M, M/16, ...
+//     points (stride S = N / 16): a unit loads x[blk N + j + S m], m < 16,
+//     takes the 16-point DFT and multiplies output k by w_N^(j k) (Gentleman-
+//     Sande), and stores it back to x[blk N + j + S k];
+//   * a last pass of radix RL = 2^(LOGM - 4F) on blocks of RL contiguous
+//     points, each unit taking 16 / RL of them (the points 16 u .. 16 u + 15).
+// The forward output is in digit-reversed order.  The inverse runs the same
+// passes backwards (conjugate twiddles on the inputs, then the inverse DFT)
+// and ends in natural order, so the filter product needs the filter spectrum
+// in digit-reversed order, which is what the same forward passes produce for
+// the plan.  A unit writes exactly the points it read, so a pass needs one
+// barrier (before the next pass reads) instead of the two of a Stockham pass,
+// and the forward last pass, the filter product and the inverse last pass
+// run in registers.
+template <int LOGM>
+struct Dif {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int F = (LOGM - 1) / 4;          // full radix-16 passes
+    static constexpr int RL = 1 << (LOGM - 4 * F);    // radix of the last pass
+    static constexpr int SMIN = (M / 16) >> (4 * (F - 1));   // stride of the last full pass
+    static_assert(LOGM >= 11 && RL >= 2 && RL <= 16, "in-place passes cover M >= 2048");
+};
+
+// Twiddle bases of the in-place passes in shared memory: the pass of stride
+// S (block N = 16 S) holds w1[j] = w_N^j and w4[j] = w_N^(4 j), j < S, at
+// off(S).  For M = 16384 that is 2 (1024 + 64 + 4) entries (17 KB).
+template <int LOGM>
+struct TwDifShared {
+    static constexpr int off(int S) {
+        int o = 0;
+        for (int st = (1 << LOGM) / 16; st > S; st /= 16) o += 2 * st;
+        return o;
+    }
+    static constexpr int kTotal = off(Dif<LOGM>::SMIN) + 2 * Dif<LOGM>::SMIN;
+    const float2* base;
+    template <int M, int R, int NS>
+    __device__ __forceinline__ float2 w1(int j) const { return base[off(NS) + j]; }
+    template <int M, int R, int NS>
+    __device__ __forceinline__ float2 w4(int j) const { return base[off(NS) + NS + j]; }
+    // all threads of the CTA; the caller synchronizes before the first use
+    __device__ static void fill(float2* dst, const float2* __restrict__ tw) {
+        int o = 0, step = 1;   // step = M / N
+        for (int st = (1 << LOGM) / 16; st >= Dif<LOGM>::SMIN; st /= 16) {
+            for (int i = threadIdx.x; i < st; i += blockDim.x) {
+                dst[o + i] = __ldg(&tw[step * i]);
+                dst[o + st + i] = __ldg(&tw[4 * step * i]);
+            }
+            o += 2 * st;
+            step *= 16;
+        }
+    }
+};
+
+// w^(j k) for k < 16 from w1 = w^j and w4 = w^(4 j): wa[k / 4] * wb[k % 4].
+__device__ __forceinline__ void twiddle_powers(float2 w1, float2 w4, float2 (&wb)[4], float2 (&wa)[4]) {
+    wb[0] = make_float2(1.f, 0.f);
+    wb[1] = w1;
+    wb[2] = c_mul(w1, w1);
+    wb[3] = c_mul(wb[2], w1);
+    wa[0] = make_float2(1.f, 0.f);
+    wa[1] = w4;
+    wa[2] = c_mul(w4, w4);
+    wa[3] = c_mul(wa[2], w4);
+}
+__device__ __forceinline__ float2 twiddle_k(const float2 (&wb)[4], const float2 (&wa)[4], int k) {
+    return (k >> 2) == 0 ? wb[k & 3] : ((k & 3) == 0 ? wa[k >> 2] : c_mul(wa[k >> 2], wb[k & 3]));
+}
+
+// One full radix-16 in-place pass on blocks of N points (S = N / 16).
+// Forward: DFT, then output k times w_N^(j k).  Inverse: input m times
+// w_N^(-j m), then the inverse DFT.  HALFIN: the line is zero from M/2 on
+// (only the first forward pass, N = M).  EPI = kEpiOut (only the last
+// inverse pass, N = M): for k < L, X_k <- chirp_k X_k + peel rot_k, and
+// points k >= L are not stored (nothing reads them).
+template <int M, int N, bool INV, bool HALFIN, int EPI, class TW>
+__device__ __forceinline__ void dif_pass16(float2* x, const TW tw, const FftEpi& ep) {
+    constexpr int S = N / 16;
+    const int u = tid_here();
+    const int j = u & (S - 1);
+    const int base = (u - j) * 16 + j;                 // blk N + j, blk = u / S
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if (HALFIN && m >= 8) v[m] = make_float2(0.f, 0.f);
+        else v[m] = (S % 16 == 0) ? x[pidx(base) + m * (S + S / 16)] : x[pidx(base + S * m)];
+    }
+    if constexpr (S > 1) {
+        float2 wb[4], wa[4];
+        twiddle_powers(tw.template w1<M, 16, S>(j), tw.template w4<M, 16, S>(j), wb, wa);
+        if constexpr (INV) {
+#pragma unroll
+            for (int m = 1; m < 16; ++m) v[m] = c_mul(v[m], c_conj(twiddle_k(wb, wa, m)));
+            dft16<true>(v);
+        } else {
+            dft16<false>(v);
+#pragma unroll
+            for (int k = 1; k < 16; ++k) v[k] = c_mul(v[k], twiddle_k(wb, wa, k));
+        }
+    } else {
+        dft16<INV>(v);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        float2 y = v[k];
+        if constexpr (EPI == kEpiOut) {
+            static_assert(N == M, "the output epilogue belongs to the last inverse pass");
+            // points j + S k with k > 8 lie beyond 9 M / 16 > L - 1: never read
+            if (k > 8) continue;
+            const int p = base + S * k;
+            if (p >= ep.L) continue;
+            y = c_add(c_mul(__ldg(&ep.chirp[p]), y), c_mul(ep.peel[0], __ldg(&ep.rot[p])));
+        }
+        if (S % 16 == 0) x[pidx(base) + k * (S + S / 16)] = y;
+        else x[pidx(base + S * k)] = y;
+    }
+    __syncthreads();
+}
+
+// The last pass (radix RL on contiguous blocks): unit u holds the points
+// 16 u .. 16 u + 15.  MID: forward last pass, times the filter spectrum,
+// inverse last pass, all in registers; the spectrum of point 16 u + i (in
+// digit-reversed order) is stored at mul[i T + u], T = M / 16 units, so that
+// each of the 16 loads of a warp is one contiguous run.  Otherwise the
+// forward last pass alone (the plan's filter spectrum).
+template <int RL, bool MID, int T>
+__device__ __forceinline__ void dif_last(float2* x, const float2* __restrict__ mul) {
+    const int u = tid_here();
+    float2 v[16];
+    float2* xu = x + 17 * u;                            // pidx(16 u + i) = 17 u + i
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = xu[i];
+    dft_slices<RL, false, 16 / RL>(v, std::make_integer_sequence<int, 16 / RL>{});
+    if constexpr (MID) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = c_mul(v[i], __ldg(&mul[i * T + u]));
+        dft_slices<RL, true, 16 / RL>(v, std::make_integer_sequence<int, 16 / RL>{});
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) xu[i] = v[i];
+    __syncthreads();
+}
+
+// Forward full passes from stride S_ (M / 16 first) down to Dif::SMIN.
+template <int LOGM, int S_, bool HALFIN, class TW>
+__device__ __forceinline__ void dif_passes_fwd(float2* x, const TW tw) {
+    if constexpr (S_ >= Dif<LOGM>::SMIN) {
+        dif_pass16<(1 << LOGM), 16 * S_, false, HALFIN, kEpiNone>(x, tw, FftEpi{});
+        if constexpr (S_ / 16 >= 1) dif_passes_fwd<LOGM, S_ / 16, false>(x, tw);
+    }
+}
+// Inverse full passes from stride S_ (Dif::SMIN first) up to M / 16; the
+// last one applies Bluestein's output step.
+template <int LOGM, int S_, class TW>
+__device__ __forceinline__ void dif_passes_inv(float2* x, const TW tw, const FftEpi& ep) {
+    if constexpr (S_ <= (1 << LOGM) / 16) {
+        dif_pass16<(1 << LOGM), 16 * S_, true, false, (S_ == (1 << LOGM) / 16) ? kEpiOut : kEpiNone>(x, tw, ep);
+        dif_passes_inv<LOGM, S_ * 16>(x, tw, ep);
+    }
+}
+
 // Offset (log2) of the last pass in fft_from's sequence for M = 2^LOGM.
 template <int LOGM, int LOGUV>
 constexpr int last_pass_logns() { return (LOGM - 1) / LOGUV * LOGUV; }
@@ -435,8 +610,8 @@ struct FftShape {
 };
 
 // HALFIN: every line is zero from M/2 on.
-template <int LOGM, bool INV, int EPI = kEpiNone, bool HALFIN = false>
-__device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const float2* __restrict__ tw,
+template <int LOGM, bool INV, int EPI = kEpiNone, bool HALFIN = false, class TW>
+__device__ __forceinline__ void fft_stockham(float2* buf, int stride, int nfft, const TW tw,
                                              const FftEpi& ep = FftEpi{}) {
     fft_from<LOGM, 0, INV, FftShape<LOGM>::UPT, FftShape<LOGM>::LOGUV, EPI, HALFIN>(buf, stride, nfft, tw, ep);
 }
@@ -461,10 +636,19 @@ __global__ void __launch_bounds__(fft_threads(1 << LOGM)) plan_bhat_kernel(const
         sm[pidx(m)] = v;
     }
     __syncthreads();
-    fft_stockham<LOGM, false>(sm, padded_len(M), 1, pl.tw);
+    if constexpr (LOGM >= 11) {
+        // the in-place forward passes: the spectrum in their digit-reversed order
+        dif_passes_fwd<LOGM, (1 << LOGM) / 16, false>(sm, TwGlobal{pl.tw});
+        dif_last<Dif<LOGM>::RL, false, (1 << LOGM) / 16>(sm, nullptr);
+    } else {
+        fft_stockham<LOGM, false>(sm, padded_len(M), 1, TwGlobal{pl.tw});
+    }
     const float inv = 1.0f / (float)M;
-    for (int m = threadIdx.x; m < M; m += blockDim.x)
-        pl.bhat[m] = make_float2(sm[pidx(m)].x * inv, sm[pidx(m)].y * inv);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        // in-place layout: point m = 16 u + i of the digit-reversed spectrum at i (M / 16) + u
+        const int d = LOGM >= 11 ? (m & 15) * (M >> 4) + (m >> 4) : m;
+        pl.bhat[d] = make_float2(sm[pidx(m)].x * inv, sm[pidx(m)].y * inv);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -472,24 +656,30 @@ __global__ void __launch_bounds__(fft_threads(1 << LOGM)) plan_bhat_kernel(const
 // buf[g][L-1 .. M) is zero and peel[g] = z_{L-1}.  On return buf[g][k] =
 // Z_k = sum_n z_n exp(-2 pi i n k / L) for k < L.
 // --------------------------------------------------------------------------
-template <int LOGM>
-__device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const DctPlan& pl, const float2* peel) {
+template <int LOGM, class TW>
+__device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const DctPlan& pl, const float2* peel,
+                                          const TW tw) {
     const FftEpi ep{pl.bhat, pl.chirp, pl.rot, peel, pl.L};
     // FFT, times the filter spectrum (fused into the last pass), inverse FFT,
     // then the chirp and the peeled sample (fused into its last pass)
     // the chirped input occupies [0, L - 1) with L - 1 <= M / 2, so the first
     // pass reads only the lower half
     using Sh = FftShape<LOGM>;
-    if constexpr (LOGM > Sh::LOGUV) {
+    if constexpr (LOGM >= 11) {
+        // in-place passes (one line per CTA): forward, filter, inverse
+        dif_passes_fwd<LOGM, (1 << LOGM) / 16, true>(buf, tw);
+        dif_last<Dif<LOGM>::RL, true, (1 << LOGM) / 16>(buf, pl.bhat);
+        dif_passes_inv<LOGM, Dif<LOGM>::SMIN>(buf, tw, ep);
+    } else if constexpr (LOGM > Sh::LOGUV) {
         // at least two passes each: the forward's last pass, the filter and
         // the inverse's first pass run as one (fft_mid_pass)
         constexpr int LN = last_pass_logns<LOGM, Sh::LOGUV>();
-        fft_until_last<LOGM, 0, false, Sh::UPT, Sh::LOGUV, true>(buf, stride, G, pl.tw);
-        fft_mid_pass<(1 << (LOGM - LN)), Sh::UPT, (1 << LOGM), Sh::UV>(buf, stride, G, pl.tw, pl.bhat);
-        fft_from<LOGM, Sh::LOGUV, true, Sh::UPT, Sh::LOGUV, kEpiOut, false>(buf, stride, G, pl.tw, ep);
+        fft_until_last<LOGM, 0, false, Sh::UPT, Sh::LOGUV, true>(buf, stride, G, tw);
+        fft_mid_pass<(1 << (LOGM - LN)), Sh::UPT, (1 << LOGM), Sh::UV>(buf, stride, G, tw, pl.bhat);
+        fft_from<LOGM, Sh::LOGUV, true, Sh::UPT, Sh::LOGUV, kEpiOut, false>(buf, stride, G, tw, ep);
     } else {
-        fft_stockham<LOGM, false, kEpiMul, true>(buf, stride, G, pl.tw, ep);
-        fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, pl.tw, ep);
+        fft_stockham<LOGM, false, kEpiMul, true>(buf, stride, G, tw, ep);
+        fft_stockham<LOGM, true, kEpiOut>(buf, stride, G, tw, ep);
     }
 }
 
@@ -589,8 +779,43 @@ __device__ __forceinline__ float row_source(const RowSrcArgs& sa, int r, int c, 
 // --------------------------------------------------------------------------
 // Kernels
 // --------------------------------------------------------------------------
+// The transforms with in-place passes (FFT lengths of 2048 points or more)
+// copy the twiddle bases of their passes into shared memory (2 to 17 KB,
+// loaded while the lines are staged) instead of reading the plan's global
+// table in every pass.  The shared loads cost fewer L1 wavefronts than the
+// strided global ones, and cannot be moved across the passes' barriers (the
+// read-only global loads were hoisted, held in registers, and spilled).
+// A persistent CTA looping over line pairs would load the bases once, but
+// that loop raised register pressure into spills as well.
+template <int LOGM>
+constexpr bool dct_tw_in_smem() { return LOGM >= 11; }
+template <int LOGM>
+constexpr int dct_tw_smem_entries() {
+    if constexpr (dct_tw_in_smem<LOGM>()) return TwDifShared<LOGM>::kTotal;
+    return 0;
+}
+// Dynamic shared memory of a row-transform CTA: G line buffers, G peeled
+// samples, then the twiddle bases.
+template <int LOGM>
+constexpr size_t dct_rows_smem(int G) {
+    return ((size_t)G * (padded_len(1 << LOGM) + 1) + dct_tw_smem_entries<LOGM>()) * sizeof(float2);
+}
+
+template <int LOGM>
+__device__ __forceinline__ auto dct_twiddles(const DctPlan& pl, float2* smem_tw) {
+    if constexpr (dct_tw_in_smem<LOGM>()) {
+        TwDifShared<LOGM>::fill(smem_tw, pl.tw);   // ordered before the first pass by the barrier after staging
+        return TwDifShared<LOGM>{smem_tw};
+    } else {
+        return TwGlobal{pl.tw};
+    }
+}
+
+// Launch bounds: at most 64 registers per thread (as many CTAs as make 1024
+// threads per SM), so that registers never limit residency below what the
+// shared memory of a line pair allows.
 template <RowSource SRC, int LOGM>
-__global__ void __launch_bounds__(fft_threads(1 << LOGM))
+__global__ void __launch_bounds__(fft_threads(1 << LOGM), 1024 / fft_threads(1 << LOGM))
 dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl,
                     RowSrcArgs sa, int G, const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
@@ -607,6 +832,7 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
         const int base = blockIdx.x * G;
         if (base >= npairs) return;
         const int gc = min(G, npairs - base);
+        const auto tw = dct_twiddles<LOGM>(pl, peel + G);
         if (SRC == RowSource::Plain && vec4_ok(sa.a, sa.pitch) && vec4_ok(out, pitch)) {
             // groups of four samples, one 16-byte load per row
             const int ng = (L + 3) >> 2;
@@ -656,7 +882,7 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
         }
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
-        bluestein<LOGM>(buf, stride, gc, pl, peel);
+        bluestein<LOGM>(buf, stride, gc, pl, peel, tw);
         if (vec4_ok(out, pitch)) {
             // groups of four outputs, one 16-byte store per row
             const int ng = (L + 3) >> 2;
@@ -701,7 +927,7 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
 }
 
 template <int LOGM>
-__global__ void __launch_bounds__(fft_threads(1 << LOGM))
+__global__ void __launch_bounds__(fft_threads(1 << LOGM), 1024 / fft_threads(1 << LOGM))
 dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const __grid_constant__ DctPlan pl, int G,
                     const __grid_constant__ BatchArgs ba) {
     extern __shared__ float2 sm[];
@@ -718,6 +944,7 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
         const int base = blockIdx.x * G;
         if (base >= npairs) return;
         const int gc = min(G, npairs - base);
+        const auto tw = dct_twiddles<LOGM>(pl, peel + G);
         // one thread per pair (k, L - k): the same four loads stage both samples
         const int half = L / 2 + 1;
         for (int b = threadIdx.x; b < gc * half; b += blockDim.x) {
@@ -740,7 +967,7 @@ dct_rows_inv_kernel(float* __restrict__ S, int rows, int cols, int pitch, const 
         }
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
-        bluestein<LOGM>(buf, stride, gc, pl, peel);
+        bluestein<LOGM>(buf, stride, gc, pl, peel, tw);
         if (vec4_ok(S, pitch)) {
             // groups of four outputs, one 16-byte store per row
             const int ng = (L + 3) >> 2;
@@ -818,7 +1045,7 @@ template <int LM>
 cudaError_t launch_rows_fwd_lm(RowSource src, float* S, int rows, int cols, int pitch, const DctPlan& pl,
                                const RowSrcArgs& sa, const BatchArgs& ba, int nbatch, int maxrows, cudaStream_t s) {
     static std::once_flag once;
-    const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    const size_t smem = dct_rows_smem<LM>(1);
     std::call_once(once, [smem] {
         allow_dct_smem(dct_rows_fwd_kernel<RowSource::Plain, LM>, smem);
         allow_dct_smem(dct_rows_fwd_kernel<RowSource::DivField, LM>, smem);
@@ -838,7 +1065,7 @@ template <int LM>
 cudaError_t launch_rows_inv_lm(float* S, int rows, int cols, int pitch, const DctPlan& pl, const BatchArgs& ba,
                                int nbatch, int maxrows, cudaStream_t s) {
     static std::once_flag once;
-    const size_t smem = (size_t)(padded_len(pl.M) + 1) * sizeof(float2);
+    const size_t smem = dct_rows_smem<LM>(1);
     std::call_once(once, [smem] { allow_dct_smem(dct_rows_inv_kernel<LM>, smem); });
     const dim3 grid((maxrows + 1) / 2, nbatch);
     return launch_pdl(dct_rows_inv_kernel<LM>, grid, dim3(fft_threads(pl.M)), smem, s, S, rows, cols, pitch, pl, 1,

@@ -452,10 +452,11 @@ tri_chunk_scan_kernel(int rows, int cols, const float4* __restrict__ tab, float*
     const float mu = zero_mode ? S1 / (float)L : 0.f;   // k_x = 0: the input loses its mean
     // composite of range x with the mean removed (r = 1 there, so it is a plain sum)
     auto fx = [&](int x) {
+        if (!zero_mode) return sh_f[x][lane];
+        // rows of range x: full chunks, the last chunk of the column holding nlast
         const int xc0 = min(nch, x * cpw), xc1 = min(nch, xc0 + cpw);
-        int nr = 0;
-        for (int c = xc0; c < xc1; ++c) nr += c == nch - 1 ? nlast : kTriChunk;
-        return zero_mode ? sh_f[x][lane] - mu * (float)nr : sh_f[x][lane];
+        const int nr = (xc1 - xc0) * kTriChunk - ((xc1 == nch && xc1 > xc0) ? kTriChunk - nlast : 0);
+        return sh_f[x][lane] - mu * (float)nr;
     };
     const float u0 = (S1 + rL * R2) * dnm;                 // c_{-1} (0 for k_x = 0)
     float carry = u0;

@@ -109,7 +109,8 @@ struct DctPlan {
     float2* rot;    // exp(+2 pi i k / L), k < L (the peeled sample's phase)
     float2* post;   // exp(-i pi k / (2L)), k < L (Makhoul's post-twiddle)
     float2* tw;     // exp(-2 pi i j / M), j < M/2
-    float2* bhat;   // FFT_M of the chirp filter, bit-reversed order, times 1/M
+    float2* bhat;   // FFT_M of the chirp filter times 1/M: natural order for M < 2048, else the
+                    // digit-reversed order of the in-place passes, point 16 u + i at i M/16 + u
     float* sig2;    // sigma_{L,k}^2 = (2 sin(pi k / (2L)))^2, k < L: eigenvalues of the 1-D Neumann Laplacian
 };
 
