@@ -117,6 +117,13 @@ __device__ __forceinline__ float fast_norm(float a, float b) {
     const float s2 = fmaf(a, a, fmaf(b, b, 1e-30f));
     return s2 * rsqrtf(s2);
 }
+// Two-lane FP32 arithmetic on pixel pairs (one instruction for two pixels,
+// each lane rounded exactly like the scalar operation).
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // 4 consecutive elements of a box row in shared memory, widened to float
 template <class S>
 __device__ __forceinline__ float4 sm_ld4(const S* p) {
@@ -247,12 +254,17 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
                         pyc[0] = pyc[1] = pyc[2] = pyc[3] = 0.f;
                         cpyr_m = 0.f;
                     }
-                    const float pyp[4] = {pyu.x, pyu.y, pyu.z, pyu.w};
-                    const float fv[4] = {cf.x, cf.y, cf.z, cf.w};
+                    // z = ((p_x - p_x,left) + (p_y - p_y,up)) - f2, two pixels per instruction
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float pl = e == 0 ? left : pxs[e - 1];
-                        zc[e] = ((pxs[e] - pl) + (pyc[e] - pyp[e])) - fv[e];
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const float2 px2 = make_float2(pxs[2 * h2], pxs[2 * h2 + 1]);
+                        const float2 pl2 = make_float2(h2 == 0 ? left : pxs[1], pxs[2 * h2]);
+                        const float2 py2 = make_float2(pyc[2 * h2], pyc[2 * h2 + 1]);
+                        const float2 pu2 = h2 == 0 ? make_float2(pyu.x, pyu.y) : make_float2(pyu.z, pyu.w);
+                        const float2 f2v = h2 == 0 ? make_float2(cf.x, cf.y) : make_float2(cf.z, cf.w);
+                        const float2 z2 = p_sub(p_add(p_sub(px2, pl2), p_sub(py2, pu2)), f2v);
+                        zc[2 * h2] = z2.x;
+                        zc[2 * h2 + 1] = z2.y;
                     }
                     if (lane == 31 && jr < C) {
                         const float pxr_m = (jr <= C - 2) ? cpxr : 0.f;
@@ -268,7 +280,7 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             if (j0 + e < C) {
-                                const float dv = zc[e] + fv[e];   // div p
+                                const float dv = zc[e] + comp(cf, e);   // div p
                                 ks[3].add(dv * dv);
                             }
                     }
@@ -282,27 +294,49 @@ irv1_stream_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_consta
                     if (lane == 31) zright = zpr;
                     float res_x[4], res_y[4];
                     const bool last_row = ir >= R - 1;       // D^+ is zero across the last row
+                    const float2 t2 = make_float2(t, t);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float zn = e == 3 ? zright : zp[e + 1];
-                        float gx = zn - zp[e];
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        // pixels e = 2 h2, 2 h2 + 1 as one pair
+                        const float2 zp2 = make_float2(zp[2 * h2], zp[2 * h2 + 1]);
+                        const float2 zn2 = make_float2(zp[2 * h2 + 1], h2 == 1 ? zright : zp[2]);
+                        float2 gx2 = p_sub(zn2, zp2);
                         if (edge_col) {
-                            if (j0 + e >= C - 1) gx = 0.f;
+                            if (j0 + 2 * h2 >= C - 1) gx2.x = 0.f;
+                            if (j0 + 2 * h2 + 1 >= C - 1) gx2.y = 0.f;
                         }
-                        const float gy = last_row ? 0.f : zc[e] - zp[e];
-                        const float pxv = comp(pprevx, e), pyv = comp(pprevy, e);
-                        const float ng = fast_norm(gx, gy);  // |psi|
+                        const float2 gy2 = last_row ? make_float2(0.f, 0.f)
+                                                    : p_sub(make_float2(zc[2 * h2], zc[2 * h2 + 1]), zp2);
+                        const float2 px2 = h2 == 0 ? make_float2(pprevx.x, pprevx.y) : make_float2(pprevx.z, pprevx.w);
+                        const float2 py2 = h2 == 0 ? make_float2(pprevy.x, pprevy.y) : make_float2(pprevy.z, pprevy.w);
+                        // |psi| = s2 rsqrt(s2), s2 = gx^2 + gy^2 + 1e-30 (as fast_norm)
+                        const float2 s2 = p_fma(gx2, gx2, p_fma(gy2, gy2, make_float2(1e-30f, 1e-30f)));
+                        const float2 ng2 = p_mul(s2, make_float2(rsqrtf(s2.x), rsqrtf(s2.y)));
                         if (WRITE_P) {
                             // p <- (p + t psi) / (1 + t |psi|)
-                            const float inv = __fdividef(1.0f, fmaf(t, ng, 1.0f));
-                            res_x[e] = fmaf(t, gx, pxv) * inv;
-                            res_y[e] = fmaf(t, gy, pyv) * inv;
+                            const float2 den = p_fma(t2, ng2, make_float2(1.f, 1.f));
+                            const float2 inv = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+                            const float2 rx = p_mul(p_fma(t2, gx2, px2), inv);
+                            const float2 ry = p_mul(p_fma(t2, gy2, py2), inv);
+                            res_x[2 * h2] = rx.x;
+                            res_x[2 * h2 + 1] = rx.y;
+                            res_y[2 * h2] = ry.x;
+                            res_y[2 * h2 + 1] = ry.y;
                         }
-                        if (CHECK && j0 + e < C) {
-                            ks[0].add(ng);
-                            ks[1].add(ng - (gx * pxv + gy * pyv));
-                            ks[2].add(zp[e] * zp[e]);
-                            pmax = fmaxf(pmax, fast_norm(pxv, pyv));
+                        if (CHECK) {
+#pragma unroll
+                            for (int l = 0; l < 2; ++l) {
+                                const int e = 2 * h2 + l;
+                                if (j0 + e < C) {
+                                    const float gx = l ? gx2.y : gx2.x, gy = l ? gy2.y : gy2.x;
+                                    const float ng = l ? ng2.y : ng2.x;
+                                    const float pxv = l ? px2.y : px2.x, pyv = l ? py2.y : py2.x;
+                                    ks[0].add(ng);
+                                    ks[1].add(ng - (gx * pxv + gy * pyv));
+                                    ks[2].add(zp[e] * zp[e]);
+                                    pmax = fmaxf(pmax, fast_norm(pxv, pyv));
+                                }
+                            }
                         }
                     }
                     if (WRITE_P) {

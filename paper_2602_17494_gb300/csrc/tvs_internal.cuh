@@ -320,11 +320,23 @@ __device__ __forceinline__ __half f16_sr(float x, uint32_t r) {
     return __float2half_rz(__uint_as_float(b));
 }
 constexpr float kS16Scale = 32767.0f;   // fixed point: value = code / 32767, |code| <= 32767
+// code = floor(x S + u), u = (r + 1/2) / 2^BITS, clamped to |code| <= S (the
+// bounds are integers, so clamping before the round-down conversion is the same)
+__device__ __forceinline__ int16_t s16_from_dithered(float x, float u) {
+    const float y = fmaf(x, kS16Scale, u);
+    return (int16_t)__float2int_rd(fminf(fmaxf(y, -kS16Scale), kS16Scale));
+}
 template <int BITS>
 __device__ __forceinline__ int16_t s16_sr(float x, uint32_t r) {
-    const float u = ((float)r + 0.5f) * (1.0f / (float)(1u << BITS));
-    const float y = fmaf(x, kS16Scale, u);
-    return (int16_t)fminf(fmaxf(floorf(y), -kS16Scale), kS16Scale);
+    return s16_from_dithered(x, ((float)r + 0.5f) * (1.0f / (float)(1u << BITS)));
+}
+// The same with the 8 random bits taken from byte E of k: the byte goes into
+// the mantissa of 1.0f (bits 8..15, one byte permute), f = 1 + b / 2^15, and
+// u = 128 f - 128 + 2^-9 = (b + 1/2) / 256 exactly.
+template <int E>
+__device__ __forceinline__ int16_t s16_sr_byte(float x, uint32_t k) {
+    const float f = __uint_as_float(__byte_perm(k, 0x3F800000u, 0x7604u | (E << 4)));
+    return s16_from_dithered(x, fmaf(f, 128.0f, -128.0f + 1.0f / 512.0f));
 }
 
 template <class S>
@@ -362,8 +374,8 @@ struct Stor16 {
     }
     static __device__ __forceinline__ void st4(T* p, float4 v, uint32_t k) {
         uint2 u;
-        u.x = (uint32_t)D::template from_f<8>(v.x, k & 0xffU) | ((uint32_t)D::template from_f<8>(v.y, (k >> 8) & 0xffU) << 16);
-        u.y = (uint32_t)D::template from_f<8>(v.z, (k >> 16) & 0xffU) | ((uint32_t)D::template from_f<8>(v.w, k >> 24) << 16);
+        u.x = (uint32_t)D::template from_f_byte<0>(v.x, k) | ((uint32_t)D::template from_f_byte<1>(v.y, k) << 16);
+        u.y = (uint32_t)D::template from_f_byte<2>(v.z, k) | ((uint32_t)D::template from_f_byte<3>(v.w, k) << 16);
         *reinterpret_cast<uint2*>(p) = u;
     }
     static __device__ __forceinline__ void st1(T* p, float v, uint32_t k) {
@@ -374,22 +386,33 @@ struct Stor16 {
         *reinterpret_cast<uint16_t*>(p) = D::template from_f<8>(v, r8);
     }
 };
+// from_f_byte<E>(x, k): from_f<8> with the random bits of byte E of k
 struct Bf16Bits {
     static __device__ __forceinline__ float to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
     template <int BITS>
     static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) {
         return __bfloat16_as_ushort(bf16_sr<BITS>(x, r));
     }
+    template <int E>
+    static __device__ __forceinline__ uint16_t from_f_byte(float x, uint32_t k) {
+        return from_f<8>(x, (k >> (8 * E)) & 0xffU);
+    }
 };
 struct F16Bits {
     static __device__ __forceinline__ float to_f(uint16_t b) { return __half2float(__ushort_as_half(b)); }
     template <int BITS>
     static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return __half_as_ushort(f16_sr<BITS>(x, r)); }
+    template <int E>
+    static __device__ __forceinline__ uint16_t from_f_byte(float x, uint32_t k) {
+        return from_f<8>(x, (k >> (8 * E)) & 0xffU);
+    }
 };
 struct S16Bits {
     static __device__ __forceinline__ float to_f(uint16_t b) { return (float)(int16_t)b * (1.0f / kS16Scale); }
     template <int BITS>
     static __device__ __forceinline__ uint16_t from_f(float x, uint32_t r) { return (uint16_t)s16_sr<BITS>(x, r); }
+    template <int E>
+    static __device__ __forceinline__ uint16_t from_f_byte(float x, uint32_t k) { return (uint16_t)s16_sr_byte<E>(x, k); }
 };
 template <>
 struct Stor<__nv_bfloat16> : Stor16<__nv_bfloat16, Bf16Bits> {};
