@@ -47,7 +47,7 @@ CORE, OVERLAP, K_INNER = 64, 4, 16
 SEC_N, SEC_ITERS1, SEC_M, SEC_OVERLAP, SEC_K, SEC_OUTER = 1024, 300, 4, 8, 10, 30
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of each kernel at 8193^2, as the kernels stand (None: no capture)
-TRAFFIC_8192 = {"dct_rows_fwd": 477.85e6, "dct_rows_inv": 477.58e6}
+TRAFFIC_8192 = {"dct_rows_fwd": 493.80e6, "dct_rows_inv": 477.58e6, "tfs_update": 3.2016e9}
 
 
 def parse():
@@ -293,7 +293,9 @@ def algorithmic(name: str, n: int, k: int) -> tuple[float, float]:
     if name == "tri_cols_solve":
         return 8.0 * R * C, 0.0           # one tridiagonal solve per column, read and write once
     if name in ("tfs_update", "tfs_check"):
-        return 44.0 * R * C, 0.0          # read p 16, phi 4, f1 8; write p 16
+        # the global loop's fused step: read p 16, phi 4, f1 8; write p 16 and
+        # the next source div(vecdiv p) 4
+        return 48.0 * R * C, 0.0
     if name == "stencil_other":
         return 20.0 * R * C, 0.0          # div(vecdiv p): read p 16, write 4
     if name == "irv1_update":

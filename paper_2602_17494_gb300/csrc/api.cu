@@ -36,6 +36,7 @@ size_t layout_step1(Carver& cv, int n2, int n1, Step1Layout& L, int storage) {
     L.pb = reinterpret_cast<float*>(cv.take<char>(4 * (size_t)L.plane * storage_bytes(storage)));
     L.f1 = cv.take<float>(2 * (size_t)L.plane);
     L.S = cv.take<float>((size_t)L.plane);
+    L.src = cv.take<float>((size_t)L.plane);
     carve_red(cv, L.red, tfs_blocks(L.R, L.C));
     return cv.used();
 }
@@ -183,13 +184,23 @@ static void key_plan(GraphKey& k, const DctPlan& pl) {
 }
 
 // `count` plain TFS iterations from cur on stream st (cur and nxt alternate; FP32 dual).
+// One update of the global TFS loop.  On entry L.src holds div(vecdiv cur);
+// phi = Delta^dagger of it goes to L.S, then the fused step writes nxt and
+// div(vecdiv nxt) into L.src, so the invariant holds for the next update.
+static cudaError_t tfs_one(const Step1Layout& L, const float* cur, float* nxt, uint32_t seed, float t, bool check,
+                           cudaStream_t st) {
+    RowSrcArgs sa{L.src, 0, L.P};
+    cudaError_t e = poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::Plain, sa, st);
+    if (e != cudaSuccess) return e;
+    return launch_tfs_step_st(cur, nxt, L.st, seed, L.S, L.f1, L.src, L.R, L.C, L.P, L.plane, t, check,
+                              L.red.partial, L.red.err, st);
+}
+
 static cudaError_t tfs_iters(const Step1Layout& L, float* cur, float* nxt, int count, float t, float fd,
                              cudaStream_t st) {
+    (void)fd;
     for (int i = 0; i < count; ++i) {
-        cudaError_t e = tfs_phi(cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, st);
-        if (e != cudaSuccess) return e;
-        e = launch_tfs_update(cur, nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, false, true, nullptr, 0, 0,
-                              L.red.partial, L.red.err, st);
+        const cudaError_t e = tfs_one(L, cur, nxt, 0u, t, false, st);
         if (e != cudaSuccess) return e;
         std::swap(cur, nxt);
     }
@@ -224,6 +235,8 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
     int n = 0;
     bool converged = !check_loop;
     double r[kRedSlots];
+    // the loop keeps L.src = div(vecdiv cur) (tfs_one)
+    TVS_CUDA(launch_div_vecdiv_st(cur, L.st, L.R, L.C, L.P, L.plane, L.src, L.red.err, s));
     while (n < it.max_iter) {
         const bool ck = check_loop && n > 0 && (n % it.check_every) == 0;
         // FP32 dual only: 16-bit stores draw their rounding bits from the update
@@ -231,7 +244,7 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
         const int run = (ck || L.st != TVS_F32) ? 0 : plain_run(check_loop, n, it);
         if (run >= 4) {
             GraphKey key;
-            key.add(1).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.S).ptr(L.f1).add((uint64_t)L.R).add((uint64_t)L.C)
+            key.add(1).add((uint64_t)run).ptr(cur).ptr(nxt).ptr(L.S).ptr(L.src).ptr(L.f1).add((uint64_t)L.R).add((uint64_t)L.C)
                 .add((uint64_t)L.P).add((uint64_t)L.plane).num(t).num(fd).ptr(L.red.partial).ptr(L.red.err);
             key_plan(key, L.pp.row);
             key.add((uint64_t)L.pp.rows).ptr(L.pp.tri);
@@ -239,9 +252,7 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             n += run;
             continue;
         }
-        TVS_CUDA(tfs_phi_st(cur, L.st, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
-        TVS_CUDA(launch_tfs_update_st(cur, nxt, L.st, (uint32_t)n + 1u, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck,
-                                      true, nullptr, TVS_F32, 0, 0, L.red.partial, L.red.err, s));
+        TVS_CUDA(tfs_one(L, cur, nxt, (uint32_t)n + 1u, t, ck, s));
         std::swap(cur, nxt);
         ++n;
         if (ck) {
@@ -255,7 +266,10 @@ static tvs_status run_tfs(const Step1Layout& L, const float* d0, int n2, int n1,
             }
         }
     }
-    TVS_CUDA(tfs_phi_st(cur, L.st, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s));
+    {
+        RowSrcArgs sa{L.src, 0, L.P};
+        TVS_CUDA(poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::Plain, sa, s));
+    }
     TVS_CUDA(launch_tfs_update_st(cur, nullptr, L.st, 0u, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, true, false, tau,
                                   tau_storage, tau_pitch, tau_plane, L.red.partial, L.red.err, s));
     st = read_result(L.red, nb, s, r);

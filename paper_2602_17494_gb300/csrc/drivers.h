@@ -27,6 +27,7 @@ struct Step1Layout {
     int st = TVS_F32;   // tvs_storage of the dual p (pa, pb; 4 planes each)
     PoissonPlans pp;
     float *pa, *pb, *f1, *S;
+    float* src = nullptr;   // div(vecdiv p) of the current dual (the global loop's Poisson source)
     RedBuf red;
 };
 

@@ -22,6 +22,12 @@ cudaError_t launch_tfs_update_st(const void* pin, void* pout, int storage, uint3
                                  const float* f1, int R, int C, int pitch, long plane, float t, float delta,
                                  bool check, bool write_p, void* tau_out, int tau_storage, int tau_pitch,
                                  long tau_plane, double* partial, unsigned* err, cudaStream_t s);
+// The update (as launch_tfs_update_st with write_p, no tau) fused with the
+// source of the next Poisson solve: src <- div(vecdiv pout).  src must not be
+// phi.  Partial sums (check) are the gap terms at pin, as launch_tfs_update_st.
+cudaError_t launch_tfs_step_st(const void* pin, void* pout, int storage, uint32_t seed, const float* phi,
+                               const float* f1, float* src, int R, int C, int pitch, long plane, float t, bool check,
+                               double* partial, unsigned* err, cudaStream_t s);
 int tfs_blocks(int R, int C);
 // Limit of the bounded TMA waits of the kernels in tfs.cu / irv.cu (SM cycles).
 cudaError_t tfs_set_wait_limit(long long cycles);

@@ -46,6 +46,7 @@ inline int pbox_width(int storage) { return kTX + 2 * (16 / (int)storage_bytes(s
 
 // Cached tensor maps of one field: rebuilt only when the base, sizes, plane
 // count or storage change.
+template <int BH>
 struct MapCache {
     const void* base = nullptr;
     int R = 0, C = 0, pitch = 0, planes = 0, st = 0;
@@ -53,20 +54,23 @@ struct MapCache {
     CUtensorMap map;
     bool get(const void* b, int r, int c, int pt, long pl, int np, CUtensorMap* out, int storage = TVS_F32) {
         if (b != base || r != R || c != C || pt != pitch || pl != plane || np != planes || storage != st) {
-            if (!make_tensor_map(&map, b, storage, r, c, pt, pl, np, pbox_width(storage), kBH)) return false;
+            if (!make_tensor_map(&map, b, storage, r, c, pt, pl, np, pbox_width(storage), BH)) return false;
             base = b; R = r; C = c; pitch = pt; plane = pl; planes = np; st = storage;
         }
         *out = map;
         return true;
     }
 };
-thread_local MapCache g_map_p[4], g_map_phi[2], g_map_f1[2];
-thread_local int g_map_next[3];
+// boxes of kTY + 4 rows (the update, div_vecdiv) and kTY + 5 rows (the fused step)
+thread_local MapCache<kBH> g_map_p[4], g_map_phi[2], g_map_f1[2];
+thread_local MapCache<kTY + 5> g_map5_p[4], g_map5_phi[2], g_map5_f1[2];
+thread_local int g_map_next[3], g_map5_next[3];
 
-static MapCache* map_slot(MapCache* c, int n, int* next, const void* base) {
+template <class MC>
+static MC* map_slot(MC* c, int n, int* next, const void* base) {
     for (int i = 0; i < n; ++i)
         if (c[i].base == base) return &c[i];
-    MapCache* r = &c[*next];
+    MC* r = &c[*next];
     *next = (*next + 1) % n;
     return r;
 }
@@ -78,6 +82,12 @@ static bool tile_maps(const void* p, int storage, const float* phi, const float*
         return false;
     if (f1 && !map_slot(g_map_f1, 2, &g_map_next[2], f1)->get(f1, R, C, pitch, plane, 2, mf)) return false;
     return true;
+}
+static bool tile_maps5(const void* p, int storage, const float* phi, const float* f1, int R, int C, int pitch,
+                       long plane, CUtensorMap* mp, CUtensorMap* mphi, CUtensorMap* mf) {
+    return map_slot(g_map5_p, 4, &g_map5_next[0], p)->get(p, R, C, pitch, plane, 4, mp, storage) &&
+           map_slot(g_map5_phi, 2, &g_map5_next[1], phi)->get(phi, R, C, pitch, (long)R * pitch, 1, mphi) &&
+           map_slot(g_map5_f1, 2, &g_map5_next[2], f1)->get(f1, R, C, pitch, plane, 2, mf);
 }
 
 // One thread issues the box loads of a tile; every thread waits (bounded).
@@ -204,8 +214,9 @@ div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pi
         const bool ok = (q & 1) == 0 ? j <= C - 2 : i <= R - 2;
         return ok ? v : 0.f;
     };
-    for (int idx = tid; idx < WH * WW; idx += NT) {
-        const int r = idx / WW, c = idx - r * WW;
+    // a warp takes the tile's 32 columns of one w row (no bank conflicts);
+    // the halo column j0 - 1 is spread over the CTA
+    auto wpoint = [&](int r, int c) {
         const int i = i0 - 1 + r, j = j0 - 1 + c;
         float w1 = 0.f, w2 = 0.f;
         if (i >= 0 && j >= 0 && i < R && j < C) {
@@ -216,7 +227,9 @@ div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pi
         }
         sw[r * WW + c] = w1;
         sw[(WH + r) * WW + c] = w2;
-    }
+    };
+    for (int r = ty; r < WH; r += kBY) wpoint(r, tx + 1);
+    for (int r = tid; r < WH; r += NT) wpoint(r, 0);
     __syncthreads();
 #pragma unroll
     for (int rr = ty; rr < kTY; rr += kBY) {
@@ -325,9 +338,10 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
     };
 
     // z = w - grad phi - f1 on the z region (zero outside the grid); w = vecdiv p
-    // with D^- reading x-parts as zero in the last column and y-parts in the last row
-    for (int idx = tid; idx < kZH * kZW; idx += NT) {
-        const int r = idx / kZW, c = idx - r * kZW;
+    // with D^- reading x-parts as zero in the last column and y-parts in the last row.
+    // A warp takes the tile's 32 columns of one z row (no bank conflicts); the
+    // halo columns j0 - 1 and j0 + 32 are spread over the CTA.
+    auto zpoint = [&](int r, int c) {
         const int i = i0 - 1 + r, j = j0 - 1 + c;
         float z1 = 0.f, z2 = 0.f;
         if (i >= 0 && i < R && j >= 0 && j < C) {
@@ -344,7 +358,9 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
         }
         sz[r * kZW + c] = z1;
         sz[(kZH + r) * kZW + c] = z2;
-    }
+    };
+    for (int r = ty; r < kZH; r += kBY) zpoint(r, tx + 1);
+    for (int e = tid; e < 2 * kZH; e += NT) zpoint(e >> 1, (e & 1) ? kZW - 1 : 0);
     __syncthreads();
 
     // check sums: each thread adds the 8 terms of its 4 points and 2 channels
@@ -410,13 +426,9 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
             }
         }
     }
-    if (CHECK) {
-        FF acc[kRedSlots];
-#pragma unroll
-        for (int k = 0; k < kRedSlots; ++k)
-            acc[k] = k < 4 ? FF{ks[k], 0.0f} : FF{k == 4 ? sqrtf(pmax2) : (k == 5 ? dmax : 0.0f), 0.0f};
-        block_reduce_store_ff<NT>(acc, partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
-    }
+    if (CHECK)
+        block_reduce_store_tfs<NT>(ks, sqrtf(pmax2), dmax,
+                                   partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
 }
 
 int tfs_blocks(int R, int C) { return ((C + kTX - 1) / kTX) * ((R + kTY - 1) / kTY); }
@@ -436,6 +448,236 @@ static cudaError_t tfs_update_go(dim3 grd, dim3 blk, cudaStream_t s, const CUten
     return launch_pdl(tfs_update_kernel<SP, CK, WP, WT, TT>, grd, blk, upd_smem<SP>(), s, mp, mphi, mf,
                       static_cast<SP*>(pout), R, C, pitch, plane, t, delta, static_cast<TT*>(tau_out), tau_pitch,
                       tau_plane, partial, seed, err);
+}
+
+// ---------------------------------------------------------------------------
+// The TFS update fused with the source of the next Poisson solve:
+//   p <- the Chambolle update of p (as tfs_update_kernel, WRITE_P), then
+//   src <- div(vecdiv p) of the new p (as div_vecdiv_kernel).
+// div(vecdiv .) takes backward differences twice, so s on the 32 x 32 tile
+// needs the new p on the tile plus a two-point halo above and to the left;
+// that needs z one row and column further than the update alone, so the
+// boxes cover rows i0 - 3 .. i0 + 33 (37 rows; the columns already span
+// j0 - 4 .. j0 + 35).  The new p of the 34 x 34 region overwrites the old p
+// in its box slot (each point reads only its own old value), rounded exactly
+// as it is stored, so s equals what div_vecdiv_kernel computes from the
+// stored p; the halo points are recomputed here, not read from the CTAs that
+// own them.  Reads 28 and writes 20 algorithmic bytes per point, against 28 +
+// 16 for the update and 16 + 4 for a separate div_vecdiv.  src must not alias
+// phi (other CTAs still read their phi halo while this one writes src).
+// ---------------------------------------------------------------------------
+constexpr int kBH5 = kTY + 5;               // box rows i0 - 3 .. i0 + 33
+constexpr int kBoxR5 = 3;                   // box row of grid row i0
+constexpr int kBoxFloats5 = kBW * kBH5;
+constexpr int kZ5 = kTX + 3;                // z region: rows and columns i0 - 2 .. i0 + 32 (35)
+constexpr int kU5 = kTX + 2;                // new-p region: i0 - 2 .. i0 + 31 (34)
+constexpr int kW5 = kTX + 1;                // w region: i0 - 1 .. i0 + 31 (33)
+
+template <class SP>
+struct PBox5 {
+    static constexpr int C0 = PBox<SP>::C0;
+    static constexpr int W = PBox<SP>::W;
+    static constexpr int BYTES = 4 * W * kBH5 * (int)sizeof(SP);
+    static constexpr int BYTES_AL = (BYTES + 127) / 128 * 128;
+};
+// The tensor copies land on 128-byte boundaries: the phi box is padded to one
+// (1480 floats are not a multiple of 32), so the f1 box behind it is aligned.
+constexpr int kPhi5Al = (kBoxFloats5 + 31) / 32 * 32;
+static_assert((kPhi5Al * 4) % 128 == 0, "f1 box of the fused step on a 128-byte boundary");
+static_assert(((kPhi5Al + 2 * kBoxFloats5 + 2 * kZ5 * kZ5) * 4) % 8 == 0, "mbarrier of the fused step 8-byte aligned");
+template <class SP>
+constexpr size_t step_smem() {
+    return (size_t)PBox5<SP>::BYTES_AL + (size_t)(kPhi5Al + 2 * kBoxFloats5) * 4 + (size_t)2 * kZ5 * kZ5 * 4 + 256;
+}
+static_assert(2 * kW5 * kW5 <= kPhi5Al + 2 * kBoxFloats5, "w fits over the phi and f1 boxes");
+
+template <class SP, bool CHECK>
+__global__ void __launch_bounds__(kTX * kBY)
+tfs_step_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap phimap,
+                const __grid_constant__ CUtensorMap fmap, SP* __restrict__ pout, float* __restrict__ src, int R,
+                int C, int pitch, long plane, float t, double* __restrict__ partial, uint32_t seed,
+                unsigned* __restrict__ err) {
+    using PB = PBox5<SP>;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* base = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    SP* sp = reinterpret_cast<SP*>(base);                             // [4][BH5][PB::W]
+    float* sphi = reinterpret_cast<float*>(base + PB::BYTES_AL);      // [BH5][BW], padded to 128 bytes
+    float* sf = sphi + kPhi5Al;                    // [2][BH5][BW]
+    float* sz = sf + 2 * kBoxFloats5;              // [2][Z5][Z5]
+    float* sw = sphi;                              // [2][W5][W5], over phi and f1 once z is done
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sz + 2 * kZ5 * kZ5);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    constexpr int NT = kTX * kBY;
+    const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
+    if (!tile_load_early(bar, PB::BYTES + 3 * kBoxFloats5 * 4, base, &pmap, j0 - PB::C0, sphi, &phimap, sf, &fmap,
+                         j0 - kBoxC, i0 - kBoxR5, err))
+        return;
+    auto B = [&](int i, int j) -> int { return (i - i0 + kBoxR5) * kBW + (j - j0 + kBoxC); };
+    auto PO = [&](int q, int i, int j) -> int { return (q * kBH5 + (i - i0 + kBoxR5)) * PB::W + (j - j0 + PB::C0); };
+    auto PV = [&](int q, int i, int j) -> float { return Stor<SP>::ld1c(sp + PO(q, i, j)); };
+
+    // Every phase works on a region a few columns wider than the tile: a warp
+    // takes the tile's 32 columns of one region row (contiguous, no bank
+    // conflicts), and a second loop spreads the few halo columns over the CTA.
+    // z = vecdiv p - grad phi - f1 on rows/columns i0 - 2 .. i0 + 32 (as tfs_update_kernel)
+    auto zpoint = [&](int r, int c) {
+        const int i = i0 - 2 + r, j = j0 - 2 + c;
+        float z1 = 0.f, z2 = 0.f;
+        if (i >= 0 && i < R && j >= 0 && j < C) {
+            const int o = B(i, j);
+            const float xm = (j <= C - 2) ? 1.f : 0.f;
+            const float ym = (i <= R - 2) ? 1.f : 0.f;
+            const float w1 = (PV(0, i, j) * xm - PV(0, i, j - 1)) + (PV(1, i, j) * ym - PV(1, i - 1, j));
+            const float w2 = (PV(2, i, j) * xm - PV(2, i, j - 1)) + (PV(3, i, j) * ym - PV(3, i - 1, j));
+            const float pc = sphi[o];
+            const float gx = (j < C - 1) ? sphi[o + 1] - pc : 0.f;
+            const float gy = (i < R - 1) ? sphi[o + kBW] - pc : 0.f;
+            z1 = w1 - gx - sf[o];
+            z2 = w2 - gy - sf[kBoxFloats5 + o];
+        }
+        sz[r * kZ5 + c] = z1;
+        sz[(kZ5 + r) * kZ5 + c] = z2;
+    };
+    for (int r = ty; r < kZ5; r += kBY) zpoint(r, tx + 2);
+    for (int e = tid; e < 3 * kZ5; e += NT) {           // region columns 0, 1 and 34
+        const int r = e / 3, k = e - 3 * r;
+        zpoint(r, k < 2 ? k : kZ5 - 1);
+    }
+    __syncthreads();
+
+    // the update on rows/columns i0 - 2 .. i0 + 31, in place in the p box; the
+    // tile itself also goes to pout; CHECK: the gap terms at the input p (tile only)
+    float ks[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float pmax2 = 0.0f, dmax = 0.0f;
+    auto upoint = [&](int r, int c) {                   // z region position of (i, j) is (r, c)
+        const int i = i0 - 2 + r, j = j0 - 2 + c;
+        const bool in_grid = i >= 0 && j >= 0 && i < R && j < C;
+        const bool tile = i >= i0 && j >= j0 && in_grid;
+        float pv[4] = {0.f, 0.f, 0.f, 0.f};
+        float vnew[4] = {0.f, 0.f, 0.f, 0.f};
+        float zc[2] = {0.f, 0.f}, gx[2] = {0.f, 0.f}, gy[2] = {0.f, 0.f};
+        if (in_grid) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float* zk = sz + k * kZ5 * kZ5;
+                zc[k] = zk[r * kZ5 + c];
+                gx[k] = (j < C - 1) ? zk[r * kZ5 + c + 1] - zc[k] : 0.f;
+                gy[k] = (i < R - 1) ? zk[(r + 1) * kZ5 + c] - zc[k] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pv[q] = PV(q, i, j);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float s2 = fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1e-30f));
+                const float inv = rcp_ftz(fmaf(t, s2 * rsqrt_ftz(s2), 1.0f));
+                vnew[2 * k] = fmaf(t, gx[k], pv[2 * k]) * inv;
+                vnew[2 * k + 1] = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
+            }
+        }
+        const size_t o = (size_t)i * pitch + j;
+        const uint32_t h = (sizeof(SP) == 4 || !in_grid) ? 0u : rkey(seed, o, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            SP* slot = sp + PO(q, i, j);
+            // the same rounding as tfs_update_kernel's store of this point (zero outside the grid)
+            Stor<SP>::st1r8(slot, vnew[q], (h >> (8 * q)) & 0xffU);
+            if (tile) pout[(size_t)q * plane + o] = *slot;
+        }
+        if (CHECK && tile) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
+                const float s2 = fmaf(a, a, fmaf(b, b, 1e-30f));
+                const float ng = s2 * rsqrt_ftz(s2);
+                ks[0] += ng;
+                ks[1] += ng - fmaf(a, px, b * py);
+                ks[2] = fmaf(zc[k], zc[k], ks[2]);
+                const float zf = zc[k] + sf[k * kBoxFloats5 + B(i, j)];
+                ks[3] = fmaf(zf, zf, ks[3]);
+                pmax2 = fmaxf(pmax2, fmaf(px, px, py * py));
+            }
+            const float z1c = (j <= C - 2) ? zc[0] : 0.f;
+            const float z1l = (j >= 1) ? sz[r * kZ5 + c - 1] : 0.f;
+            const float z2c = (i <= R - 2) ? zc[1] : 0.f;
+            const float z2u = (i >= 1) ? sz[(kZ5 + r - 1) * kZ5 + c] : 0.f;
+            dmax = fmaxf(dmax, fabsf((z1c - z1l) + (z2c - z2u)));
+        }
+    };
+    for (int r = ty; r < kU5; r += kBY) upoint(r, tx + 2);
+    for (int e = tid; e < 2 * kU5; e += NT) upoint(e >> 1, e & 1);   // region columns 0 and 1
+    __syncthreads();
+
+    // w = vecdiv p_new on rows/columns i0 - 1 .. i0 + 31, then s = div w on the
+    // tile (as div_vecdiv_kernel, with the D^- rule)
+    auto P = [&](int q, int i, int j) -> float {
+        const float v = PV(q, i, j);
+        const bool ok = (q & 1) == 0 ? j <= C - 2 : i <= R - 2;
+        return ok ? v : 0.f;
+    };
+    auto wpoint = [&](int r, int c) {
+        const int i = i0 - 1 + r, j = j0 - 1 + c;
+        float w1 = 0.f, w2 = 0.f;
+        if (i >= 0 && j >= 0 && i < R && j < C) {
+            w1 = (P(0, i, j) - P(0, i, j - 1)) + (P(1, i, j) - P(1, i - 1, j));
+            w2 = (P(2, i, j) - P(2, i, j - 1)) + (P(3, i, j) - P(3, i - 1, j));
+            if (j > C - 2) w1 = 0.f;
+            if (i > R - 2) w2 = 0.f;
+        }
+        sw[r * kW5 + c] = w1;
+        sw[(kW5 + r) * kW5 + c] = w2;
+    };
+    for (int r = ty; r < kW5; r += kBY) wpoint(r, tx + 1);
+    for (int r = tid; r < kW5; r += NT) wpoint(r, 0);            // region column 0
+    __syncthreads();
+#pragma unroll
+    for (int rr = ty; rr < kTY; rr += kBY) {
+        const int i = i0 + rr, j = j0 + tx;
+        if (i < R && j < C) {
+            const int r = rr + 1, c = tx + 1;
+            src[(size_t)i * pitch + j] =
+                (sw[r * kW5 + c] - sw[r * kW5 + c - 1]) + (sw[(kW5 + r) * kW5 + c] - sw[(kW5 + r - 1) * kW5 + c]);
+        }
+    }
+    if (CHECK)
+        block_reduce_store_tfs<NT>(ks, sqrtf(pmax2), dmax,
+                                   partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
+}
+
+template <class SP, bool CK>
+static cudaError_t tfs_step_go(dim3 grd, dim3 blk, cudaStream_t s, const CUtensorMap& mp, const CUtensorMap& mphi,
+                               const CUtensorMap& mf, void* pout, float* src, int R, int C, int pitch, long plane,
+                               float t, double* partial, uint32_t seed, unsigned* err) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(tfs_step_kernel<SP, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_smem<SP>());
+    });
+    return launch_pdl(tfs_step_kernel<SP, CK>, grd, blk, step_smem<SP>(), s, mp, mphi, mf, static_cast<SP*>(pout),
+                      src, R, C, pitch, plane, t, partial, seed, err);
+}
+
+cudaError_t launch_tfs_step_st(const void* pin, void* pout, int storage, uint32_t seed, const float* phi,
+                               const float* f1, float* src, int R, int C, int pitch, long plane, float t, bool check,
+                               double* partial, unsigned* err, cudaStream_t s) {
+    if (!pin || !pout || !phi || !f1 || !src || src == phi) return cudaErrorInvalidValue;
+    CUtensorMap mp, mphi, mf;
+    if (!tile_maps5(pin, storage, phi, f1, R, C, pitch, plane, &mp, &mphi, &mf)) return cudaErrorInvalidValue;
+    dim3 blk(kTX, kBY), grd((C + kTX - 1) / kTX, (R + kTY - 1) / kTY);
+    ProfScope ps(check ? kProfTfsCheck : kProfTfsUpdate, s);
+    if (storage == TVS_F32) {
+        if (check) return tfs_step_go<float, true>(grd, blk, s, mp, mphi, mf, pout, src, R, C, pitch, plane, t,
+                                                   partial, seed, err);
+        return tfs_step_go<float, false>(grd, blk, s, mp, mphi, mf, pout, src, R, C, pitch, plane, t, partial, seed,
+                                         err);
+    }
+    TVS_STORAGE_SWITCH(storage, {
+        if (check) return tfs_step_go<S, true>(grd, blk, s, mp, mphi, mf, pout, src, R, C, pitch, plane, t, partial,
+                                               seed, err);
+        return tfs_step_go<S, false>(grd, blk, s, mp, mphi, mf, pout, src, R, C, pitch, plane, t, partial, seed,
+                                     err);
+    })
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tfs_update_st(const void* pin, void* pout, int storage, uint32_t seed, const float* phi,

@@ -266,6 +266,53 @@ __device__ __forceinline__ void block_reduce_store_ff(FF v[kRedSlots], double* o
     }
 }
 
+// The TFS check layout of block_reduce_store_ff with only its live slots
+// reduced: the four sums (slots 0-3) as FP32 pairs, the two maxima (slots 4,
+// 5) as plain FP32, slots 6 and 7 written as zero.  Same results as
+// block_reduce_store_ff on that layout, at about half the shuffles and adds
+// (which matter: a 32 x 32 tile's reduction costs a third of its update).
+template <int NT>
+__device__ __forceinline__ void block_reduce_store_tfs(const float (&sum)[4], float mx4, float mx5, double* out,
+                                                       int tid) {
+    __shared__ FF red_s[NT / 32][4];
+    __shared__ float red_m[NT / 32][2];
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        FF x{sum[k], 0.0f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const FF y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+            x = ff_add(x, y);
+        }
+        if (lane == 0) red_s[wid][k] = x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx4 = fmaxf(mx4, __shfl_xor_sync(0xffffffffu, mx4, o));
+        mx5 = fmaxf(mx5, __shfl_xor_sync(0xffffffffu, mx5, o));
+    }
+    if (lane == 0) {
+        red_m[wid][0] = mx4;
+        red_m[wid][1] = mx5;
+    }
+    __syncthreads();
+    if (tid < kRedSlots) {
+        const int k = tid;
+        double v = 0.0;
+        if (k < 4) {
+            FF x = red_s[0][k];
+            for (int w = 1; w < NT / 32; ++w) x = ff_add(x, red_s[w][k]);
+            v = (double)x.hi + (double)x.lo;
+        } else if (k < 6) {
+            float m = red_m[0][k - 4];
+            for (int w = 1; w < NT / 32; ++w) m = fmaxf(m, red_m[w][k - 4]);
+            v = (double)m;
+        }
+        out[k] = v;
+    }
+}
+
 // --------------------------------------------------------------------------
 // Error bookkeeping
 // --------------------------------------------------------------------------
