@@ -505,8 +505,26 @@ __device__ __forceinline__ float2 twiddle_k(const float2 (&wb)[4], const float2 
 // (only the first forward pass, N = M).  EPI = kEpiOut (only the last
 // inverse pass, N = M): for k < L, X_k <- chirp_k X_k + peel rot_k, and
 // points k >= L are not stored (nothing reads them).
+// The input of the first forward pass read straight from a pair of rows:
+// point n of the line is Makhoul's reordering of the two rows (even columns
+// 2n for n < (L+1)/2, odd columns 2(L-1-n)+1 after), times chirp_n, for
+// n < L - 1; zero from L - 1 on (the peeled sample z_{L-1}, column 1, is
+// staged separately).  a1 == nullptr: the second row is zero.
+struct RowPairIn {
+    const float* a0;
+    const float* a1;
+    const float2* chirp;
+    int L;
+    __device__ __forceinline__ float2 at(int n) const {
+        if (n >= L - 1) return make_float2(0.f, 0.f);
+        const int c = n < (L + 1) / 2 ? 2 * n : 2 * (L - 1 - n) + 1;
+        return c_mul(make_float2(__ldg(a0 + c), a1 ? __ldg(a1 + c) : 0.f), __ldg(&chirp[n]));
+    }
+};
+
 template <int M, int N, bool INV, bool HALFIN, int EPI, class TW>
-__device__ __forceinline__ void dif_pass16(float2* x, const TW tw, const FftEpi& ep) {
+__device__ __forceinline__ void dif_pass16(float2* x, const TW tw, const FftEpi& ep,
+                                           const RowPairIn* rows = nullptr) {
     constexpr int S = N / 16;
     const int u = tid_here();
     const int j = u & (S - 1);
@@ -515,6 +533,7 @@ __device__ __forceinline__ void dif_pass16(float2* x, const TW tw, const FftEpi&
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         if (HALFIN && m >= 8) v[m] = make_float2(0.f, 0.f);
+        else if (rows) v[m] = rows->at(base + S * m);   // first forward pass only (N = M, base = u)
         else v[m] = (S % 16 == 0) ? x[pidx(base) + m * (S + S / 16)] : x[pidx(base + S * m)];
     }
     if constexpr (S > 1) {
@@ -683,6 +702,22 @@ __device__ __forceinline__ void bluestein(float2* buf, int stride, int G, const 
     }
 }
 
+// Bluestein core of the in-place path with the first forward pass reading a
+// pair of rows directly (no staging through shared memory); the first pass
+// takes its twiddles from the plan's global table, the later passes from the
+// CTA's shared copy (written before, ordered by the first pass's barrier).
+template <int LOGM, class TW>
+__device__ __forceinline__ void bluestein_rows(float2* buf, const DctPlan& pl, float2* peel, const TW tw,
+                                               const RowPairIn& rows) {
+    constexpr int M = 1 << LOGM;
+    if (threadIdx.x == 0) *peel = make_float2(__ldg(rows.a0 + 1), rows.a1 ? __ldg(rows.a1 + 1) : 0.f);
+    const FftEpi ep{pl.bhat, pl.chirp, pl.rot, peel, pl.L};
+    dif_pass16<M, M, false, true, kEpiNone>(buf, TwGlobal{pl.tw}, FftEpi{}, &rows);
+    dif_passes_fwd<LOGM, M / 256, false>(buf, tw);
+    dif_last<Dif<LOGM>::RL, true, M / 16>(buf, pl.bhat);
+    dif_passes_inv<LOGM, Dif<LOGM>::SMIN>(buf, tw, ep);
+}
+
 // Rows start on 16-byte boundaries: base and pitch (in floats) allow float4 access.
 __device__ __forceinline__ bool vec4_ok(const float* base, int pitch) {
     return ((reinterpret_cast<uintptr_t>(base) & 15) == 0) && ((pitch & 3) == 0);
@@ -833,6 +868,13 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
         if (base >= npairs) return;
         const int gc = min(G, npairs - base);
         const auto tw = dct_twiddles<LOGM>(pl, peel + G);
+        if constexpr (LOGM >= 11 && SRC == RowSource::Plain) {
+            // in-place path: the first pass reads the rows itself (one line pair per CTA)
+            const int r0 = rr.x + 2 * base, r1 = r0 + 1;
+            const RowPairIn rows{sa.a + row_off(ba, rr, r0, sa.pitch),
+                                 r1 < rr.y ? sa.a + row_off(ba, rr, r1, sa.pitch) : nullptr, pl.chirp, L};
+            bluestein_rows<LOGM>(buf, pl, peel, tw, rows);
+        } else {
         if (SRC == RowSource::Plain && vec4_ok(sa.a, sa.pitch) && vec4_ok(out, pitch)) {
             // groups of four samples, one 16-byte load per row
             const int ng = (L + 3) >> 2;
@@ -883,6 +925,7 @@ dct_rows_fwd_kernel(float* __restrict__ out, int rows, int cols, int pitch, cons
         zero_tail(buf, stride, gc, L, M);
         __syncthreads();
         bluestein<LOGM>(buf, stride, gc, pl, peel, tw);
+        }
         if (vec4_ok(out, pitch)) {
             // groups of four outputs, one 16-byte store per row
             const int ng = (L + 3) >> 2;
