@@ -14,6 +14,7 @@
 #include "tma.cuh"
 
 #include <mutex>
+#include <type_traits>
 
 namespace tvs {
 
@@ -520,125 +521,138 @@ tfs_step_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant_
     // Every phase works on a region a few columns wider than the tile: a warp
     // takes the tile's 32 columns of one region row (contiguous, no bank
     // conflicts), and a second loop spreads the few halo columns over the CTA.
-    // z = vecdiv p - grad phi - f1 on rows/columns i0 - 2 .. i0 + 32 (as tfs_update_kernel)
-    auto zpoint = [&](int r, int c) {
-        const int i = i0 - 2 + r, j = j0 - 2 + c;
-        float z1 = 0.f, z2 = 0.f;
-        if (i >= 0 && i < R && j >= 0 && j < C) {
-            const int o = B(i, j);
-            const float xm = (j <= C - 2) ? 1.f : 0.f;
-            const float ym = (i <= R - 2) ? 1.f : 0.f;
-            const float w1 = (PV(0, i, j) * xm - PV(0, i, j - 1)) + (PV(1, i, j) * ym - PV(1, i - 1, j));
-            const float w2 = (PV(2, i, j) * xm - PV(2, i, j - 1)) + (PV(3, i, j) * ym - PV(3, i - 1, j));
-            const float pc = sphi[o];
-            const float gx = (j < C - 1) ? sphi[o + 1] - pc : 0.f;
-            const float gy = (i < R - 1) ? sphi[o + kBW] - pc : 0.f;
-            z1 = w1 - gx - sf[o];
-            z2 = w2 - gy - sf[kBoxFloats5 + o];
-        }
-        sz[r * kZ5 + c] = z1;
-        sz[(kZ5 + r) * kZ5 + c] = z2;
-    };
-    for (int r = ty; r < kZ5; r += kBY) zpoint(r, tx + 2);
-    for (int e = tid; e < 3 * kZ5; e += NT) {           // region columns 0, 1 and 34
-        const int r = e / 3, k = e - 3 * r;
-        zpoint(r, k < 2 ? k : kZ5 - 1);
-    }
-    __syncthreads();
-
-    // the update on rows/columns i0 - 2 .. i0 + 31, in place in the p box; the
-    // tile itself also goes to pout; CHECK: the gap terms at the input p (tile only)
+    // Tiles whose regions lie inside the grid away from its last row and column
+    // (almost all) run the phases without bounds checks and boundary masks
+    // (EDGE false; the masks would all pass there, so the results are the same).
     float ks[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     float pmax2 = 0.0f, dmax = 0.0f;
-    auto upoint = [&](int r, int c) {                   // z region position of (i, j) is (r, c)
-        const int i = i0 - 2 + r, j = j0 - 2 + c;
-        const bool in_grid = i >= 0 && j >= 0 && i < R && j < C;
-        const bool tile = i >= i0 && j >= j0 && in_grid;
-        float pv[4] = {0.f, 0.f, 0.f, 0.f};
-        float vnew[4] = {0.f, 0.f, 0.f, 0.f};
-        float zc[2] = {0.f, 0.f}, gx[2] = {0.f, 0.f}, gy[2] = {0.f, 0.f};
-        if (in_grid) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float* zk = sz + k * kZ5 * kZ5;
-                zc[k] = zk[r * kZ5 + c];
-                gx[k] = (j < C - 1) ? zk[r * kZ5 + c + 1] - zc[k] : 0.f;
-                gy[k] = (i < R - 1) ? zk[(r + 1) * kZ5 + c] - zc[k] : 0.f;
+    const bool interior = i0 >= kTY && j0 >= kTX && i0 + kTY + 2 <= R && j0 + kTX + 2 <= C;
+    auto phases = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        // z = vecdiv p - grad phi - f1 on rows/columns i0 - 2 .. i0 + 32 (as tfs_update_kernel)
+        auto zpoint = [&](int r, int c) {
+            const int i = i0 - 2 + r, j = j0 - 2 + c;
+            float z1 = 0.f, z2 = 0.f;
+            if (!EDGE || (i >= 0 && i < R && j >= 0 && j < C)) {
+                const int o = B(i, j);
+                const float xm = (!EDGE || j <= C - 2) ? 1.f : 0.f;
+                const float ym = (!EDGE || i <= R - 2) ? 1.f : 0.f;
+                const float w1 = (PV(0, i, j) * xm - PV(0, i, j - 1)) + (PV(1, i, j) * ym - PV(1, i - 1, j));
+                const float w2 = (PV(2, i, j) * xm - PV(2, i, j - 1)) + (PV(3, i, j) * ym - PV(3, i - 1, j));
+                const float pc = sphi[o];
+                const float gx = (!EDGE || j < C - 1) ? sphi[o + 1] - pc : 0.f;
+                const float gy = (!EDGE || i < R - 1) ? sphi[o + kBW] - pc : 0.f;
+                z1 = w1 - gx - sf[o];
+                z2 = w2 - gy - sf[kBoxFloats5 + o];
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pv[q] = PV(q, i, j);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float s2 = fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1e-30f));
-                const float inv = rcp_ftz(fmaf(t, s2 * rsqrt_ftz(s2), 1.0f));
-                vnew[2 * k] = fmaf(t, gx[k], pv[2 * k]) * inv;
-                vnew[2 * k + 1] = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
-            }
+            sz[r * kZ5 + c] = z1;
+            sz[(kZ5 + r) * kZ5 + c] = z2;
+        };
+        for (int r = ty; r < kZ5; r += kBY) zpoint(r, tx + 2);
+        for (int e = tid; e < 3 * kZ5; e += NT) {           // region columns 0, 1 and 34
+            const int r = e / 3, k = e - 3 * r;
+            zpoint(r, k < 2 ? k : kZ5 - 1);
         }
-        const size_t o = (size_t)i * pitch + j;
-        const uint32_t h = (sizeof(SP) == 4 || !in_grid) ? 0u : rkey(seed, o, 0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            SP* slot = sp + PO(q, i, j);
-            // the same rounding as tfs_update_kernel's store of this point (zero outside the grid)
-            Stor<SP>::st1r8(slot, vnew[q], (h >> (8 * q)) & 0xffU);
-            if (tile) pout[(size_t)q * plane + o] = *slot;
-        }
-        if (CHECK && tile) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
-                const float s2 = fmaf(a, a, fmaf(b, b, 1e-30f));
-                const float ng = s2 * rsqrt_ftz(s2);
-                ks[0] += ng;
-                ks[1] += ng - fmaf(a, px, b * py);
-                ks[2] = fmaf(zc[k], zc[k], ks[2]);
-                const float zf = zc[k] + sf[k * kBoxFloats5 + B(i, j)];
-                ks[3] = fmaf(zf, zf, ks[3]);
-                pmax2 = fmaxf(pmax2, fmaf(px, px, py * py));
-            }
-            const float z1c = (j <= C - 2) ? zc[0] : 0.f;
-            const float z1l = (j >= 1) ? sz[r * kZ5 + c - 1] : 0.f;
-            const float z2c = (i <= R - 2) ? zc[1] : 0.f;
-            const float z2u = (i >= 1) ? sz[(kZ5 + r - 1) * kZ5 + c] : 0.f;
-            dmax = fmaxf(dmax, fabsf((z1c - z1l) + (z2c - z2u)));
-        }
-    };
-    for (int r = ty; r < kU5; r += kBY) upoint(r, tx + 2);
-    for (int e = tid; e < 2 * kU5; e += NT) upoint(e >> 1, e & 1);   // region columns 0 and 1
-    __syncthreads();
+        __syncthreads();
 
-    // w = vecdiv p_new on rows/columns i0 - 1 .. i0 + 31, then s = div w on the
-    // tile (as div_vecdiv_kernel, with the D^- rule)
-    auto P = [&](int q, int i, int j) -> float {
-        const float v = PV(q, i, j);
-        const bool ok = (q & 1) == 0 ? j <= C - 2 : i <= R - 2;
-        return ok ? v : 0.f;
-    };
-    auto wpoint = [&](int r, int c) {
-        const int i = i0 - 1 + r, j = j0 - 1 + c;
-        float w1 = 0.f, w2 = 0.f;
-        if (i >= 0 && j >= 0 && i < R && j < C) {
-            w1 = (P(0, i, j) - P(0, i, j - 1)) + (P(1, i, j) - P(1, i - 1, j));
-            w2 = (P(2, i, j) - P(2, i, j - 1)) + (P(3, i, j) - P(3, i - 1, j));
-            if (j > C - 2) w1 = 0.f;
-            if (i > R - 2) w2 = 0.f;
-        }
-        sw[r * kW5 + c] = w1;
-        sw[(kW5 + r) * kW5 + c] = w2;
-    };
-    for (int r = ty; r < kW5; r += kBY) wpoint(r, tx + 1);
-    for (int r = tid; r < kW5; r += NT) wpoint(r, 0);            // region column 0
-    __syncthreads();
+        // the update on rows/columns i0 - 2 .. i0 + 31, in place in the p box; the
+        // tile itself also goes to pout; CHECK: the gap terms at the input p (tile only)
+        auto upoint = [&](int r, int c) {                   // z region position of (i, j) is (r, c)
+            const int i = i0 - 2 + r, j = j0 - 2 + c;
+            const bool in_grid = !EDGE || (i >= 0 && j >= 0 && i < R && j < C);
+            const bool tile = r >= 2 && c >= 2 && in_grid;
+            float pv[4] = {0.f, 0.f, 0.f, 0.f};
+            float vnew[4] = {0.f, 0.f, 0.f, 0.f};
+            float zc[2] = {0.f, 0.f}, gx[2] = {0.f, 0.f}, gy[2] = {0.f, 0.f};
+            if (in_grid) {
 #pragma unroll
-    for (int rr = ty; rr < kTY; rr += kBY) {
-        const int i = i0 + rr, j = j0 + tx;
-        if (i < R && j < C) {
-            const int r = rr + 1, c = tx + 1;
-            src[(size_t)i * pitch + j] =
-                (sw[r * kW5 + c] - sw[r * kW5 + c - 1]) + (sw[(kW5 + r) * kW5 + c] - sw[(kW5 + r - 1) * kW5 + c]);
+                for (int k = 0; k < 2; ++k) {
+                    const float* zk = sz + k * kZ5 * kZ5;
+                    zc[k] = zk[r * kZ5 + c];
+                    gx[k] = (!EDGE || j < C - 1) ? zk[r * kZ5 + c + 1] - zc[k] : 0.f;
+                    gy[k] = (!EDGE || i < R - 1) ? zk[(r + 1) * kZ5 + c] - zc[k] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pv[q] = PV(q, i, j);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float s2 = fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1e-30f));
+                    const float inv = rcp_ftz(fmaf(t, s2 * rsqrt_ftz(s2), 1.0f));
+                    vnew[2 * k] = fmaf(t, gx[k], pv[2 * k]) * inv;
+                    vnew[2 * k + 1] = fmaf(t, gy[k], pv[2 * k + 1]) * inv;
+                }
+            }
+            const size_t o = (size_t)i * pitch + j;
+            const uint32_t h = (sizeof(SP) == 4 || !in_grid) ? 0u : rkey(seed, o, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                SP* slot = sp + PO(q, i, j);
+                // the same rounding as tfs_update_kernel's store of this point (zero outside the grid)
+                Stor<SP>::st1r8(slot, vnew[q], (h >> (8 * q)) & 0xffU);
+                if (tile) {
+                    if constexpr (sizeof(SP) == 4) pout[(size_t)q * plane + o] = vnew[q];
+                    else pout[(size_t)q * plane + o] = *slot;
+                }
+            }
+            if (CHECK && tile) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float a = gx[k], b = gy[k], px = pv[2 * k], py = pv[2 * k + 1];
+                    const float s2 = fmaf(a, a, fmaf(b, b, 1e-30f));
+                    const float ng = s2 * rsqrt_ftz(s2);
+                    ks[0] += ng;
+                    ks[1] += ng - fmaf(a, px, b * py);
+                    ks[2] = fmaf(zc[k], zc[k], ks[2]);
+                    const float zf = zc[k] + sf[k * kBoxFloats5 + B(i, j)];
+                    ks[3] = fmaf(zf, zf, ks[3]);
+                    pmax2 = fmaxf(pmax2, fmaf(px, px, py * py));
+                }
+                const float z1c = (!EDGE || j <= C - 2) ? zc[0] : 0.f;
+                const float z1l = (!EDGE || j >= 1) ? sz[r * kZ5 + c - 1] : 0.f;
+                const float z2c = (!EDGE || i <= R - 2) ? zc[1] : 0.f;
+                const float z2u = (!EDGE || i >= 1) ? sz[(kZ5 + r - 1) * kZ5 + c] : 0.f;
+                dmax = fmaxf(dmax, fabsf((z1c - z1l) + (z2c - z2u)));
+            }
+        };
+        for (int r = ty; r < kU5; r += kBY) upoint(r, tx + 2);
+        for (int e = tid; e < 2 * kU5; e += NT) upoint(e >> 1, e & 1);   // region columns 0 and 1
+        __syncthreads();
+
+        // w = vecdiv p_new on rows/columns i0 - 1 .. i0 + 31, then s = div w on the
+        // tile (as div_vecdiv_kernel, with the D^- rule)
+        auto P = [&](int q, int i, int j) -> float {
+            const float v = PV(q, i, j);
+            if constexpr (!EDGE) return v;
+            const bool ok = (q & 1) == 0 ? j <= C - 2 : i <= R - 2;
+            return ok ? v : 0.f;
+        };
+        auto wpoint = [&](int r, int c) {
+            const int i = i0 - 1 + r, j = j0 - 1 + c;
+            float w1 = 0.f, w2 = 0.f;
+            if (!EDGE || (i >= 0 && j >= 0 && i < R && j < C)) {
+                w1 = (P(0, i, j) - P(0, i, j - 1)) + (P(1, i, j) - P(1, i - 1, j));
+                w2 = (P(2, i, j) - P(2, i, j - 1)) + (P(3, i, j) - P(3, i - 1, j));
+                if (EDGE && j > C - 2) w1 = 0.f;
+                if (EDGE && i > R - 2) w2 = 0.f;
+            }
+            sw[r * kW5 + c] = w1;
+            sw[(kW5 + r) * kW5 + c] = w2;
+        };
+        for (int r = ty; r < kW5; r += kBY) wpoint(r, tx + 1);
+        for (int r = tid; r < kW5; r += NT) wpoint(r, 0);            // region column 0
+        __syncthreads();
+#pragma unroll
+        for (int rr = ty; rr < kTY; rr += kBY) {
+            const int i = i0 + rr, j = j0 + tx;
+            if (!EDGE || (i < R && j < C)) {
+                const int r = rr + 1, c = tx + 1;
+                src[(size_t)i * pitch + j] =
+                    (sw[r * kW5 + c] - sw[r * kW5 + c - 1]) + (sw[(kW5 + r) * kW5 + c] - sw[(kW5 + r - 1) * kW5 + c]);
+            }
         }
-    }
+    };
+    if (interior) phases(std::false_type{});
+    else phases(std::true_type{});
     if (CHECK)
         block_reduce_store_tfs<NT>(ks, sqrtf(pmax2), dmax,
                                    partial + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kRedSlots, tid);
