@@ -170,8 +170,10 @@ cudaError_t poisson_solve_batched(float* S, int nbatch, long bstride, const int2
 // terms, each >= 0 while |p| <= 1), 2 sum z^2, 3 sum (z + f)^2, 4 max |p|,
 // 5 max |div z|; 6, 7 unused.
 constexpr int kRedSlots = 8;
+constexpr int kFinCTAs = 128;   // CTAs of the first pass of finalize_red
 struct RedBuf {
     double* partial;   // [nblocks][kRedSlots]
+    double* stage;     // [kFinCTAs][kRedSlots]: the first pass of finalize_red
     double* result;    // [kRedSlots]
     unsigned* err;     // bit 0: a bounded device-side wait gave up
     int cap;           // capacity in blocks
