@@ -343,19 +343,25 @@ static tvs_status admit(EngineImpl* e) {
 // n TFS updates (the last with the check sums), the reduction and its copy
 // to the request's row of the pinned result array, on stream s; cur1/nxt1
 // alternate from *cur, *nxt.
+// The updates are the fused step of the global loop: div(vecdiv p) of the
+// chunk's first iterate, then per update the Poisson solve of the current
+// source and the update that also writes the next source.
 static cudaError_t step1_launches(EngineImpl* e, Request* r, int n, float** cur, float** nxt, cudaStream_t s) {
     const Step1Layout& L = r->L1;
-    const float t = (float)e->cfg.it1.t, fd = (float)e->cfg.delta;
+    const float t = (float)e->cfg.it1.t;
+    cudaError_t err = launch_div_vecdiv_st(*cur, TVS_F32, L.R, L.C, L.P, L.plane, L.src, L.red.err, s);
+    if (err != cudaSuccess) return err;
     for (int j = 0; j < n; ++j) {
         const bool ck = j == n - 1;
-        cudaError_t err = tfs_phi(*cur, L.S, L.R, L.C, L.P, L.plane, L.pp, L.red.err, s);
+        RowSrcArgs sa{L.src, 0, L.P};
+        err = poisson_solve(L.S, L.R, L.C, L.P, L.pp, RowSource::Plain, sa, s);
         if (err != cudaSuccess) return err;
-        err = launch_tfs_update(*cur, *nxt, L.S, L.f1, L.R, L.C, L.P, L.plane, t, fd, ck, true, nullptr, 0, 0,
-                                L.red.partial, L.red.err, s);
+        err = launch_tfs_step_st(*cur, *nxt, TVS_F32, 0u, L.S, L.f1, L.src, L.R, L.C, L.P, L.plane, t, ck,
+                                 L.red.partial, L.red.err, s);
         if (err != cudaSuccess) return err;
         std::swap(*cur, *nxt);
     }
-    const cudaError_t err = finalize_red(L.red, tfs_blocks(L.R, L.C), s);
+    err = finalize_red(L.red, tfs_blocks(L.R, L.C), s);
     if (err != cudaSuccess) return err;
     return cudaMemcpyAsync(e->host_red + (size_t)r->slot * kRedSlots, L.red.result, kRedSlots * sizeof(double),
                            cudaMemcpyDeviceToHost, s);
