@@ -33,6 +33,15 @@ constexpr int kBoxC = 4;          // box column of grid column j0
 constexpr int kBoxR = 2;          // box row of grid row i0
 constexpr int kBoxFloats = kBW * kBH;
 
+// The halo points of a phase whose main loop gives warp w the region rows
+// w, w + kBY, ... go first to the warps with one row fewer (w >= rows % kBY):
+// thread slots are rotated so that warp rows % kBY takes halo point 0.  The
+// rotation is a bijection of 0 .. NT - 1, so every point is still done once.
+__device__ __forceinline__ int halo_slot(int tid, int rows) {
+    constexpr int NT = kTX * kBY;
+    return (tid + NT - (rows % kBY) * kTX) % NT;
+}
+
 // Box of the dual p in storage S: columns j0 - C0 .. j0 + kTX + C0 - 1, so
 // that the box starts on a 16-byte boundary for 4- and 2-byte elements.
 template <class S>
@@ -230,7 +239,7 @@ div_vecdiv_kernel(const __grid_constant__ CUtensorMap pmap, int R, int C, int pi
         sw[(WH + r) * WW + c] = w2;
     };
     for (int r = ty; r < WH; r += kBY) wpoint(r, tx + 1);
-    for (int r = tid; r < WH; r += NT) wpoint(r, 0);
+    for (int r = halo_slot(tid, WH); r < WH; r += NT) wpoint(r, 0);
     __syncthreads();
 #pragma unroll
     for (int rr = ty; rr < kTY; rr += kBY) {
@@ -361,7 +370,7 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
         sz[(kZH + r) * kZW + c] = z2;
     };
     for (int r = ty; r < kZH; r += kBY) zpoint(r, tx + 1);
-    for (int e = tid; e < 2 * kZH; e += NT) zpoint(e >> 1, (e & 1) ? kZW - 1 : 0);
+    for (int e = halo_slot(tid, kZH); e < 2 * kZH; e += NT) zpoint(e >> 1, (e & 1) ? kZW - 1 : 0);
     __syncthreads();
 
     // check sums: each thread adds the 8 terms of its 4 points and 2 channels
@@ -549,7 +558,7 @@ tfs_step_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant_
             sz[(kZ5 + r) * kZ5 + c] = z2;
         };
         for (int r = ty; r < kZ5; r += kBY) zpoint(r, tx + 2);
-        for (int e = tid; e < 3 * kZ5; e += NT) {           // region columns 0, 1 and 34
+        for (int e = halo_slot(tid, kZ5); e < 3 * kZ5; e += NT) {   // region columns 0, 1 and 34
             const int r = e / 3, k = e - 3 * r;
             zpoint(r, k < 2 ? k : kZ5 - 1);
         }
@@ -615,7 +624,7 @@ tfs_step_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant_
             }
         };
         for (int r = ty; r < kU5; r += kBY) upoint(r, tx + 2);
-        for (int e = tid; e < 2 * kU5; e += NT) upoint(e >> 1, e & 1);   // region columns 0 and 1
+        for (int e = halo_slot(tid, kU5); e < 2 * kU5; e += NT) upoint(e >> 1, e & 1);   // region columns 0, 1
         __syncthreads();
 
         // w = vecdiv p_new on rows/columns i0 - 1 .. i0 + 31, then s = div w on the
@@ -639,7 +648,7 @@ tfs_step_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant_
             sw[(kW5 + r) * kW5 + c] = w2;
         };
         for (int r = ty; r < kW5; r += kBY) wpoint(r, tx + 1);
-        for (int r = tid; r < kW5; r += NT) wpoint(r, 0);            // region column 0
+        for (int r = halo_slot(tid, kW5); r < kW5; r += NT) wpoint(r, 0);   // region column 0
         __syncthreads();
 #pragma unroll
         for (int rr = ty; rr < kTY; rr += kBY) {

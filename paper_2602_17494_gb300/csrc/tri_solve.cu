@@ -306,7 +306,7 @@ cudaError_t launch_n(float* S, int rows, int cols, int pitch, const float4* tab,
 // and (mu, mean w) of column 0.
 // ---------------------------------------------------------------------------
 constexpr int kChunkWarps = 8;    // warps (chunks) per CTA of the sum and apply kernels
-constexpr int kScanWarps = 16;    // warps (chunk ranges) per CTA of the scan kernel
+constexpr int kScanWarps = 24;    // warps (chunk ranges) per CTA of the scan kernel
 
 struct ChunkBufs {
     float *h, *a, *g, *cin, *win, *k0, *par;

@@ -90,7 +90,7 @@ def test_rows_then_columns_reproduce_the_oracle_pseudo_inverse():
     assert np.abs(phi - ops.inv_lap(s)).max() <= 1e-10 * np.abs(phi).max()
 
 
-def chunked(b: np.ndarray, lam: float, chunk: int = 32, ranges: int = 16) -> np.ndarray:
+def chunked(b: np.ndarray, lam: float, chunk: int = 32, ranges: int = 24) -> np.ndarray:
     """The same solve in the chunked form of the long-column kernels.
 
     Per chunk of `chunk` rows, summaries from a zero carry: h = sum r^(i-i0) b_i,
@@ -180,12 +180,13 @@ def chunked(b: np.ndarray, lam: float, chunk: int = 32, ranges: int = 16) -> np.
     return out
 
 
+@pytest.mark.parametrize("ranges", [24, 16, 7])
 @pytest.mark.parametrize("rows,cols", [(1537, 64), (2049, 2049), (1601, 33), (40, 7)])
-def test_chunked_recursions_equal_the_one_pass_recursions(rows, cols):
+def test_chunked_recursions_equal_the_one_pass_recursions(rows, cols, ranges):
     rng = np.random.default_rng(rows + cols)
     lam = ops.sigma(cols) ** 2
     for k in sorted({0, 1, 2, cols // 2, cols - 1}):
         b = rng.standard_normal(rows)
-        got = chunked(b, float(lam[k]))
+        got = chunked(b, float(lam[k]), ranges=ranges)
         ref = recursions(b, float(lam[k]))
         assert np.abs(got - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max())
