@@ -23,11 +23,12 @@ constexpr int kTY = 32;   // tile height (outputs)
 constexpr int kBY = 8;    // thread rows; each thread does kTY / kBY output rows
 
 // The tiled stencils below receive their inputs as TMA boxes covering the
-// tile plus a halo: columns j0 - 4 .. j0 + kTX + 3 (16-byte aligned start),
-// rows i0 - 2 .. i0 + kTY + 1.  Reads outside the grid come back as zeros;
+// tile plus a halo: columns j0 - 4 .. j0 + kTX + 3 are read (16-byte aligned
+// start; an FP32 box carries 4 more, unused, see PBox), rows i0 - 2 ..
+// i0 + kTY + 1.  Reads outside the grid come back as zeros;
 // the D^- rule (x-parts zero in the last column, y-parts in the last row) is
 // applied when the box is read.
-constexpr int kBW = kTX + 8;      // box width
+constexpr int kBW = kTX + 12;     // box width (see PBox for the 4 unused columns)
 constexpr int kBH = kTY + 4;      // box height
 constexpr int kBoxC = 4;          // box column of grid column j0
 constexpr int kBoxR = 2;          // box row of grid row i0
@@ -42,17 +43,29 @@ __device__ __forceinline__ int halo_slot(int tid, int rows) {
     return (tid + NT - (rows % kBY) * kTX) % NT;
 }
 
-// Box of the dual p in storage S: columns j0 - C0 .. j0 + kTX + C0 - 1, so
-// that the box starts on a 16-byte boundary for 4- and 2-byte elements.
+// Box of the dual p in storage S: columns j0 - C0 .. j0 + kTX + C0 - 1 + PAD,
+// so that the box starts on a 16-byte boundary for 4- and 2-byte elements.
+// In FP32 the last PAD = 4 columns (16 bytes) are never read: they make a
+// box row 4 mod 8 words long (16 mod 32 bytes), so the rows of one box column
+// fall into 8 groups of banks instead of 4, which halves the bank conflicts
+// of the loops that walk the halo columns.  The FP32 phi and f1 boxes have
+// that width too.  A 16-bit box keeps 48 columns: 16 more bytes per row would
+// leave the fused step four CTAs per SM instead of five.
 template <class S>
 struct PBox {
     static constexpr int C0 = 16 / (int)sizeof(S);
-    static constexpr int W = kTX + 2 * C0;
+    static constexpr int PAD = sizeof(S) == 4 ? C0 : 0;
+    static constexpr int W = kTX + 2 * C0 + PAD;
     static constexpr int ELEMS = W * kBH;                        // one plane
     static constexpr int BYTES = 4 * ELEMS * (int)sizeof(S);     // four planes
     static constexpr int BYTES_AL = (BYTES + 127) / 128 * 128;
 };
-inline int pbox_width(int storage) { return kTX + 2 * (16 / (int)storage_bytes(storage)); }
+static_assert(PBox<float>::W == kBW, "phi and f1 boxes as wide as an FP32 p box");
+static_assert((PBox<float>::W * 4) % 32 == 16, "FP32 box rows 4 mod 8 words long");
+inline int pbox_width(int storage) {
+    const int c0 = 16 / (int)storage_bytes(storage);
+    return kTX + 2 * c0 + (storage == TVS_F32 ? c0 : 0);
+}
 
 // Cached tensor maps of one field: rebuilt only when the base, sizes, plane
 // count or storage change.
@@ -310,9 +323,13 @@ cudaError_t launch_grad_sub(const float* u, int upitch, long uplane, const float
 // the TY x TX outputs.
 // ---------------------------------------------------------------------------
 constexpr int kZH = kTY + 2, kZW = kTX + 2;   // z region: rows i0-1.., cols j0-1..
+// The tensor copies land on 128-byte boundaries: the phi box is padded to one.
+constexpr int kPhiAl = (kBoxFloats + 31) / 32 * 32;
+static_assert((kPhiAl * 4) % 128 == 0, "f1 box of the update on a 128-byte boundary");
+static_assert(((kPhiAl + 2 * kBoxFloats + 2 * kZH * kZW) * 4) % 8 == 0, "mbarrier of the update 8-byte aligned");
 template <class SP>
 constexpr size_t upd_smem() {
-    return (size_t)PBox<SP>::BYTES_AL + (size_t)3 * kBoxFloats * 4 + (size_t)2 * kZH * kZW * 4 + 256;
+    return (size_t)PBox<SP>::BYTES_AL + (size_t)(kPhiAl + 2 * kBoxFloats) * 4 + (size_t)2 * kZH * kZW * 4 + 256;
 }
 
 // SP: storage of p (in and out); TT: type of tau_out (float, or a 16-bit
@@ -330,8 +347,8 @@ tfs_update_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constan
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* base = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     const SP* sp = reinterpret_cast<const SP*>(base);                  // [4][BH][PB::W]
-    float* sphi = reinterpret_cast<float*>(base + PB::BYTES_AL);      // [BH][BW]
-    float* sf = sphi + kBoxFloats;                 // [2][BH][BW]
+    float* sphi = reinterpret_cast<float*>(base + PB::BYTES_AL);      // [BH][BW], padded to 128 bytes
+    float* sf = sphi + kPhiAl;                     // [2][BH][BW]
     float* sz = sf + 2 * kBoxFloats;               // [2][ZH][ZW]
     uint64_t* bar = reinterpret_cast<uint64_t*>(sz + 2 * kZH * kZW);   // 8-byte aligned (even float count)
     const int tx = threadIdx.x, ty = threadIdx.y;
